@@ -1,0 +1,301 @@
+/*
+ * FP64 CPU oracle for one step of Lenia with localized genes.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library.  It shares no
+ * code, header, table or constant with the CUDA library: every formula is
+ * written out here again from the paper (arXiv 2304.05639) and from the
+ * original Lenia definitions that paper builds on.
+ *
+ * Plain, slow, obviously correct: direct periodic (toroidal) convolution,
+ * loops in the order the definitions are written, double precision
+ * throughout, OpenMP only across independent output rows (each output is
+ * computed by one thread in a fixed order, so results do not depend on the
+ * thread count).
+ *
+ * Step order follows Algorithm 2 (intrinsic evolution loop): diffuse the
+ * genospace, convolve the phenospace, compute alpha, mask the genospace,
+ * growth mapping and clipped update.  Environment, E_pen, mutation and
+ * penalization (the other lines of Algorithm 2) are not part of this step.
+ *
+ * Readings where the paper is silent or ambiguous (each one is also listed in
+ * the design notes):
+ *  R1 growth: signed form h*(2*exp(-(u-m)^2/(2 s^2)) - 1) (form 0) or the
+ *     paper's h*exp(...) (form 1, Section 2.4).
+ *  R2 dt multiplies the growth sum; the paper's update is dt = 1.
+ *  R3 kernel: rho = |d|_2 / R, zero for rho >= 1.  Shell form
+ *     beta[floor(B rho)] * core(B rho mod 1), core(q) = exp(4 - 1/(q(1-q))),
+ *     core(0) = 0.  Bump form sum_i b_i exp(-(rho - r_i)^2 / (2 w_i^2)).
+ *  R5 alpha tests h_k*g_k > eps_u (g in [0,1]), AND over k, and every gene
+ *     plane > eps_p (Delta_all); alpha_on = 1 tests U_k > eps_u instead.
+ *  R6 eps_u and eps_p are separate thresholds, strict '>'.
+ *  R7 K_diff is the disk |d|_2 <= r_diff.
+ *  R8 diffusion with no neighbour above eps_p gives 0.
+ *  R9 g = 0 where the gene sigma is 0; the update uses the masked genes, so
+ *     where alpha = 0 the growth is h*(2*0 - 1) = -h (form 0) or 0 (form 1).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define LOC_MU 1
+#define LOC_SIGMA 2
+#define LOC_H 4
+
+/* Lenia kernel core (original Lenia, cited in Section 1.2): a smooth bump on
+ * (0,1) with value 1 at q = 1/2 and limit 0 at both ends. */
+static double kernel_core(double q)
+{
+    if (q <= 0.0 || q >= 1.0) return 0.0;
+    return exp(4.0 - 1.0 / (q * (1.0 - q)));
+}
+
+/* Unnormalised kernel value at pixel offset (dy, dx). */
+static double kernel_value(int R, int form, int n_shells, const double* beta,
+                           const double* bump, int dy, int dx)
+{
+    double rho = sqrt((double)dy * dy + (double)dx * dx) / (double)R;
+    if (rho >= 1.0) return 0.0;
+    if (form == 0) {
+        double br = n_shells * rho;
+        int i = (int)floor(br);
+        return beta[i] * kernel_core(br - i);
+    }
+    /* Section 2.4: kernel function k(x; r, w, b) = b exp(-(x - r)^2 / 2 w^2),
+     * two bumps (r1, w1, b1, r2, w2, b2). */
+    double v = 0.0;
+    for (int i = 0; i < 2; i++) {
+        double r = bump[3 * i], w = bump[3 * i + 1], b = bump[3 * i + 2];
+        v += b * exp(-(rho - r) * (rho - r) / (2.0 * w * w));
+    }
+    return v;
+}
+
+/* Normalised kernel K~ = K / (K * 1), Algorithm 1 pre-calculation and the
+ * note after Algorithm 2 (K * 1 = sum over the kernel).  out has (2R+1)^2
+ * entries, row-major over dy = -R..R, dx = -R..R.  Returns 0, or -1 if the
+ * kernel sums to zero. */
+int oracle_kernel(int R, int form, int n_shells, const double* beta,
+                  const double* bump, double* out)
+{
+    int n = 2 * R + 1;
+    double sum = 0.0;
+    for (int dy = -R; dy <= R; dy++)
+        for (int dx = -R; dx <= R; dx++) {
+            double v = kernel_value(R, form, n_shells, beta, bump, dy, dx);
+            out[(dy + R) * n + (dx + R)] = v;
+            sum += v;
+        }
+    if (!(sum > 0.0)) return -1;
+    for (int i = 0; i < n * n; i++) out[i] /= sum;
+    return 0;
+}
+
+static inline int wrap(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+/* Periodic convolution U = K~ * A on an H x W torus (Section 2.1, toroidal
+ * world; Algorithm 1 "convolve the phenotype with kernels"):
+ *   U(y, x) = sum_{dy,dx} K~(dy, dx) A(y - dy, x - dx).
+ * Zero kernel taps are skipped (adding an exact zero changes nothing).
+ * With extended != 0 the sum is accumulated in long double, to measure the
+ * oracle's own rounding error. */
+void oracle_potential(int H, int W, const double* A, int R, const double* K,
+                      double* U, int extended)
+{
+    int n = 2 * R + 1;
+    #pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            double s = 0.0;
+            long double sl = 0.0L;
+            for (int dy = -R; dy <= R; dy++) {
+                const double* krow = K + (dy + R) * n;
+                const double* arow = A + (size_t)wrap(y - dy, H) * W;
+                for (int dx = -R; dx <= R; dx++) {
+                    double k = krow[dx + R];
+                    if (k == 0.0) continue;
+                    double a = arow[wrap(x - dx, W)];
+                    if (extended) sl += (long double)k * (long double)a;
+                    else s += k * a;
+                }
+            }
+            U[(size_t)y * W + x] = extended ? (double)sl : s;
+        }
+    }
+}
+
+/* Genospace diffusion of one gene plane (Section 2.3):
+ *   P -> clip( (P * K_diff) / (Delta_same(P) * K_diff), 0, 1 )
+ * K_diff the disk |d| <= r_diff (R7), Delta_same(P) = [P > eps_p] (Section
+ * 2.2), 0 where no disk site is above eps_p (R8). */
+void oracle_diffuse(int H, int W, const double* P, int r_diff, double eps_p, double* out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            double s = 0.0;
+            int cnt = 0;
+            for (int dy = -r_diff; dy <= r_diff; dy++)
+                for (int dx = -r_diff; dx <= r_diff; dx++) {
+                    if (dy * dy + dx * dx > r_diff * r_diff) continue;
+                    double v = P[(size_t)wrap(y + dy, H) * W + wrap(x + dx, W)];
+                    s += v;
+                    if (v > eps_p) cnt++;
+                }
+            double r = 0.0;
+            if (cnt > 0) {
+                r = s / (double)cnt;
+                if (r < 0.0) r = 0.0;
+                if (r > 1.0) r = 1.0;
+            }
+            out[(size_t)y * W + x] = r;
+        }
+    }
+}
+
+/* Gaussian bump of the growth mapping, g in [0, 1]; 0 where s <= 0 (R9). */
+static double growth_bump(double u, double m, double s)
+{
+    if (!(s > 0.0)) return 0.0;
+    double z = (u - m) / s;
+    return exp(-0.5 * z * z);
+}
+
+typedef struct {
+    int H, W, C, K;
+    double dt;
+    int growth_form, localized, maintain, r_diff, alpha_on;
+    double eps_u, eps_p;
+} oracle_cfg;
+
+/* One full step.
+ *  A[C][H][W] in, A_out out; P[n_p][K][H][W] in (NULL when no gene maps),
+ *  P_out out (NULL allowed); U_out[K][H][W], alpha_out[H][W] optional.
+ *  Kernels: src[k], dst[k], R[k], h/mu/sigma[k] global genes; Kw holds the
+ *  normalised kernels back to back, kernel k at offset kw_off[k].
+ * Returns 0. */
+int oracle_step(const oracle_cfg* cfg, const int* src, const int* dst, const int* R,
+                const double* h, const double* mu, const double* sigma,
+                const double* Kw, const long* kw_off,
+                const double* A, const double* P, double* A_out, double* P_out,
+                double* U_out, unsigned char* alpha_out)
+{
+    const int H = cfg->H, W = cfg->W, C = cfg->C, K = cfg->K;
+    const size_t N = (size_t)H * W;
+    const int loc = cfg->localized;
+    const int n_p = ((loc & LOC_MU) != 0) + ((loc & LOC_SIGMA) != 0) + ((loc & LOC_H) != 0);
+    const int p_mu = (loc & LOC_MU) ? 0 : -1;
+    const int p_sigma = (loc & LOC_SIGMA) ? ((loc & LOC_MU) ? 1 : 0) : -1;
+    const int p_h = (loc & LOC_H) ? n_p - 1 : -1;
+
+    /* Algorithm 2: diffuse the genospace (before the convolution). */
+    double* Ph = NULL;
+    if (n_p > 0) {
+        Ph = (double*)malloc(sizeof(double) * (size_t)n_p * K * N);
+        for (int pk = 0; pk < n_p * K; pk++) {
+            if (cfg->maintain)
+                oracle_diffuse(H, W, P + (size_t)pk * N, cfg->r_diff, cfg->eps_p, Ph + (size_t)pk * N);
+            else
+                memcpy(Ph + (size_t)pk * N, P + (size_t)pk * N, sizeof(double) * N);
+        }
+    }
+
+    /* Algorithm 2: convolve the phenospace with every kernel; the weighted
+     * sum over rings collapses to one normalised kernel when the kernel genes
+     * are global. */
+    double* U = (double*)malloc(sizeof(double) * (size_t)K * N);
+    for (int k = 0; k < K; k++)
+        oracle_potential(H, W, A + (size_t)src[k] * N, R[k], Kw + kw_off[k], U + (size_t)k * N, 0);
+
+    #pragma omp parallel for schedule(static)
+    for (long i = 0; i < (long)N; i++) {
+        double g[64];
+        double hk[64];
+        int alpha = 1;
+        for (int k = 0; k < K; k++) {
+            double m = p_mu >= 0 ? Ph[((size_t)p_mu * K + k) * N + i] : mu[k];
+            double s = p_sigma >= 0 ? Ph[((size_t)p_sigma * K + k) * N + i] : sigma[k];
+            hk[k] = p_h >= 0 ? Ph[((size_t)p_h * K + k) * N + i] : h[k];
+            double u = U[(size_t)k * N + i];
+            g[k] = growth_bump(u, m, s);
+            if (cfg->maintain) {
+                /* Section 2.2: alpha = Delta_all(U) AND Delta_all(P) (R5). */
+                double t = cfg->alpha_on ? u : hk[k] * g[k];
+                if (!(t > cfg->eps_u)) alpha = 0;
+            }
+        }
+        if (cfg->maintain)
+            for (int pk = 0; pk < n_p * K; pk++)
+                if (!(Ph[(size_t)pk * N + i] > cfg->eps_p)) alpha = 0;
+        if (!cfg->maintain) alpha = 1;
+        if (alpha_out) alpha_out[i] = (unsigned char)alpha;
+
+        /* Mask the genospace: P -> P (.) alpha. */
+        if (P_out)
+            for (int pk = 0; pk < n_p * K; pk++)
+                P_out[(size_t)pk * N + i] = alpha ? Ph[(size_t)pk * N + i] : 0.0;
+
+        /* Growth mapping and clipped update with the masked genes (R1, R2,
+         * R9): A_i -> [A_i + dt sum_{k: dst(k) = i} G_k(U_k)]_0^1. */
+        for (int c = 0; c < C; c++) {
+            double acc = 0.0;
+            for (int k = 0; k < K; k++) {
+                if (dst[k] != c) continue;
+                double gm = alpha ? g[k] : 0.0;
+                double hm = (p_h >= 0 && !alpha) ? 0.0 : hk[k];
+                double G = cfg->growth_form == 0 ? hm * (2.0 * gm - 1.0) : hm * gm;
+                acc += G;
+            }
+            double a = A[(size_t)c * N + i] + cfg->dt * acc;
+            if (a < 0.0) a = 0.0;
+            if (a > 1.0) a = 1.0;
+            A_out[(size_t)c * N + i] = a;
+        }
+    }
+    if (U_out) memcpy(U_out, U, sizeof(double) * (size_t)K * N);
+    free(U);
+    free(Ph);
+    return 0;
+}
+
+/* Per-channel mass and circular-mean centroid:
+ *   M = sum A,  centre_y = atan2(sum A sin(2 pi y / H), sum A cos(2 pi y / H)) H / (2 pi)
+ * wrapped to [0, H); same for x.  out[C][3] = (mass, centre_y, centre_x). */
+void oracle_stats(int C, int H, int W, const double* A, double* out)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int c = 0; c < C; c++) {
+        double m = 0.0, sy = 0.0, cy = 0.0, sx = 0.0, cx = 0.0;
+        for (int y = 0; y < H; y++)
+            for (int x = 0; x < W; x++) {
+                double a = A[((size_t)c * H + y) * W + x];
+                m += a;
+                sy += a * sin(two_pi * y / H);
+                cy += a * cos(two_pi * y / H);
+                sx += a * sin(two_pi * x / W);
+                cx += a * cos(two_pi * x / W);
+            }
+        double ty = atan2(sy, cy) * H / two_pi;
+        double tx = atan2(sx, cx) * W / two_pi;
+        if (ty < 0.0) ty += H;
+        if (tx < 0.0) tx += W;
+        out[c * 3 + 0] = m;
+        out[c * 3 + 1] = ty;
+        out[c * 3 + 2] = tx;
+    }
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
