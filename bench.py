@@ -1,0 +1,305 @@
+"""Benchmark: Lenia cell-updates/s on one GB300 (or N independent replicas).
+
+Workload: the 2048 x 2048, 3-channel, 15-kernel (R = 18) world with
+localized mu/sigma gene maps and gene maintenance on (seeded synthetic
+input shaped like the paper's runs).  One step = one pass of the whole hot
+path: row FFTs, column FFT x kernel spectra x inverse, inverse row FFTs,
+diffusion + growth + alpha mask + clipped update, and per-channel stats.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s at 2048^2 FP32 (% HBM roofline); batched & adjoint vs plain step"
+UNIT = "cell-updates/s"
+WORKLOAD = "lenia 2048x2048, 3 channels, 15 shell kernels R=18, localized mu/sigma maps, gene maintenance"
+# Algorithmic bytes per site-step: A read + write (3 channels x 4 B x 2) and
+# the 30 gene planes read + write (30 x 4 B x 2).
+ALG_BYTES_PER_SITE = 3 * 4 * 2 + 30 * 4 * 2
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class OracleSample:
+    """The FP64 oracle as it stands, on this host's cores, over bounded random
+    samples of the workload's sites (each site: 15 direct potentials, 30 gene
+    diffusions, growth, alpha mask and update)."""
+
+    def __init__(self):
+        import oracle
+        from paper_2304_05639_gb300 import inputs
+        oracle.build()
+        self.oracle, self.inputs = oracle, inputs
+        self.world = inputs.multi_channel()
+        self.rng = inputs.Rng(99)
+        self.rate = None
+
+    def run(self, n: int):
+        ys = self.rng.integers(n, 0, self.world.height - 1)
+        xs = self.rng.integers(n, 0, self.world.width - 1)
+        t0 = time.perf_counter()
+        self.oracle.step_sites(self.world, ys, xs)
+        return time.perf_counter() - t0
+
+    def sites_for(self, seconds: float) -> int:
+        if self.rate is None:
+            self.rate = 1024 / max(self.run(1024), 1e-4)
+        return int(min(2_000_000, max(256, self.rate * seconds)))
+
+    def describe(self, n, dt):
+        return {"value": n / dt, "unit": UNIT, "cores": self.oracle.num_threads(), "kind": "oracle",
+                "sample": f"{n} random sites of the 2048^2 workload, one step each "
+                          f"({dt:.2f} s; FP64 direct sums)"}
+
+
+def cpu_baseline(seconds_target: float = 15.0):
+    s = OracleSample()
+    n = s.sites_for(seconds_target)
+    return s.describe(n, s.run(n))
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    s = OracleSample()
+    per_step = max(0.25, 120.0 / max(1, args.steps + args.warmup))
+    n = s.sites_for(per_step)
+    vals, tot = [], 0.0
+    for i in range(args.warmup + args.steps):
+        dt = s.run(n)
+        if i >= args.warmup:
+            vals.append(n / dt)
+            tot += dt
+    v = len(vals) * n / tot
+    cb = s.describe(n * len(vals), tot)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 2048 * 2048 / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": 0,
+                       "parallelism": "replicas"},
+            "cpu_baseline": {**cb, "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2304_05639_gb300 import build, inputs, lenia
+    if rank == 0 or ws == 1:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    world = inputs.multi_channel()
+    cfg, ks = lenia.config_from_world(world, lenia.CONV_AUTO)
+    stream = torch.cuda.current_stream(dev)
+    ctx = lenia.lenia_init(cfg, ks, stream)
+    H, W = world.height, world.width
+    sites = H * W
+    A = torch.from_numpy(world.A).to(dev)
+    P = torch.from_numpy(world.P).to(dev)
+    A2, P2 = torch.empty_like(A), torch.empty_like(P)
+    stats = torch.zeros((args.steps + args.warmup, world.n_channels, 3), dtype=torch.float32, device=dev)
+
+    bufs = [(A, P), (A2, P2)]
+
+    def step(i):
+        a_in, p_in = bufs[i % 2]
+        a_out, p_out = bufs[(i + 1) % 2]
+        lenia.lenia_step(ctx, a_in, p_in, a_out, p_out, stats[i], stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    launches_per_step = lenia.lenia_launches_per_step(ctx)
+
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    lenia.lenia_profile_start(ctx, launches_per_step * args.steps + 8)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = lenia.lenia_profile_stop(ctx)
+    clk = clocks.stop() if clocks else None
+
+    # end to end through the public host-buffer entry point
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hA, hP = pin(world.A), pin(world.P)
+    oA, oP = torch.empty_like(hA).pin_memory(), torch.empty_like(hP).pin_memory()
+    hst = torch.zeros((world.n_channels, 3), dtype=torch.float32).pin_memory()
+    e2e_steps = max(2, min(args.steps, 10))
+    lenia.lenia_step_host(ctx, hA, hP, oA, oP, hst, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        lenia.lenia_step_host(ctx, hA if i % 2 == 0 else oA, hP if i % 2 == 0 else oP,
+                              oA if i % 2 == 0 else hA, oP if i % 2 == 0 else hP, hst, stream)
+    e2e_s = time.perf_counter() - t0
+
+    t_max = ms
+    e2e_max = e2e_s
+    if ws > 1:
+        t = torch.tensor([ms, e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max, e2e_max = float(t[0]), float(t[1])
+
+    ok_stats = bool(torch.isfinite(stats).all())
+    path = lenia.lenia_conv_path(ctx)
+    lenia.lenia_destroy(ctx)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    value = ws * sites * args.steps / (t_max / 1e3)
+    hbm, peak_kind = _peaks()
+    # dominant kernel: the largest share of the timed region
+    dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
+    dom_ms = dom[1][0] / max(1, dom[1][1])
+    alg_bytes = ALG_BYTES_PER_SITE * sites
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "height": H, "width": W, "channels": world.n_channels,
+                   "kernels": world.n_kernels, "radius": 18, "gene_planes": 30,
+                   "global_batch": ws, "seq_len": 0,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "conv_path": "fft" if path == lenia.CONV_FFT else "direct",
+                   "l2": "inputs larger than L2 (A + P = 551 MB per world)"},
+        "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None,
+                     "alg_bytes_per_site": ALG_BYTES_PER_SITE,
+                     "step_frac": (ALG_BYTES_PER_SITE * sites * args.steps / (t_max / 1e3) / 1e9) / hbm},
+        "kernels_ms": {k: {"avg_ms": v[0] / max(1, v[1]), "launches": v[1],
+                           "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
+                       for k, v in prof.items()},
+        "e2e": {"value": ws * sites * e2e_steps / e2e_max, "unit": UNIT,
+                "h2d_bytes_per_step": int(world.A.nbytes + world.P.nbytes),
+                "d2h_bytes_per_step": int(world.A.nbytes + world.P.nbytes + hst.numel() * 4)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "stats_finite": ok_stats,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

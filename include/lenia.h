@@ -1,0 +1,192 @@
+/*
+ * lenia.h - C ABI of the GB300 Lenia step library (liblenia.so).
+ *
+ * The library advances a multi-channel Lenia world with localized genes by
+ * one or more steps on one NVIDIA GB300 (sm_103a), following "Towards
+ * Large-Scale Simulations of Open-Ended Evolution in Continuous Cellular
+ * Automata" (Chan, arXiv 2304.05639):
+ *   - phenospace A in R^{c x y x x}, values in [0, 1], toroidal grid (Section 2.1, 2.2);
+ *   - genospace P in R^{p x k x y x x} holding per-site growth genes (Section 2.2);
+ *   - kernels K_k, normalised K~ = K / (K * 1) (Algorithm 1, note after Algorithm 2),
+ *     kernel k reading channel src(k) and writing channel dst(k) (Section 2.1);
+ *   - growth mapping and clipped update A_i -> [A_i + dt sum_k G_k(K~_k * A_j)]_0^1
+ *     (Section 2.1, Algorithm 2), with dt and the signed growth
+ *     2 exp(-(u-m)^2 / 2s^2) - 1 of the original Lenia;
+ *   - gene maintenance: genospace diffusion (Section 2.3) and the alpha mask
+ *     P -> P (.) alpha, alpha = Delta_all(U) AND Delta_all(P) (Section 2.2).
+ *
+ * Conventions for every entry point:
+ *   - Layout: A is float32 [C][H][W]; P is float32 [n_p][K][H][W] with the
+ *     gene planes in the order mu, sigma, h (only the localized ones);
+ *     U is float32 [K][H][W].  All contiguous, row-major, x fastest.
+ *   - Pointers named *_in / *_out / A / P / U / stats_out are DEVICE pointers
+ *     unless the entry point's name ends in _host.  The caller owns them.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Work is enqueued on it and is asynchronous; results are valid after the
+ *     stream is synchronised.  A context is not thread-safe.
+ *   - The library owns the context and all scratch memory (kernel spectra,
+ *     FFT intermediates, potentials, stats partials), allocated in lenia_init
+ *     and freed in lenia_destroy.  No entry point allocates device memory
+ *     after lenia_init.
+ *   - Errors: every entry point returns a status; nothing aborts and nothing
+ *     is thrown.  Arguments are validated before any launch; a CUDA error
+ *     seen after a launch returns LENIA_ECUDA.  lenia_last_error() gives a
+ *     one-line description of the last failure on that context.
+ */
+#ifndef LENIA_H
+#define LENIA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LENIA_API __attribute__((visibility("default")))
+#else
+#define LENIA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lenia_ctx lenia_ctx;
+
+typedef enum {
+    LENIA_OK = 0,
+    LENIA_EINVAL = 1,    /* invalid argument, shape, or aliasing */
+    LENIA_ENOMEM = 2,    /* device or host allocation failed in lenia_init */
+    LENIA_ECUDA = 3,     /* a CUDA call or kernel launch failed */
+    LENIA_ETIMEOUT = 4,  /* a device-side bounded wait gave up */
+    LENIA_ENOTSUP = 5    /* valid request this build does not implement */
+} lenia_status;
+
+enum { LENIA_KERNEL_SHELLS = 0, LENIA_KERNEL_BUMPS = 1 };
+enum { LENIA_GROWTH_SIGNED = 0, LENIA_GROWTH_PAPER = 1 };
+enum { LENIA_LOC_MU = 1, LENIA_LOC_SIGMA = 2, LENIA_LOC_H = 4 };
+enum { LENIA_CONV_AUTO = 0, LENIA_CONV_FFT = 1, LENIA_CONV_DIRECT = 2 };
+
+/* One kernel k (Section 2.1: kernels with their growth mappings).
+ *   src_channel, dst_channel: the channel convolved and the channel updated.
+ *   radius R >= 1 pixels; 2R+1 <= min(H, W).
+ *   form LENIA_KERNEL_SHELLS: K(d) = beta[floor(B rho)] core(B rho mod 1),
+ *     rho = |d|_2 / R < 1, B = n_shells in 1..4, core(q) = exp(4 - 1/(q(1-q)))
+ *     (the original Lenia kernel shell; Section 1.2 cites it).
+ *   form LENIA_KERNEL_BUMPS: K(d) = sum_{i=0,1} b_i exp(-(rho - r_i)^2 / (2 w_i^2))
+ *     for rho < 1, bump = {r1, w1, b1, r2, w2, b2} (Section 2.1 and 2.4).
+ *   h, mu, sigma: global growth genes (used for every gene not localized). */
+typedef struct {
+    int32_t src_channel;
+    int32_t dst_channel;
+    int32_t radius;
+    int32_t form;
+    int32_t n_shells;
+    double beta[4];
+    double bump[6];
+    float h, mu, sigma;
+} lenia_kernel_desc;
+
+/* World configuration.
+ *   height H, width W: W % 4 == 0, H, W >= 8.  The FFT path needs H and W
+ *     powers of two in [64, 4096].
+ *   n_channels C in 1..8, n_kernels K in 1..64.
+ *   dt: time step multiplying the growth sum (the paper's update is dt = 1).
+ *   growth_form: LENIA_GROWTH_SIGNED, h (2g - 1); LENIA_GROWTH_PAPER, h g
+ *     (Section 2.4), g = exp(-(u - m)^2 / (2 s^2)) and g = 0 where s <= 0.
+ *   localized: OR of LENIA_LOC_* - the genes read per site from P.
+ *   maintain_genes: 1 runs diffusion (Section 2.3) and the alpha mask
+ *     (Section 2.2); needs localized != 0.
+ *   eps_u: alpha threshold on the growth h g (or on U when alpha_on = 1);
+ *   eps_p: gene threshold of Delta_same / Delta_all (strict '>').
+ *   r_diff: radius of the diffusion disk |d|_2 <= r_diff, 0..8.
+ *   conv_path: LENIA_CONV_* (AUTO picks FFT for power-of-two worlds).
+ *   max_rollout_steps, ckpt_every: reserved for the adjoint (set 0). */
+typedef struct {
+    int32_t height, width, n_channels, n_kernels;
+    float dt;
+    int32_t growth_form;
+    int32_t localized;
+    int32_t maintain_genes;
+    float eps_u, eps_p;
+    int32_t r_diff;
+    int32_t alpha_on;
+    int32_t conv_path;
+    int32_t max_rollout_steps, ckpt_every;
+} lenia_config;
+
+/* Validate cfg and kernels[0..n_kernels), build the normalised kernels in
+ * FP64 (Algorithm 1 pre-calculation; Algorithm 2 "pre-calculate kernel"),
+ * their FP32 spectra for the FFT path, and all scratch.  Work for the spectra
+ * runs on `stream` and is complete when lenia_init returns.  On success *out
+ * holds a new context; on failure *out is NULL. */
+LENIA_API lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernels,
+                        void* stream, lenia_ctx** out);
+
+/* One step (Algorithm 2, diffuse .. update): reads A_in [C][H][W] and, when
+ * localized != 0, P_in [n_p][K][H][W]; writes A_out and P_out (P_out may be
+ * NULL only when localized == 0).  stats_out (nullable, device, C*3 floats)
+ * receives mass, circular-mean centre y and centre x of each channel of
+ * A_out.  In and out buffers must not overlap (EINVAL). */
+LENIA_API lenia_status lenia_step(lenia_ctx* ctx, const float* A_in, const float* P_in,
+                        float* A_out, float* P_out, float* stats_out, void* stream);
+
+/* n_steps steps in place on A (and P): the state ping-pongs through
+ * library-owned buffers and ends in the caller's.  stats_out (nullable,
+ * device) receives n_steps * C * 3 floats, step s at offset s*C*3. */
+LENIA_API lenia_status lenia_rollout(lenia_ctx* ctx, float* A, float* P, int32_t n_steps,
+                           float* stats_out, void* stream);
+
+/* Adjoint of a rollout (reserved): returns LENIA_ENOTSUP in this build. */
+LENIA_API lenia_status lenia_backward(lenia_ctx* ctx, const float* A0, const float* P0, int32_t n_steps,
+                            const float* gA_T, float* gA0, float* g_genes, void* stream);
+
+/* Mass, circular-mean centre y, centre x of each channel of A: out is a
+ * device array of C*3 floats.  Sums run in a fixed order (deterministic). */
+LENIA_API lenia_status lenia_stats(lenia_ctx* ctx, const float* A, float* out, void* stream);
+
+/* Potentials U_k = K~_k * A_src(k) for every kernel (Algorithm 2, convolve
+ * and normalised sum; note after Algorithm 2 for the FFT route) into U_out
+ * [K][H][W], through the context's convolution path. */
+LENIA_API lenia_status lenia_potentials(lenia_ctx* ctx, const float* A_in, float* U_out, void* stream);
+
+/* The step after the convolution: diffusion, growth, alpha mask, masking and
+ * clipped update (Sections 2.2-2.4, Algorithm 2) from given potentials
+ * U_in [K][H][W].  alpha_out (nullable) receives one byte per site. */
+LENIA_API lenia_status lenia_update_from_potentials(lenia_ctx* ctx, const float* A_in, const float* P_in,
+                                          const float* U_in, float* A_out, float* P_out,
+                                          uint8_t* alpha_out, void* stream);
+
+/* lenia_step with HOST buffers: copies A_in/P_in host->device into library
+ * buffers, steps, and copies A_out/P_out (and stats_out, C*3 floats, nullable)
+ * back; returns after the stream has finished.  Page-locked host memory
+ * makes the copies fast; pageable memory works. */
+LENIA_API lenia_status lenia_step_host(lenia_ctx* ctx, const float* A_in, const float* P_in,
+                             float* A_out, float* P_out, float* stats_out, void* stream);
+
+/* Per-launch timing for benchmarks.  lenia_profile_start makes the library
+ * record a CUDA event pair on the launching stream around each of its next
+ * max_launches kernel launches (event creation only; no device memory).
+ * lenia_profile_stop waits for those events and fills total_ms[kind] (summed
+ * milliseconds) and counts[kind] for the launch kinds 0..LENIA_PROFILE_KINDS-1
+ * (names from lenia_profile_kind_name), then turns recording off. */
+#define LENIA_PROFILE_KINDS 7
+LENIA_API lenia_status lenia_profile_start(lenia_ctx* ctx, int32_t max_launches);
+LENIA_API lenia_status lenia_profile_stop(lenia_ctx* ctx, float* total_ms, int32_t* counts);
+LENIA_API const char* lenia_profile_kind_name(int32_t kind);
+
+/* The normalised FP64 kernel k, (2R+1)^2 values row-major over dy, dx in
+ * -R..R, copied to the HOST buffer out. */
+LENIA_API lenia_status lenia_kernel_weights(const lenia_ctx* ctx, int32_t k, double* out);
+
+/* Convolution path in use: LENIA_CONV_FFT or LENIA_CONV_DIRECT. */
+LENIA_API int32_t lenia_conv_path(const lenia_ctx* ctx);
+
+/* Number of CUDA kernel launches one lenia_step enqueues (with stats). */
+LENIA_API int32_t lenia_launches_per_step(const lenia_ctx* ctx);
+
+LENIA_API const char* lenia_last_error(const lenia_ctx* ctx);
+LENIA_API const char* lenia_status_string(lenia_status s);
+LENIA_API void lenia_destroy(lenia_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LENIA_H */

@@ -70,6 +70,14 @@ def _load():
                                         ctypes.POINTER(ctypes.c_long), dp, dp, dp, dp, dp,
                                         ctypes.POINTER(ctypes.c_ubyte)]
             lib.oracle_step.restype = ctypes.c_int
+            lib.oracle_update.argtypes = [ctypes.POINTER(OracleCfg), ip, dp, dp, dp, dp, dp, dp, dp, dp,
+                                          ctypes.POINTER(ctypes.c_ubyte)]
+            lib.oracle_update.restype = ctypes.c_int
+            fp = ctypes.POINTER(ctypes.c_float)
+            lib.oracle_step_sites.argtypes = [ctypes.POINTER(OracleCfg), ip, ip, ip, dp, dp, dp, dp,
+                                              ctypes.POINTER(ctypes.c_long), fp, fp, ctypes.c_long,
+                                              ip, ip, dp, dp, dp, dp, ctypes.POINTER(ctypes.c_ubyte)]
+            lib.oracle_step_sites.restype = ctypes.c_int
             lib.oracle_stats.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -136,55 +144,123 @@ def world_kernels(world) -> list:
     return [kernel(k.radius, k.form, k.beta, k.bump) for k in world.kernels]
 
 
+class _Args:
+    """ctypes views of a world's configuration and kernels."""
+
+    def __init__(self, world, kernels=None):
+        K = world.n_kernels
+        if K > 64:
+            raise ValueError("oracle supports at most 64 kernels")
+        ks = world_kernels(world) if kernels is None else kernels
+        self.off = np.zeros(K, np.int64)
+        o = 0
+        for i, k in enumerate(ks):
+            self.off[i] = o
+            o += k.size
+        self.Kw = _f64(np.concatenate([k.ravel() for k in ks]))
+        self.cfg = OracleCfg(world.height, world.width, world.n_channels, K, float(world.dt),
+                             world.growth_form, world.localized, world.maintain_genes, world.r_diff,
+                             world.alpha_on, float(world.eps_u), float(world.eps_p))
+        ia = lambda v: np.ascontiguousarray(np.asarray(v, np.int32))
+        self.src = ia([k.src for k in world.kernels])
+        self.dst = ia([k.dst for k in world.kernels])
+        self.rad = ia([k.radius for k in world.kernels])
+        self.h = _f64([k.h for k in world.kernels])
+        self.mu = _f64([k.mu for k in world.kernels])
+        self.sg = _f64([k.sigma for k in world.kernels])
+
+    def ip(self, a):
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+    def kernel_args(self):
+        return (ctypes.byref(self.cfg), self.ip(self.src), self.ip(self.dst), self.ip(self.rad),
+                _dp(self.h), _dp(self.mu), _dp(self.sg), _dp(self.Kw),
+                self.off.ctypes.data_as(ctypes.POINTER(ctypes.c_long)))
+
+
+_NULL_D = ctypes.POINTER(ctypes.c_double)()
+_NULL_B = ctypes.POINTER(ctypes.c_ubyte)()
+
+
+def _bp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)) if a is not None else _NULL_B
+
+
+def _opt(a):
+    return _dp(a) if a is not None else _NULL_D
+
+
 def step(world, A=None, P=None, kernels=None, return_u=False, return_alpha=False):
     """One step of ``world`` (an inputs.World) from state (A, P), FP64.
 
     Returns (A_out, P_out) and, on request, U[K, H, W] and alpha[H, W]."""
     lib = _load()
+    args = _Args(world, kernels)
     A = _f64(world.A if A is None else A)
     P = world.P if P is None else P
     K = world.n_kernels
-    if K > 64:
-        raise ValueError("oracle supports at most 64 kernels")
     C, H, W = A.shape
-    ks = world_kernels(world) if kernels is None else kernels
-    off = np.zeros(K, np.int64)
-    o = 0
-    for i, k in enumerate(ks):
-        off[i] = o
-        o += k.size
-    Kw = _f64(np.concatenate([k.ravel() for k in ks]))
-    cfg = OracleCfg(H, W, C, K, float(world.dt), world.growth_form, world.localized,
-                    world.maintain_genes, world.r_diff, world.alpha_on,
-                    float(world.eps_u), float(world.eps_p))
-    ia = lambda v: np.ascontiguousarray(np.asarray(v, np.int32))
-    src = ia([k.src for k in world.kernels])
-    dst = ia([k.dst for k in world.kernels])
-    rad = ia([k.radius for k in world.kernels])
-    h = _f64([k.h for k in world.kernels])
-    mu = _f64([k.mu for k in world.kernels])
-    sg = _f64([k.sigma for k in world.kernels])
     A_out = np.zeros_like(A)
-    n_p = world.n_planes
-    Pp = _f64(P) if (n_p and P is not None) else None
+    Pp = _f64(P) if (world.n_planes and P is not None) else None
     P_out = np.zeros_like(Pp) if Pp is not None else None
     U = np.zeros((K, H, W), np.float64) if return_u else None
     alpha = np.zeros((H, W), np.uint8) if return_alpha else None
-    ipp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-    null = ctypes.POINTER(ctypes.c_double)()
-    lib.oracle_step(ctypes.byref(cfg), ipp(src), ipp(dst), ipp(rad), _dp(h), _dp(mu), _dp(sg),
-                    _dp(Kw), off.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
-                    _dp(A), _dp(Pp) if Pp is not None else null, _dp(A_out),
-                    _dp(P_out) if P_out is not None else null,
-                    _dp(U) if U is not None else null,
-                    alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)) if alpha is not None
-                    else ctypes.POINTER(ctypes.c_ubyte)())
+    rc = lib.oracle_step(*args.kernel_args(), _dp(A), _opt(Pp), _dp(A_out), _opt(P_out), _opt(U),
+                         _bp(alpha))
+    if rc != 0:
+        raise RuntimeError("oracle_step failed")
     out = [A_out, P_out]
     if return_u:
         out.append(U)
     if return_alpha:
         out.append(alpha)
     return tuple(out)
+
+
+def update(world, A, P, U, return_alpha=False):
+    """The step after the convolution from given potentials U[K, H, W]."""
+    lib = _load()
+    args = _Args(world)
+    A = _f64(A)
+    U = _f64(U)
+    Pp = _f64(P) if (world.n_planes and P is not None) else None
+    A_out = np.zeros_like(A)
+    P_out = np.zeros_like(Pp) if Pp is not None else None
+    alpha = np.zeros(A.shape[1:], np.uint8)
+    rc = lib.oracle_update(ctypes.byref(args.cfg), args.ip(args.dst), _dp(args.h), _dp(args.mu),
+                           _dp(args.sg), _dp(A), _opt(Pp), _dp(U), _dp(A_out), _opt(P_out), _bp(alpha))
+    if rc != 0:
+        raise RuntimeError("oracle_update failed")
+    return (A_out, P_out, alpha) if return_alpha else (A_out, P_out)
+
+
+def step_sites(world, ys, xs, A=None, P=None):
+    """The step at listed sites only (direct sums), for worlds too large for a
+    full oracle step.  A and P are float32 arrays of the world's shape.
+    Returns dict with A [C, n], P [n_p K, n] (or None), U [K, n], the diffused
+    unmasked genes Ph [n_p K, n] (or None) and alpha [n]."""
+    lib = _load()
+    args = _Args(world)
+    A = np.ascontiguousarray(world.A if A is None else A, dtype=np.float32)
+    P = world.P if P is None else P
+    ys = np.ascontiguousarray(ys, np.int32)
+    xs = np.ascontiguousarray(xs, np.int32)
+    n = len(ys)
+    C, K = world.n_channels, world.n_kernels
+    npk = world.n_planes * K
+    Pf = np.ascontiguousarray(P, dtype=np.float32) if npk else None
+    A_out = np.zeros((C, n))
+    P_out = np.zeros((npk, n)) if npk else None
+    U = np.zeros((K, n))
+    Ph = np.zeros((npk, n)) if npk else None
+    alpha = np.zeros(n, np.uint8)
+    fptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if a is not None \
+        else ctypes.POINTER(ctypes.c_float)()
+    rc = lib.oracle_step_sites(*args.kernel_args(), fptr(A), fptr(Pf), n, args.ip(ys), args.ip(xs),
+                               _dp(A_out), _opt(P_out), _dp(U), _opt(Ph), _bp(alpha))
+    if rc != 0:
+        raise RuntimeError("oracle_step_sites failed")
+    return {"A": A_out, "P": P_out, "U": U, "Ph": Ph, "alpha": alpha}
 
 
 def rollout(world, n_steps: int, A=None, P=None):

@@ -173,93 +173,199 @@ typedef struct {
     double eps_u, eps_p;
 } oracle_cfg;
 
-/* One full step.
- *  A[C][H][W] in, A_out out; P[n_p][K][H][W] in (NULL when no gene maps),
- *  P_out out (NULL allowed); U_out[K][H][W], alpha_out[H][W] optional.
- *  Kernels: src[k], dst[k], R[k], h/mu/sigma[k] global genes; Kw holds the
- *  normalised kernels back to back, kernel k at offset kw_off[k].
- * Returns 0. */
-int oracle_step(const oracle_cfg* cfg, const int* src, const int* dst, const int* R,
-                const double* h, const double* mu, const double* sigma,
-                const double* Kw, const long* kw_off,
-                const double* A, const double* P, double* A_out, double* P_out,
-                double* U_out, unsigned char* alpha_out)
+typedef struct {
+    int n_p, p_mu, p_sigma, p_h;
+} plane_map;
+
+static plane_map planes_of(int loc)
+{
+    plane_map m;
+    m.n_p = ((loc & LOC_MU) != 0) + ((loc & LOC_SIGMA) != 0) + ((loc & LOC_H) != 0);
+    m.p_mu = (loc & LOC_MU) ? 0 : -1;
+    m.p_sigma = (loc & LOC_SIGMA) ? ((loc & LOC_MU) ? 1 : 0) : -1;
+    m.p_h = (loc & LOC_H) ? m.n_p - 1 : -1;
+    return m;
+}
+
+/* Growth, alpha mask, genospace masking and clipped update at one site.
+ *  u[k]: potentials; ph[pk]: the site's genes after diffusion (pk = p*K + k);
+ *  a_in[c]: the site's state.  Writes a_out[c], p_out[pk] and returns alpha. */
+static int site_update(const oracle_cfg* cfg, plane_map pm, const int* dst, const double* h,
+                       const double* mu, const double* sigma, const double* u, const double* ph,
+                       const double* a_in, double* a_out, double* p_out)
+{
+    const int K = cfg->K;
+    double g[64];
+    double hk[64];
+    int alpha = 1;
+    for (int k = 0; k < K; k++) {
+        double m = pm.p_mu >= 0 ? ph[pm.p_mu * K + k] : mu[k];
+        double s = pm.p_sigma >= 0 ? ph[pm.p_sigma * K + k] : sigma[k];
+        hk[k] = pm.p_h >= 0 ? ph[pm.p_h * K + k] : h[k];
+        g[k] = growth_bump(u[k], m, s);
+        if (cfg->maintain) {
+            /* Section 2.2: alpha = Delta_all(U) AND Delta_all(P) (R5). */
+            double t = cfg->alpha_on ? u[k] : hk[k] * g[k];
+            if (!(t > cfg->eps_u)) alpha = 0;
+        }
+    }
+    if (cfg->maintain)
+        for (int pk = 0; pk < pm.n_p * K; pk++)
+            if (!(ph[pk] > cfg->eps_p)) alpha = 0;
+
+    /* Mask the genospace: P -> P (.) alpha. */
+    if (p_out)
+        for (int pk = 0; pk < pm.n_p * K; pk++)
+            p_out[pk] = alpha ? ph[pk] : 0.0;
+
+    /* Growth mapping and clipped update with the masked genes (R1, R2, R9):
+     * A_i -> [A_i + dt sum_{k: dst(k) = i} G_k(U_k)]_0^1. */
+    for (int c = 0; c < cfg->C; c++) {
+        double acc = 0.0;
+        for (int k = 0; k < K; k++) {
+            if (dst[k] != c) continue;
+            double gm = alpha ? g[k] : 0.0;
+            double hm = (pm.p_h >= 0 && !alpha) ? 0.0 : hk[k];
+            double G = cfg->growth_form == 0 ? hm * (2.0 * gm - 1.0) : hm * gm;
+            acc += G;
+        }
+        double a = a_in[c] + cfg->dt * acc;
+        if (a < 0.0) a = 0.0;
+        if (a > 1.0) a = 1.0;
+        a_out[c] = a;
+    }
+    return alpha;
+}
+
+/* The step after the convolution, on the whole grid, from given potentials
+ * U[K][H][W]: diffusion (or plain genes), then site_update everywhere. */
+int oracle_update(const oracle_cfg* cfg, const int* dst, const double* h, const double* mu,
+                  const double* sigma, const double* A, const double* P, const double* U,
+                  double* A_out, double* P_out, unsigned char* alpha_out)
 {
     const int H = cfg->H, W = cfg->W, C = cfg->C, K = cfg->K;
     const size_t N = (size_t)H * W;
-    const int loc = cfg->localized;
-    const int n_p = ((loc & LOC_MU) != 0) + ((loc & LOC_SIGMA) != 0) + ((loc & LOC_H) != 0);
-    const int p_mu = (loc & LOC_MU) ? 0 : -1;
-    const int p_sigma = (loc & LOC_SIGMA) ? ((loc & LOC_MU) ? 1 : 0) : -1;
-    const int p_h = (loc & LOC_H) ? n_p - 1 : -1;
+    const plane_map pm = planes_of(cfg->localized);
+    if (K > 64 || C > 64) return -1;
 
-    /* Algorithm 2: diffuse the genospace (before the convolution). */
+    /* Algorithm 2: diffuse the genospace. */
     double* Ph = NULL;
-    if (n_p > 0) {
-        Ph = (double*)malloc(sizeof(double) * (size_t)n_p * K * N);
-        for (int pk = 0; pk < n_p * K; pk++) {
+    if (pm.n_p > 0) {
+        Ph = (double*)malloc(sizeof(double) * (size_t)pm.n_p * K * N);
+        for (int pk = 0; pk < pm.n_p * K; pk++) {
             if (cfg->maintain)
                 oracle_diffuse(H, W, P + (size_t)pk * N, cfg->r_diff, cfg->eps_p, Ph + (size_t)pk * N);
             else
                 memcpy(Ph + (size_t)pk * N, P + (size_t)pk * N, sizeof(double) * N);
         }
     }
+    #pragma omp parallel for schedule(static)
+    for (long i = 0; i < (long)N; i++) {
+        double u[64], ph[192], a_in[64], a_out[64], p_out[192];
+        for (int k = 0; k < K; k++) u[k] = U[(size_t)k * N + i];
+        for (int pk = 0; pk < pm.n_p * K; pk++) ph[pk] = Ph[(size_t)pk * N + i];
+        for (int c = 0; c < C; c++) a_in[c] = A[(size_t)c * N + i];
+        int alpha = site_update(cfg, pm, dst, h, mu, sigma, u, ph, a_in, a_out, p_out);
+        for (int c = 0; c < C; c++) A_out[(size_t)c * N + i] = a_out[c];
+        if (P_out)
+            for (int pk = 0; pk < pm.n_p * K; pk++) P_out[(size_t)pk * N + i] = p_out[pk];
+        if (alpha_out) alpha_out[i] = (unsigned char)alpha;
+    }
+    free(Ph);
+    return 0;
+}
 
-    /* Algorithm 2: convolve the phenospace with every kernel; the weighted
-     * sum over rings collapses to one normalised kernel when the kernel genes
-     * are global. */
+/* One full step.
+ *  A[C][H][W] in, A_out out; P[n_p][K][H][W] in (NULL when no gene maps),
+ *  P_out out (NULL allowed); U_out[K][H][W], alpha_out[H][W] optional.
+ *  Kernels: src[k], dst[k], R[k], h/mu/sigma[k] global genes; Kw holds the
+ *  normalised kernels back to back, kernel k at offset kw_off[k].
+ * Order of Algorithm 2: diffuse, convolve (the weighted ring sum collapses
+ * to one normalised kernel when kernel genes are global), alpha, mask,
+ * update.  Returns 0. */
+int oracle_step(const oracle_cfg* cfg, const int* src, const int* dst, const int* R,
+                const double* h, const double* mu, const double* sigma,
+                const double* Kw, const long* kw_off,
+                const double* A, const double* P, double* A_out, double* P_out,
+                double* U_out, unsigned char* alpha_out)
+{
+    const int H = cfg->H, W = cfg->W, K = cfg->K;
+    const size_t N = (size_t)H * W;
     double* U = (double*)malloc(sizeof(double) * (size_t)K * N);
     for (int k = 0; k < K; k++)
         oracle_potential(H, W, A + (size_t)src[k] * N, R[k], Kw + kw_off[k], U + (size_t)k * N, 0);
-
-    #pragma omp parallel for schedule(static)
-    for (long i = 0; i < (long)N; i++) {
-        double g[64];
-        double hk[64];
-        int alpha = 1;
-        for (int k = 0; k < K; k++) {
-            double m = p_mu >= 0 ? Ph[((size_t)p_mu * K + k) * N + i] : mu[k];
-            double s = p_sigma >= 0 ? Ph[((size_t)p_sigma * K + k) * N + i] : sigma[k];
-            hk[k] = p_h >= 0 ? Ph[((size_t)p_h * K + k) * N + i] : h[k];
-            double u = U[(size_t)k * N + i];
-            g[k] = growth_bump(u, m, s);
-            if (cfg->maintain) {
-                /* Section 2.2: alpha = Delta_all(U) AND Delta_all(P) (R5). */
-                double t = cfg->alpha_on ? u : hk[k] * g[k];
-                if (!(t > cfg->eps_u)) alpha = 0;
-            }
-        }
-        if (cfg->maintain)
-            for (int pk = 0; pk < n_p * K; pk++)
-                if (!(Ph[(size_t)pk * N + i] > cfg->eps_p)) alpha = 0;
-        if (!cfg->maintain) alpha = 1;
-        if (alpha_out) alpha_out[i] = (unsigned char)alpha;
-
-        /* Mask the genospace: P -> P (.) alpha. */
-        if (P_out)
-            for (int pk = 0; pk < n_p * K; pk++)
-                P_out[(size_t)pk * N + i] = alpha ? Ph[(size_t)pk * N + i] : 0.0;
-
-        /* Growth mapping and clipped update with the masked genes (R1, R2,
-         * R9): A_i -> [A_i + dt sum_{k: dst(k) = i} G_k(U_k)]_0^1. */
-        for (int c = 0; c < C; c++) {
-            double acc = 0.0;
-            for (int k = 0; k < K; k++) {
-                if (dst[k] != c) continue;
-                double gm = alpha ? g[k] : 0.0;
-                double hm = (p_h >= 0 && !alpha) ? 0.0 : hk[k];
-                double G = cfg->growth_form == 0 ? hm * (2.0 * gm - 1.0) : hm * gm;
-                acc += G;
-            }
-            double a = A[(size_t)c * N + i] + cfg->dt * acc;
-            if (a < 0.0) a = 0.0;
-            if (a > 1.0) a = 1.0;
-            A_out[(size_t)c * N + i] = a;
-        }
-    }
+    int rc = oracle_update(cfg, dst, h, mu, sigma, A, P, U, A_out, P_out, alpha_out);
     if (U_out) memcpy(U_out, U, sizeof(double) * (size_t)K * N);
     free(U);
-    free(Ph);
+    return rc;
+}
+
+/* The same step evaluated only at n listed sites (ys[i], xs[i]): the
+ * potential by its direct sum, diffusion of each gene plane over the disk,
+ * then site_update.  Outputs are [C][n], [n_p K][n], [K][n], the diffused
+ * unmasked genes [n_p K][n] and alpha [n]. */
+int oracle_step_sites(const oracle_cfg* cfg, const int* src, const int* dst, const int* R,
+                      const double* h, const double* mu, const double* sigma,
+                      const double* Kw, const long* kw_off, const float* A, const float* P,
+                      long n, const int* ys, const int* xs, double* A_out, double* P_out,
+                      double* U_out, double* Ph_out, unsigned char* alpha_out)
+{
+    const int H = cfg->H, W = cfg->W, C = cfg->C, K = cfg->K;
+    const size_t N = (size_t)H * W;
+    const plane_map pm = planes_of(cfg->localized);
+    const int rd = cfg->r_diff;
+    if (K > 64 || C > 64) return -1;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (long i = 0; i < n; i++) {
+        const int y = ys[i], x = xs[i];
+        double u[64], ph[192], a_in[64], a_out[64], p_out[192];
+        for (int k = 0; k < K; k++) {
+            const int r = R[k], nn = 2 * r + 1;
+            const double* Kk = Kw + kw_off[k];
+            const float* Ac = A + (size_t)src[k] * N;
+            double s = 0.0;
+            for (int dy = -r; dy <= r; dy++)
+                for (int dx = -r; dx <= r; dx++) {
+                    double kv = Kk[(dy + r) * nn + (dx + r)];
+                    if (kv == 0.0) continue;
+                    s += kv * (double)Ac[(size_t)wrap(y - dy, H) * W + wrap(x - dx, W)];
+                }
+            u[k] = s;
+        }
+        for (int pk = 0; pk < pm.n_p * K; pk++) {
+            const float* pl = P + (size_t)pk * N;
+            if (!cfg->maintain) {
+                ph[pk] = (double)pl[(size_t)y * W + x];
+                continue;
+            }
+            double s = 0.0;
+            int cnt = 0;
+            for (int dy = -rd; dy <= rd; dy++)
+                for (int dx = -rd; dx <= rd; dx++) {
+                    if (dy * dy + dx * dx > rd * rd) continue;
+                    double v = (double)pl[(size_t)wrap(y + dy, H) * W + wrap(x + dx, W)];
+                    s += v;
+                    if (v > cfg->eps_p) cnt++;
+                }
+            double r = 0.0;
+            if (cnt > 0) {
+                r = s / (double)cnt;
+                if (r < 0.0) r = 0.0;
+                if (r > 1.0) r = 1.0;
+            }
+            ph[pk] = r;
+        }
+        for (int c = 0; c < C; c++) a_in[c] = (double)A[(size_t)c * N + (size_t)y * W + x];
+        int alpha = site_update(cfg, pm, dst, h, mu, sigma, u, ph, a_in, a_out, p_out);
+        for (int c = 0; c < C; c++) A_out[(size_t)c * n + i] = a_out[c];
+        if (P_out)
+            for (int pk = 0; pk < pm.n_p * K; pk++) P_out[(size_t)pk * n + i] = p_out[pk];
+        if (U_out)
+            for (int k = 0; k < K; k++) U_out[(size_t)k * n + i] = u[k];
+        if (Ph_out)
+            for (int pk = 0; pk < pm.n_p * K; pk++) Ph_out[(size_t)pk * n + i] = ph[pk];
+        if (alpha_out) alpha_out[i] = (unsigned char)alpha;
+    }
     return 0;
 }
 

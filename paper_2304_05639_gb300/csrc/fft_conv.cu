@@ -1,0 +1,279 @@
+// Spectral convolution U_k = K~_k * A_src(k) for all kernels (convolution
+// theorem, note after Algorithm 2 of arXiv 2304.05639; cached kernel
+// spectra, Section 2.4).
+//
+// Three passes over the world, each a set of shared-memory FFTs:
+//   rows_r2c  : real row FFT of every channel row (length-W real signal as a
+//               length-W/2 complex FFT plus the standard even/odd split).
+//               Output row: W/2 complex values; element 0 packs the two real
+//               values X[0] (DC) and X[W/2] (Nyquist) as (re, im).
+//   cols_conv : for a tile of TC spectrum columns of one channel, forward
+//               column FFT, then for each kernel reading that channel the
+//               product with the real kernel spectrum and the inverse column
+//               FFT, written per kernel.  Column 0 holds the packed DC and
+//               Nyquist columns (both real along y), which are separated,
+//               multiplied by their own spectra and re-packed in one step.
+//   rows_c2r  : inverse real row FFT of every kernel row -> U_k.
+// Forward and inverse transforms are unnormalised; 1/(H W) is folded into
+// the stored kernel spectra.
+#include "fft_core.cuh"
+#include "lenia_internal.cuh"
+
+namespace lenia {
+
+// ---------------------------------------------------------------- rows R2C
+template <int M, int T, int NB>
+__global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
+{
+    extern __shared__ float2 sm[];
+    constexpr int SZ = swz_size(M);
+    const int c = blockIdx.y;
+    const int y0 = blockIdx.x * NB;
+    const int W = 2 * M;
+    const float2* src = reinterpret_cast<const float2*>(p.A + ((size_t)c * p.H + y0) * W);
+    auto ld_g = [&](int b, int i) { return __ldg(&src[(size_t)b * M + i]); };
+    auto sld = [&](int b, int i) { return sm[b * SZ + swz(i)]; };
+    auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz(i)] = v; };
+    fft_run<M, NB, T, false, false>(p.tw_M, ld_g, sld, sst, sst);
+
+    // X[k] = E[k] + w_W^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i
+    for (int u = threadIdx.x; u < NB * (M / 2 + 1); u += T) {
+        const int b = u / (M / 2 + 1);
+        const int k = u % (M / 2 + 1);
+        float2* out = p.Ahat + ((size_t)c * p.H + y0 + b) * M;
+        if (k == 0) {
+            float2 z = sm[b * SZ + swz(0)];
+            out[0] = make_float2(z.x + z.y, z.x - z.y);
+            continue;
+        }
+        const float2 zk = sm[b * SZ + swz(k)];
+        const float2 zm = sm[b * SZ + swz(M - k)];
+        {
+            float2 e = cscale(cadd(zk, cconj(zm)), 0.5f);
+            float2 d = cscale(csub(zk, cconj(zm)), 0.5f);
+            float2 o = make_float2(d.y, -d.x);               // d / i
+            out[k] = cadd(e, cmul(__ldg(&p.tw_W[k]), o));
+        }
+        if (k != M - k) {
+            float2 e = cscale(cadd(zm, cconj(zk)), 0.5f);
+            float2 d = cscale(csub(zm, cconj(zk)), 0.5f);
+            float2 o = make_float2(d.y, -d.x);
+            out[M - k] = cadd(e, cmul(__ldg(&p.tw_W[M - k]), o));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- rows C2R
+template <int M, int T, int NB>
+__global__ void __launch_bounds__(T) k_rows_c2r(FftParams p)
+{
+    extern __shared__ float2 sm[];
+    constexpr int SZ = swz_size(M);
+    const int k = blockIdx.y;
+    const int y0 = blockIdx.x * NB;
+    const int W = 2 * M;
+    const float2* in = p.Uhat + ((size_t)k * p.H + y0) * M;
+
+    // Z'[k] = (X[k] + conj X[M-k]) + i w_W^{-k} (X[k] - conj X[M-k])  (= 2 Z[k])
+    for (int u = threadIdx.x; u < NB * (M / 2 + 1); u += T) {
+        const int b = u / (M / 2 + 1);
+        const int q = u % (M / 2 + 1);
+        const float2* row = in + (size_t)b * M;
+        if (q == 0) {
+            float2 x = __ldg(&row[0]);                       // (DC, Nyquist)
+            sm[b * SZ + swz(0)] = make_float2(x.x + x.y, x.x - x.y);
+            continue;
+        }
+        const float2 xk = __ldg(&row[q]);
+        const float2 xm = __ldg(&row[M - q]);
+        {
+            float2 s = cadd(xk, cconj(xm));
+            float2 d = cmulc(csub(xk, cconj(xm)), __ldg(&p.tw_W[q]));
+            sm[b * SZ + swz(q)] = make_float2(s.x - d.y, s.y + d.x);   // s + i d
+        }
+        if (q != M - q) {
+            float2 s = cadd(xm, cconj(xk));
+            float2 d = cmulc(csub(xm, cconj(xk)), __ldg(&p.tw_W[M - q]));
+            sm[b * SZ + swz(M - q)] = make_float2(s.x - d.y, s.y + d.x);
+        }
+    }
+    __syncthreads();
+    float2* out = reinterpret_cast<float2*>(p.U + ((size_t)k * p.H + y0) * W);
+    auto sld = [&](int b, int i) { return sm[b * SZ + swz(i)]; };
+    auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz(i)] = v; };
+    auto st_g = [&](int b, int i, float2 v) { out[(size_t)b * M + i] = v; };
+    fft_run<M, NB, T, true, false>(p.tw_M, sld, sld, sst, st_g);
+}
+
+// ------------------------------------------------------- columns: fwd, x K^, inv
+template <int H, int TC, int T>
+__global__ void __launch_bounds__(T) k_cols_conv(FftParams p)
+{
+    extern __shared__ float2 sm[];
+    constexpr int SZ = swz_size(H * TC);
+    float2* F = sm;
+    float2* Wk = sm + SZ;
+    const int c = blockIdx.y;
+    const int kx0 = blockIdx.x * TC;
+    const int M = p.W / 2;
+    const int HS = H / 2 + 1;
+
+    const float2* src = p.Ahat + (size_t)c * H * M + kx0;
+    auto ld_g = [&](int b, int i) { return __ldg(&src[(size_t)i * M + b]); };
+    auto sldF = [&](int b, int i) { return F[swz(i * TC + b)]; };
+    auto sstF = [&](int b, int i, float2 v) { F[swz(i * TC + b)] = v; };
+    fft_run<H, TC, T, false, true>(p.tw_H, ld_g, sldF, sstF, sstF);
+
+    const int nk = p.kcount[c];
+    for (int t = 0; t < nk; t++) {
+        const int k = p.klist[c][t];
+        const float* Sk = p.S + (size_t)k * (M + 1) * HS;
+        auto ld_mul = [&](int b, int i) {
+            const int kx = kx0 + b;
+            const int ky = i;
+            const int kyr = ky <= H / 2 ? ky : H - ky;
+            const float2 f = F[swz(i * TC + b)];
+            if (kx == 0) {
+                // packed (DC, Nyquist) column: out = f a + conj(f(-ky)) b
+                const float s0 = __ldg(&Sk[kyr]);
+                const float sn = __ldg(&Sk[(size_t)M * HS + kyr]);
+                const float2 fm = cconj(F[swz(((H - ky) & (H - 1)) * TC + b)]);
+                const float a = 0.5f * (s0 + sn), bb = 0.5f * (s0 - sn);
+                return make_float2(f.x * a + fm.x * bb, f.y * a + fm.y * bb);
+            }
+            const float s = __ldg(&Sk[(size_t)kx * HS + kyr]);
+            return cscale(f, s);
+        };
+        float2* dst = p.Uhat + (size_t)k * H * M + kx0;
+        auto sldW = [&](int b, int i) { return Wk[swz(i * TC + b)]; };
+        auto sstW = [&](int b, int i, float2 v) { Wk[swz(i * TC + b)] = v; };
+        auto st_g = [&](int b, int i, float2 v) { dst[(size_t)i * M + b] = v; };
+        fft_run<H, TC, T, true, true>(p.tw_H, ld_mul, sldW, sstW, st_g);
+    }
+}
+
+// ------------------------------------------------------------ dispatch
+template <int M>
+static cudaError_t rows_launch(const FftParams& p, cudaStream_t s, bool inverse)
+{
+    // 4096 complex values per block (NB rows), one radix-16 butterfly per thread
+    constexpr int NB = (4096 / M) < 64 ? (4096 / M) : 64;
+    constexpr int T = (NB * M / 16) < 256 ? (NB * M / 16) : 256;
+    const size_t smem = (size_t)NB * swz_size(M) * sizeof(float2);
+    if (p.H % NB) return cudaErrorInvalidValue;
+    if (!inverse) {
+        auto kern = k_rows_r2c<M, T, NB>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<dim3(p.H / NB, p.C), T, smem, s>>>(p);
+    } else {
+        auto kern = k_rows_c2r<M, T, NB>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<dim3(p.H / NB, p.K), T, smem, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+template <int H>
+static cudaError_t cols_launch(const FftParams& p, cudaStream_t s)
+{
+    constexpr int TC = H >= 4096 ? 2 : 4;
+    constexpr int T = (H * TC / 16) >= 512 ? 512 : (H * TC / 16 >= 128 ? H * TC / 16 : 128);
+    const size_t smem = 2 * (size_t)swz_size(H * TC) * sizeof(float2);
+    const int M = p.W / 2;
+    if (M % TC) return cudaErrorInvalidValue;
+    auto kern = k_cols_conv<H, TC, T>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<dim3(M / TC, p.C), T, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+static cudaError_t rows_dispatch(const FftParams& p, cudaStream_t s, bool inverse)
+{
+    switch (p.W / 2) {
+        case 32: return rows_launch<32>(p, s, inverse);
+        case 64: return rows_launch<64>(p, s, inverse);
+        case 128: return rows_launch<128>(p, s, inverse);
+        case 256: return rows_launch<256>(p, s, inverse);
+        case 512: return rows_launch<512>(p, s, inverse);
+        case 1024: return rows_launch<1024>(p, s, inverse);
+        case 2048: return rows_launch<2048>(p, s, inverse);
+    }
+    return cudaErrorInvalidValue;
+}
+
+static cudaError_t cols_dispatch(const FftParams& p, cudaStream_t s)
+{
+    switch (p.H) {
+        case 64: return cols_launch<64>(p, s);
+        case 128: return cols_launch<128>(p, s);
+        case 256: return cols_launch<256>(p, s);
+        case 512: return cols_launch<512>(p, s);
+        case 1024: return cols_launch<1024>(p, s);
+        case 2048: return cols_launch<2048>(p, s);
+        case 4096: return cols_launch<4096>(p, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool fft_size_supported(int H, int W)
+{
+    auto pow2 = [](int n) { return n > 0 && (n & (n - 1)) == 0; };
+    return pow2(H) && pow2(W) && H >= 64 && H <= 4096 && W >= 64 && W <= 4096;
+}
+
+cudaError_t launch_fft_rows_r2c(const FftParams& p, cudaStream_t s) { return rows_dispatch(p, s, false); }
+cudaError_t launch_fft_cols(const FftParams& p, cudaStream_t s) { return cols_dispatch(p, s); }
+cudaError_t launch_fft_rows_c2r(const FftParams& p, cudaStream_t s) { return rows_dispatch(p, s, true); }
+
+// ------------------------------------------------------- kernel spectra (FP64)
+// S(ky, kx) = (1 / (H W)) sum_{dy,dx} K~(dy, dx) cos(2 pi ky dy / H) cos(2 pi kx dx / W):
+// the DFT of the kernel placed on the torus; it is real and even in each axis
+// because K~ depends on |d| only.  Computed in two separable FP64 sums.
+__global__ void k_spec_rows(const double* Kd, int R, int W, const double* cos_W, double* T)
+{
+    // T[dy + R][kx] = sum_dx K(dy, dx) cos(2 pi kx dx / W), kx in 0..W/2
+    const int M1 = W / 2 + 1;
+    const int n = 2 * R + 1;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n * M1; u += gridDim.x * blockDim.x) {
+        const int r = u / M1, kx = u % M1;
+        double acc = 0.0;
+        for (int dx = -R; dx <= R; dx++) {
+            const int m = (int)(((long long)kx * (dx + W)) % W);
+            acc += Kd[r * n + dx + R] * cos_W[m];
+        }
+        T[u] = acc;
+    }
+}
+
+__global__ void k_spec_cols(const double* T, int R, int H, int W, const double* cos_H, float* S)
+{
+    // S[kx][ky] for ky in 0..H/2
+    const int M1 = W / 2 + 1;
+    const int HS = H / 2 + 1;
+    const double scale = 1.0 / ((double)H * (double)W);
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < M1 * HS; u += gridDim.x * blockDim.x) {
+        const int kx = u / HS, ky = u % HS;
+        double acc = 0.0;
+        for (int dy = -R; dy <= R; dy++) {
+            const int m = (int)(((long long)ky * (dy + H)) % H);
+            acc += T[(dy + R) * M1 + kx] * cos_H[m];
+        }
+        S[u] = (float)(acc * scale);
+    }
+}
+
+cudaError_t launch_spectra(const double* Kd, int R, int H, int W, const double* cos_H,
+                           const double* cos_W, double* T_scratch, float* S_out, cudaStream_t s)
+{
+    const int n = 2 * R + 1;
+    const int M1 = W / 2 + 1;
+    int blocks = (n * M1 + 255) / 256;
+    k_spec_rows<<<blocks, 256, 0, s>>>(Kd, R, W, cos_W, T_scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    blocks = (M1 * (H / 2 + 1) + 255) / 256;
+    k_spec_cols<<<blocks, 256, 0, s>>>(T_scratch, R, H, W, cos_H, S_out);
+    return cudaGetLastError();
+}
+
+}  // namespace lenia

@@ -1,0 +1,189 @@
+// Shared-memory FFT building blocks for the spectral convolution route
+// (convolution theorem, note after Algorithm 2 of arXiv 2304.05639:
+// X * Y = F^-1(F X . F Y)).
+//
+// A length-N complex FFT (N a power of two) runs as a sequence of Stockham
+// decimation-in-time passes.  In one pass of radix R with sub-transform size
+// Ns, butterfly j (0 <= j < N/R) reads x[j + r N/R] (r < R), multiplies by
+// w^{r k} with k = j mod Ns and w = exp(-+2 pi i / (Ns R)), takes an R-point
+// DFT in registers and writes y_q to position (j - k) R + k + q Ns.  After
+// the passes (Ns = 1, R, R^2, ...) the output is in natural order.
+//
+// Each pass reads all of a thread's butterfly inputs into registers, waits at
+// a block barrier, then writes, so a single shared buffer serves as source and
+// destination.  The first pass can read through a caller-supplied functor
+// (global memory, or a spectral product) and the last pass can write through
+// one, which saves two shared-memory round trips per transform.
+//
+// Twiddles come from FP32 tables built in FP64 on the host and rounded once:
+// tw[m] = exp(-2 pi i m / N), m < N.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace lenia {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos(2 pi q / 16), q = 0..4: exact decimal expansions of 1, cos(pi/8),
+// sqrt(2)/2, sin(pi/8), 0.
+struct C16 {
+    static constexpr float c1 = 0.923879532511286756128f;
+    static constexpr float c2 = 0.707106781186547524401f;
+    static constexpr float c3 = 0.382683432365089771728f;
+};
+
+// w_R^q = exp(-+2 pi i q / R) applied to a, for q < R/2 (compile-time).
+template <int R, int Q, bool INV>
+__device__ __forceinline__ float2 rot(float2 a)
+{
+    static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
+    constexpr int q16 = Q * (16 / R);   // angle in units of 2 pi / 16
+    if constexpr (q16 == 0) return a;
+    else if constexpr (q16 == 4) return mul_mi<INV>(a);
+    else {
+        constexpr float c = (q16 == 1) ? C16::c1 : (q16 == 2) ? C16::c2 : (q16 == 3) ? C16::c3
+                          : (q16 == 5) ? -C16::c3 : (q16 == 6) ? -C16::c2 : -C16::c1;
+        constexpr float s = (q16 == 1) ? C16::c3 : (q16 == 2) ? C16::c2 : (q16 == 3) ? C16::c1
+                          : (q16 == 5) ? C16::c1 : (q16 == 6) ? C16::c2 : C16::c3;
+        // forward: multiply by (c - i s); inverse by (c + i s)
+        return INV ? make_float2(a.x * c - a.y * s, a.x * s + a.y * c)
+                   : make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
+    }
+}
+
+// In-register R-point DFT, natural-order input and output (radix-2 split).
+template <int R, bool INV>
+struct DFT {
+    template <int Q>
+    __device__ __forceinline__ static void combine(float2* v, const float2* e, const float2* o)
+    {
+        if constexpr (Q < R / 2) {
+            float2 t = rot<R, Q, INV>(o[Q]);
+            v[Q] = cadd(e[Q], t);
+            v[Q + R / 2] = csub(e[Q], t);
+            combine<Q + 1>(v, e, o);
+        }
+    }
+    __device__ __forceinline__ static void run(float2* v)
+    {
+        float2 e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; i++) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        DFT<R / 2, INV>::run(e);
+        DFT<R / 2, INV>::run(o);
+        combine<0>(v, e, o);
+    }
+};
+template <bool INV>
+struct DFT<2, INV> {
+    __device__ __forceinline__ static void run(float2* v)
+    {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+template <bool INV>
+struct DFT<1, INV> {
+    __device__ __forceinline__ static void run(float2*) {}
+};
+
+__host__ __device__ constexpr int fft_radix(int remaining) { return remaining >= 16 ? 16 : remaining; }
+
+// One Stockham pass over NB independent length-N transforms held by a block of
+// T threads.  Element i of transform b is read with ld(b, i) and written with
+// st(b, i, v).  BFAST: consecutive threads take consecutive transforms b
+// (interleaved layouts), else consecutive butterflies j.
+template <int N, int R, int NB, int T, bool INV, bool BFAST, class LD, class ST>
+__device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ tw, LD ld, ST st)
+{
+    constexpr int NBF = NB * (N / R);
+    constexpr int PER = (NBF + T - 1) / T;
+    float2 v[PER][R];
+    const int tstep = N / R;
+    // exponent step for w^{rk}: table index r*k*(N/(Ns R))
+    const int tws = N / (Ns * R);
+#pragma unroll
+    for (int p = 0; p < PER; p++) {
+        const int u = threadIdx.x + p * T;
+        if (NBF % T == 0 || u < NBF) {
+            const int b = BFAST ? (u % NB) : (u / (N / R));
+            const int j = BFAST ? (u / NB) : (u % (N / R));
+            const int k = j & (Ns - 1);
+#pragma unroll
+            for (int r = 0; r < R; r++) v[p][r] = ld(b, j + r * tstep);
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; r++) {
+                    float2 w = __ldg(&tw[r * k * tws]);
+                    v[p][r] = INV ? cmulc(v[p][r], w) : cmul(v[p][r], w);
+                }
+            }
+            DFT<R, INV>::run(v[p]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; p++) {
+        const int u = threadIdx.x + p * T;
+        if (NBF % T == 0 || u < NBF) {
+            const int b = BFAST ? (u % NB) : (u / (N / R));
+            const int j = BFAST ? (u / NB) : (u % (N / R));
+            const int k = j & (Ns - 1);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int q = 0; q < R; q++) st(b, base + q * Ns, v[p][q]);
+        }
+    }
+    __syncthreads();
+}
+
+// Full transform: pass 1 reads with ld_first, middle passes use the shared
+// accessors sld/sst, the last pass writes with st_last.  With a single pass
+// the first reader and the last writer are used together.
+template <int N, int NB, int T, bool INV, bool BFAST, int NS = 1, class LF, class SL, class SS, class STL>
+__device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_first, SL sld, SS sst, STL st_last)
+{
+    constexpr int R = fft_radix(N / NS);
+    constexpr bool first = (NS == 1);
+    constexpr bool last = (NS * R == N);
+    if constexpr (first && last) {
+        fft_pass<N, R, NB, T, INV, BFAST>(NS, tw, ld_first, st_last);
+    } else if constexpr (first) {
+        fft_pass<N, R, NB, T, INV, BFAST>(NS, tw, ld_first, sst);
+        fft_run<N, NB, T, INV, BFAST, NS * R>(tw, ld_first, sld, sst, st_last);
+    } else if constexpr (last) {
+        fft_pass<N, R, NB, T, INV, BFAST>(NS, tw, sld, st_last);
+    } else {
+        fft_pass<N, R, NB, T, INV, BFAST>(NS, tw, sld, sst);
+        fft_run<N, NB, T, INV, BFAST, NS * R>(tw, ld_first, sld, sst, st_last);
+    }
+}
+
+// Shared-memory index swizzle: one float2 of padding per 16 keeps the
+// power-of-two strides of the first passes off a single bank.
+__device__ __forceinline__ int swz(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int swz_size(int n) { return n + (n >> 4) + 1; }
+
+}  // namespace lenia

@@ -1,0 +1,701 @@
+// C ABI of liblenia (declared in include/lenia.h): validation, the FP64
+// kernel builder, scratch allocation, and the per-step launch sequence.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "../../include/lenia.h"
+#include "lenia_internal.cuh"
+
+using namespace lenia;
+
+struct lenia_ctx {
+    lenia_config cfg;
+    std::vector<lenia_kernel_desc> kd;
+    std::vector<std::vector<double>> kw;   // normalised FP64 kernels, row-major dy, dx
+    int path = LENIA_CONV_DIRECT;
+    int n_p = 0, p_mu = -1, p_sigma = -1, p_h = -1;
+    int max_R = 0;
+    size_t N = 0;                          // sites
+    // device scratch (library-owned)
+    float* d_w = nullptr;
+    int* d_w_off = nullptr;
+    int* d_yr = nullptr;
+    int* d_yr_off = nullptr;
+    float* d_S = nullptr;
+    float2* d_twM = nullptr;
+    float2* d_twW = nullptr;
+    float2* d_twH = nullptr;
+    float2* d_Ahat = nullptr;
+    float2* d_Uhat = nullptr;
+    float* d_U = nullptr;
+    double* d_partials = nullptr;
+    float* d_trig = nullptr;               // sin_y, cos_y, sin_x, cos_x
+    float* d_A2 = nullptr;
+    float* d_P2 = nullptr;
+    float* d_A3 = nullptr;
+    float* d_P3 = nullptr;
+    float* d_stats = nullptr;
+    int n_part_blocks = 0;
+    ConvParams cp;
+    FftParams fp;
+    KernelTable kt;
+    std::string err;
+    // optional per-launch timing (lenia_profile_start / lenia_profile_stop)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+};
+
+// names of the launch kinds the profiler distinguishes
+static const char* kKindNames[] = {"rows_r2c", "cols_conv", "rows_c2r", "direct_conv", "epilogue",
+                                   "stats_partials", "stats_final"};
+enum { KIND_R2C, KIND_COLS, KIND_C2R, KIND_DIRECT, KIND_EPI, KIND_STATS_P, KIND_STATS_F, KIND_COUNT };
+
+namespace {
+
+const double kTwoPi = 6.283185307179586476925286766559;
+
+lenia_status fail(lenia_ctx* c, lenia_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CUDA_OR_FAIL(ctx, call)                                                      \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(ctx, LENIA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Kernel shell of the original Lenia: beta[floor(B rho)] core(B rho mod 1),
+// core(q) = exp(4 - 1/(q (1 - q))); or the paper's two-bump kernel function.
+double kernel_at(const lenia_kernel_desc& k, int dy, int dx)
+{
+    const double rho = sqrt((double)(dy * dy + dx * dx)) / (double)k.radius;
+    if (!(rho < 1.0)) return 0.0;
+    if (k.form == LENIA_KERNEL_SHELLS) {
+        const double br = rho * k.n_shells;
+        const double fl = floor(br);
+        const double q = br - fl;
+        const double core = (q > 0.0 && q < 1.0) ? exp(4.0 - 1.0 / (q * (1.0 - q))) : 0.0;
+        return k.beta[(int)fl] * core;
+    }
+    double v = 0.0;
+    for (int b = 0; b < 2; b++) {
+        const double d = rho - k.bump[3 * b];
+        const double w = k.bump[3 * b + 1];
+        v += k.bump[3 * b + 2] * exp(-d * d / (2.0 * w * w));
+    }
+    return v;
+}
+
+bool build_kernel(const lenia_kernel_desc& k, std::vector<double>& out)
+{
+    const int R = k.radius, n = 2 * R + 1;
+    out.assign((size_t)n * n, 0.0);
+    double total = 0.0;
+    for (int dy = -R; dy <= R; dy++)
+        for (int dx = -R; dx <= R; dx++) {
+            const double v = kernel_at(k, dy, dx);
+            out[(size_t)(dy + R) * n + (dx + R)] = v;
+            total += v;
+        }
+    if (!(total > 0.0) || !isfinite(total)) return false;
+    for (double& v : out) v /= total;
+    return true;
+}
+
+lenia_status validate(const lenia_config* c, const lenia_kernel_desc* ks, std::string& why)
+{
+    auto bad = [&](const char* m) { why = m; return LENIA_EINVAL; };
+    if (!c || !ks) return bad("null config or kernels");
+    if (c->height < 8 || c->width < 8) return bad("height and width must be >= 8");
+    if (c->width % 4) return bad("width must be a multiple of 4");
+    if ((long long)c->height * c->width > (1LL << 30)) return bad("world larger than 2^30 sites");
+    if (c->n_channels < 1 || c->n_channels > kMaxChannels) return bad("n_channels must be 1..8");
+    if (c->n_kernels < 1 || c->n_kernels > kMaxKernels) return bad("n_kernels must be 1..64");
+    if (!isfinite(c->dt) || c->dt < 0.f) return bad("dt must be finite and >= 0");
+    if (c->growth_form != LENIA_GROWTH_SIGNED && c->growth_form != LENIA_GROWTH_PAPER)
+        return bad("unknown growth_form");
+    if (c->localized & ~7) return bad("localized has unknown bits");
+    if (c->maintain_genes != 0 && c->maintain_genes != 1) return bad("maintain_genes must be 0 or 1");
+    if (c->maintain_genes && !c->localized) return bad("maintain_genes needs localized genes");
+    if (c->r_diff < 0 || c->r_diff > 8 || 2 * c->r_diff + 1 > c->height || 2 * c->r_diff + 1 > c->width)
+        return bad("r_diff must be 0..8 and 2 r_diff + 1 <= min(H, W)");
+    if (!isfinite(c->eps_u) || !isfinite(c->eps_p)) return bad("eps must be finite");
+    if (c->alpha_on != 0 && c->alpha_on != 1) return bad("alpha_on must be 0 or 1");
+    if (c->conv_path < LENIA_CONV_AUTO || c->conv_path > LENIA_CONV_DIRECT) return bad("unknown conv_path");
+    if (c->conv_path == LENIA_CONV_FFT && !fft_size_supported(c->height, c->width))
+        return bad("FFT path needs H and W powers of two in [64, 4096]");
+    for (int k = 0; k < c->n_kernels; k++) {
+        const lenia_kernel_desc& d = ks[k];
+        if (d.src_channel < 0 || d.src_channel >= c->n_channels || d.dst_channel < 0 ||
+            d.dst_channel >= c->n_channels)
+            return bad("kernel channel index out of range");
+        if (d.radius < 1 || 2 * d.radius + 1 > c->height || 2 * d.radius + 1 > c->width)
+            return bad("kernel radius must be >= 1 and 2R + 1 <= min(H, W)");
+        if (d.radius > 64) return bad("kernel radius must be <= 64");
+        if (d.form == LENIA_KERNEL_SHELLS) {
+            if (d.n_shells < 1 || d.n_shells > 4) return bad("n_shells must be 1..4");
+            for (int i = 0; i < d.n_shells; i++)
+                if (!isfinite(d.beta[i])) return bad("beta must be finite");
+        } else if (d.form == LENIA_KERNEL_BUMPS) {
+            for (int i = 0; i < 6; i++)
+                if (!isfinite(d.bump[i])) return bad("bump parameters must be finite");
+            if (!(d.bump[1] > 0.0) || !(d.bump[4] > 0.0)) return bad("bump widths must be > 0");
+        } else {
+            return bad("unknown kernel form");
+        }
+        if (!isfinite(d.h) || !isfinite(d.mu) || !isfinite(d.sigma)) return bad("genes must be finite");
+        if (!(c->localized & LENIA_LOC_SIGMA) && !(d.sigma > 0.f)) return bad("global sigma must be > 0");
+    }
+    return LENIA_OK;
+}
+
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const char* pa = (const char*)a;
+    const char* pb = (const char*)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+template <class T>
+lenia_status dalloc(lenia_ctx* c, T** p, size_t n)
+{
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(c, LENIA_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return LENIA_OK;
+}
+
+std::vector<float2> twiddles(int n, int count)
+{
+    std::vector<float2> t((size_t)count);
+    for (int m = 0; m < count; m++) {
+        const double a = kTwoPi * (double)m / (double)n;
+        t[m] = make_float2((float)cos(a), (float)-sin(a));
+    }
+    return t;
+}
+
+// Records an event pair around each launch while profiling is on.
+struct ProfScope {
+    lenia_ctx* c;
+    cudaStream_t s;
+    bool on;
+    ProfScope(lenia_ctx* c_, int kind, cudaStream_t s_) : c(c_), s(s_), on(false)
+    {
+        if (c->prof && c->ev_used + 2 <= c->ev.size()) {
+            on = true;
+            c->ev_kind[c->ev_used / 2] = kind;
+            cudaEventRecord(c->ev[c->ev_used], s);
+        }
+    }
+    ~ProfScope()
+    {
+        if (on) {
+            cudaEventRecord(c->ev[c->ev_used + 1], s);
+            c->ev_used += 2;
+        }
+    }
+};
+
+lenia_status potentials(lenia_ctx* c, const float* A, float* U, cudaStream_t s)
+{
+    if (c->path == LENIA_CONV_FFT) {
+        FftParams fp = c->fp;
+        fp.A = A;
+        fp.U = U;
+        {
+            ProfScope ps(c, KIND_R2C, s);
+            CUDA_OR_FAIL(c, launch_fft_rows_r2c(fp, s));
+        }
+        {
+            ProfScope ps(c, KIND_COLS, s);
+            CUDA_OR_FAIL(c, launch_fft_cols(fp, s));
+        }
+        {
+            ProfScope ps(c, KIND_C2R, s);
+            CUDA_OR_FAIL(c, launch_fft_rows_c2r(fp, s));
+        }
+    } else {
+        ConvParams cp = c->cp;
+        cp.A = A;
+        cp.U = U;
+        ProfScope ps(c, KIND_DIRECT, s);
+        CUDA_OR_FAIL(c, launch_direct_conv(cp, c->max_R, s));
+    }
+    return LENIA_OK;
+}
+
+EpiParams epi_params(lenia_ctx* c)
+{
+    EpiParams ep;
+    memset(&ep, 0, sizeof(ep));
+    ep.sin_y = c->d_trig;
+    ep.cos_y = c->d_trig + c->cfg.height;
+    ep.sin_x = c->d_trig + 2 * c->cfg.height;
+    ep.cos_x = c->d_trig + 2 * c->cfg.height + c->cfg.width;
+    ep.H = c->cfg.height;
+    ep.W = c->cfg.width;
+    ep.n_p = c->n_p;
+    ep.p_mu = c->p_mu;
+    ep.p_sigma = c->p_sigma;
+    ep.p_h = c->p_h;
+    ep.maintain = c->cfg.maintain_genes;
+    ep.growth_form = c->cfg.growth_form;
+    ep.alpha_on = c->cfg.alpha_on;
+    ep.r_diff = c->cfg.r_diff;
+    ep.dt = c->cfg.dt;
+    ep.eps_u = c->cfg.eps_u;
+    ep.eps_p = c->cfg.eps_p;
+    ep.kt = c->kt;
+    return ep;
+}
+
+lenia_status check_state_args(lenia_ctx* c, const float* A_in, const float* P_in, const float* A_out,
+                              const float* P_out)
+{
+    if (!c) return LENIA_EINVAL;
+    const size_t abytes = c->N * c->cfg.n_channels * sizeof(float);
+    const size_t pbytes = c->N * c->n_p * c->cfg.n_kernels * sizeof(float);
+    if (!A_in || !A_out) return fail(c, LENIA_EINVAL, "A_in and A_out must be non-null");
+    if (c->n_p && (!P_in || !P_out)) return fail(c, LENIA_EINVAL, "P_in and P_out are required with localized genes");
+    if (ranges_overlap(A_in, abytes, A_out, abytes)) return fail(c, LENIA_EINVAL, "A_in and A_out overlap");
+    if (c->n_p) {
+        if (ranges_overlap(P_in, pbytes, P_out, pbytes)) return fail(c, LENIA_EINVAL, "P_in and P_out overlap");
+        if (ranges_overlap(A_out, abytes, P_out, pbytes) || ranges_overlap(A_out, abytes, P_in, pbytes) ||
+            ranges_overlap(A_in, abytes, P_out, pbytes))
+            return fail(c, LENIA_EINVAL, "A and P buffers overlap");
+    }
+    return LENIA_OK;
+}
+
+lenia_status step_impl(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
+                       float* stats_out, uint8_t* alpha_out, const float* U_given, cudaStream_t s)
+{
+    if (!U_given) {
+        lenia_status st = potentials(c, A_in, c->d_U, s);
+        if (st != LENIA_OK) return st;
+    }
+    EpiParams ep = epi_params(c);
+    ep.A = A_in;
+    ep.P = P_in;
+    ep.U = U_given ? U_given : c->d_U;
+    ep.A_out = A_out;
+    ep.P_out = c->n_p ? P_out : nullptr;
+    ep.alpha_out = alpha_out;
+    ep.partials = stats_out ? c->d_partials : nullptr;
+    int nb = 0;
+    {
+        ProfScope ps(c, KIND_EPI, s);
+        CUDA_OR_FAIL(c, launch_epilogue(ep, s, &nb));
+    }
+    if (stats_out) {
+        ProfScope ps(c, KIND_STATS_F, s);
+        CUDA_OR_FAIL(c, launch_stats_final(c->d_partials, nb, c->cfg.n_channels, c->cfg.height,
+                                           c->cfg.width, stats_out, s));
+    }
+    return LENIA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lenia_status_string(lenia_status s)
+{
+    switch (s) {
+        case LENIA_OK: return "ok";
+        case LENIA_EINVAL: return "invalid argument";
+        case LENIA_ENOMEM: return "out of memory";
+        case LENIA_ECUDA: return "CUDA error";
+        case LENIA_ETIMEOUT: return "device wait timed out";
+        case LENIA_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+const char* lenia_last_error(const lenia_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int32_t lenia_conv_path(const lenia_ctx* ctx) { return ctx ? ctx->path : -1; }
+
+int32_t lenia_launches_per_step(const lenia_ctx* ctx)
+{
+    if (!ctx) return -1;
+    return (ctx->path == LENIA_CONV_FFT ? 3 : 1) + 2;
+}
+
+void lenia_destroy(lenia_ctx* c)
+{
+    if (!c) return;
+    void* ptrs[] = {c->d_w, c->d_w_off, c->d_yr, c->d_yr_off, c->d_S, c->d_twM, c->d_twW, c->d_twH,
+                    c->d_Ahat, c->d_Uhat, c->d_U, c->d_partials, c->d_trig, c->d_A2, c->d_P2,
+                    c->d_A3, c->d_P3, c->d_stats};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+}
+
+lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernels, void* stream,
+                        lenia_ctx** out)
+{
+    if (!out) return LENIA_EINVAL;
+    *out = nullptr;
+    std::string why;
+    lenia_status st = validate(cfg, kernels, why);
+    if (st != LENIA_OK) {
+        fprintf(stderr, "lenia_init: %s\n", why.c_str());
+        return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    lenia_ctx* c = new lenia_ctx();
+    c->cfg = *cfg;
+    c->kd.assign(kernels, kernels + cfg->n_kernels);
+    const int H = cfg->height, W = cfg->width, C = cfg->n_channels, K = cfg->n_kernels;
+    c->N = (size_t)H * W;
+    const int loc = cfg->localized;
+    c->n_p = ((loc & LENIA_LOC_MU) != 0) + ((loc & LENIA_LOC_SIGMA) != 0) + ((loc & LENIA_LOC_H) != 0);
+    c->p_mu = (loc & LENIA_LOC_MU) ? 0 : -1;
+    c->p_sigma = (loc & LENIA_LOC_SIGMA) ? ((loc & LENIA_LOC_MU) ? 1 : 0) : -1;
+    c->p_h = (loc & LENIA_LOC_H) ? c->n_p - 1 : -1;
+
+    // kernels in FP64, normalised to sum 1
+    c->kw.resize(K);
+    for (int k = 0; k < K; k++) {
+        if (!build_kernel(c->kd[k], c->kw[k])) {
+            lenia_destroy(c);
+            fprintf(stderr, "lenia_init: kernel %d sums to zero\n", k);
+            return LENIA_EINVAL;
+        }
+        c->max_R = std::max(c->max_R, c->kd[k].radius);
+    }
+    memset(&c->kt, 0, sizeof(c->kt));
+    c->kt.K = K;
+    c->kt.C = C;
+    for (int k = 0; k < K; k++) {
+        c->kt.src[k] = c->kd[k].src_channel;
+        c->kt.dst[k] = c->kd[k].dst_channel;
+        c->kt.h[k] = c->kd[k].h;
+        c->kt.mu[k] = c->kd[k].mu;
+        c->kt.sigma[k] = c->kd[k].sigma;
+    }
+
+    // path choice: spectral for power-of-two worlds unless the kernels are small
+    int path = cfg->conv_path;
+    if (path == LENIA_CONV_AUTO)
+        path = (fft_size_supported(H, W) && c->max_R > 6) ? LENIA_CONV_FFT : LENIA_CONV_DIRECT;
+    if (path == LENIA_CONV_DIRECT && (size_t)(32 + 2 * c->max_R) * (32 + 2 * c->max_R) * 4 > 200 * 1024) {
+        lenia_destroy(c);
+        fprintf(stderr, "lenia_init: radius too large for the direct path\n");
+        return LENIA_EINVAL;
+    }
+    c->path = path;
+
+#define ALLOC(ptr, n)                                  \
+    do {                                               \
+        lenia_status a_ = dalloc(c, &(ptr), (n));      \
+        if (a_ != LENIA_OK) {                          \
+            fprintf(stderr, "lenia_init: %s\n", c->err.c_str()); \
+            lenia_destroy(c);                          \
+            return a_;                                 \
+        }                                              \
+    } while (0)
+#define CK_INIT(call)                                                         \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            fprintf(stderr, "lenia_init: %s: %s\n", #call, cudaGetErrorString(e_)); \
+            lenia_destroy(c);                                                 \
+            return LENIA_ECUDA;                                               \
+        }                                                                     \
+    } while (0)
+
+    const size_t nA = c->N * C, nP = c->N * c->n_p * K;
+    ALLOC(c->d_U, c->N * K);
+    ALLOC(c->d_A2, nA);
+    ALLOC(c->d_A3, nA);
+    if (nP) {
+        ALLOC(c->d_P2, nP);
+        ALLOC(c->d_P3, nP);
+    }
+    ALLOC(c->d_stats, (size_t)C * 3);
+    c->n_part_blocks = epilogue_blocks(H, W);
+    ALLOC(c->d_partials, (size_t)c->n_part_blocks * C * 5);
+
+    // circular-mean tables
+    {
+        std::vector<float> trig(2 * (size_t)H + 2 * (size_t)W);
+        for (int y = 0; y < H; y++) {
+            trig[y] = (float)sin(kTwoPi * y / H);
+            trig[H + y] = (float)cos(kTwoPi * y / H);
+        }
+        for (int x = 0; x < W; x++) {
+            trig[2 * H + x] = (float)sin(kTwoPi * x / W);
+            trig[2 * H + W + x] = (float)cos(kTwoPi * x / W);
+        }
+        ALLOC(c->d_trig, trig.size());
+        CK_INIT(cudaMemcpy(c->d_trig, trig.data(), trig.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+
+    // per-channel kernel lists
+    int kcount[kMaxChannels] = {0};
+    int klist[kMaxChannels][kMaxKernels];
+    for (int k = 0; k < K; k++) {
+        const int sc = c->kd[k].src_channel;
+        klist[sc][kcount[sc]++] = k;
+    }
+
+    if (path == LENIA_CONV_DIRECT) {
+        std::vector<float> w;
+        std::vector<int> woff(K), yr, yroff(K);
+        for (int k = 0; k < K; k++) {
+            const int R = c->kd[k].radius, n = 2 * R + 1;
+            woff[k] = (int)w.size();
+            yroff[k] = (int)yr.size();
+            for (int dx = -R; dx <= R; dx++) {
+                int r = -1;
+                for (int dy = -R; dy <= R; dy++) {
+                    const double v = c->kw[k][(size_t)(dy + R) * n + (dx + R)];
+                    w.push_back((float)v);
+                    if (v != 0.0) r = std::max(r, std::abs(dy));
+                }
+                yr.push_back(r);
+            }
+        }
+        ALLOC(c->d_w, w.size());
+        ALLOC(c->d_w_off, (size_t)K);
+        ALLOC(c->d_yr, yr.size());
+        ALLOC(c->d_yr_off, (size_t)K);
+        CK_INIT(cudaMemcpy(c->d_w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_w_off, woff.data(), K * sizeof(int), cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_yr, yr.data(), yr.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_yr_off, yroff.data(), K * sizeof(int), cudaMemcpyHostToDevice));
+        memset(&c->cp, 0, sizeof(c->cp));
+        c->cp.w = c->d_w;
+        c->cp.w_off = c->d_w_off;
+        c->cp.yr = c->d_yr;
+        c->cp.yr_off = c->d_yr_off;
+        c->cp.H = H;
+        c->cp.W = W;
+        c->cp.C = C;
+        c->cp.K = K;
+        for (int k = 0; k < K; k++) c->cp.R[k] = c->kd[k].radius;
+        memcpy(c->cp.kcount, kcount, sizeof(kcount));
+        memcpy(c->cp.klist, klist, sizeof(klist));
+    } else {
+        const int M = W / 2, HS = H / 2 + 1;
+        ALLOC(c->d_Ahat, (size_t)C * H * M);
+        ALLOC(c->d_Uhat, (size_t)K * H * M);
+        ALLOC(c->d_S, (size_t)K * (M + 1) * HS);
+        std::vector<float2> twM = twiddles(M, M), twW = twiddles(W, M + 1), twH = twiddles(H, H);
+        ALLOC(c->d_twM, twM.size());
+        ALLOC(c->d_twW, twW.size());
+        ALLOC(c->d_twH, twH.size());
+        CK_INIT(cudaMemcpy(c->d_twM, twM.data(), twM.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_twW, twW.data(), twW.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_twH, twH.data(), twH.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        // FP64 spectra of every kernel on the device, rounded once to FP32
+        std::vector<double> cosH(H), cosW(W);
+        for (int m = 0; m < H; m++) cosH[m] = cos(kTwoPi * m / H);
+        for (int m = 0; m < W; m++) cosW[m] = cos(kTwoPi * m / W);
+        double *d_cosH = nullptr, *d_cosW = nullptr, *d_Kd = nullptr, *d_T = nullptr;
+        const size_t kmax = (size_t)(2 * c->max_R + 1) * (2 * c->max_R + 1);
+        bool ok = cudaMalloc(&d_cosH, H * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&d_cosW, W * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&d_Kd, kmax * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc(&d_T, (size_t)(2 * c->max_R + 1) * (M + 1) * sizeof(double)) == cudaSuccess;
+        cudaError_t e = ok ? cudaSuccess : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMemcpy(d_cosH, cosH.data(), H * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_cosW, cosW.data(), W * sizeof(double), cudaMemcpyHostToDevice);
+        for (int k = 0; k < K && e == cudaSuccess; k++) {
+            e = cudaMemcpyAsync(d_Kd, c->kw[k].data(), c->kw[k].size() * sizeof(double),
+                                cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = launch_spectra(d_Kd, c->kd[k].radius, H, W, d_cosH, d_cosW, d_T,
+                                   c->d_S + (size_t)k * (M + 1) * HS, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        cudaFree(d_cosH);
+        cudaFree(d_cosW);
+        cudaFree(d_Kd);
+        cudaFree(d_T);
+        CK_INIT(e);
+        memset(&c->fp, 0, sizeof(c->fp));
+        c->fp.Ahat = c->d_Ahat;
+        c->fp.Uhat = c->d_Uhat;
+        c->fp.S = c->d_S;
+        c->fp.tw_M = c->d_twM;
+        c->fp.tw_W = c->d_twW;
+        c->fp.tw_H = c->d_twH;
+        c->fp.H = H;
+        c->fp.W = W;
+        c->fp.C = C;
+        c->fp.K = K;
+        memcpy(c->fp.kcount, kcount, sizeof(kcount));
+        memcpy(c->fp.klist, klist, sizeof(klist));
+    }
+    CK_INIT(cudaStreamSynchronize(s));
+    CK_INIT(cudaGetLastError());
+#undef ALLOC
+#undef CK_INIT
+    *out = c;
+    return LENIA_OK;
+}
+
+lenia_status lenia_step(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
+                        float* stats_out, void* stream)
+{
+    lenia_status st = check_state_args(c, A_in, P_in, A_out, P_out);
+    if (st != LENIA_OK) return st;
+    return step_impl(c, A_in, P_in, A_out, P_out, stats_out, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+lenia_status lenia_rollout(lenia_ctx* c, float* A, float* P, int32_t n_steps, float* stats_out, void* stream)
+{
+    if (!c) return LENIA_EINVAL;
+    if (n_steps < 0) return fail(c, LENIA_EINVAL, "n_steps must be >= 0");
+    if (!A || (c->n_p && !P)) return fail(c, LENIA_EINVAL, "A (and P with localized genes) must be non-null");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t stride = (size_t)c->cfg.n_channels * 3;
+    for (int t = 0; t < n_steps; t++) {
+        const bool even = (t % 2) == 0;
+        const float* Ai = even ? A : c->d_A2;
+        const float* Pi = even ? P : c->d_P2;
+        float* Ao = even ? c->d_A2 : A;
+        float* Po = even ? c->d_P2 : P;
+        lenia_status st = step_impl(c, Ai, c->n_p ? Pi : nullptr, Ao, c->n_p ? Po : nullptr,
+                                    stats_out ? stats_out + t * stride : nullptr, nullptr, nullptr, s);
+        if (st != LENIA_OK) return st;
+    }
+    if (n_steps % 2) {
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(A, c->d_A2, c->N * c->cfg.n_channels * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, s));
+        if (c->n_p)
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(P, c->d_P2, c->N * c->n_p * c->cfg.n_kernels * sizeof(float),
+                                            cudaMemcpyDeviceToDevice, s));
+    }
+    return LENIA_OK;
+}
+
+lenia_status lenia_backward(lenia_ctx* c, const float*, const float*, int32_t, const float*, float*, float*,
+                            void*)
+{
+    return fail(c, LENIA_ENOTSUP, "lenia_backward is not implemented in this build");
+}
+
+lenia_status lenia_stats(lenia_ctx* c, const float* A, float* out, void* stream)
+{
+    if (!c) return LENIA_EINVAL;
+    if (!A || !out) return fail(c, LENIA_EINVAL, "A and out must be non-null");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int H = c->cfg.height, W = c->cfg.width, C = c->cfg.n_channels;
+    int nb = 0;
+    CUDA_OR_FAIL(c, launch_stats_partials(A, C, H, W, c->d_trig, c->d_trig + H, c->d_trig + 2 * H,
+                                          c->d_trig + 2 * H + W, c->d_partials, s, &nb));
+    CUDA_OR_FAIL(c, launch_stats_final(c->d_partials, nb, C, H, W, out, s));
+    return LENIA_OK;
+}
+
+lenia_status lenia_potentials(lenia_ctx* c, const float* A_in, float* U_out, void* stream)
+{
+    if (!c) return LENIA_EINVAL;
+    if (!A_in || !U_out) return fail(c, LENIA_EINVAL, "A_in and U_out must be non-null");
+    if (ranges_overlap(A_in, c->N * c->cfg.n_channels * sizeof(float), U_out,
+                       c->N * c->cfg.n_kernels * sizeof(float)))
+        return fail(c, LENIA_EINVAL, "A_in and U_out overlap");
+    return potentials(c, A_in, U_out, (cudaStream_t)stream);
+}
+
+lenia_status lenia_update_from_potentials(lenia_ctx* c, const float* A_in, const float* P_in, const float* U_in,
+                                          float* A_out, float* P_out, uint8_t* alpha_out, void* stream)
+{
+    lenia_status st = check_state_args(c, A_in, P_in, A_out, P_out);
+    if (st != LENIA_OK) return st;
+    if (!U_in) return fail(c, LENIA_EINVAL, "U_in must be non-null");
+    return step_impl(c, A_in, P_in, A_out, P_out, nullptr, alpha_out, U_in, (cudaStream_t)stream);
+}
+
+lenia_status lenia_step_host(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
+                             float* stats_out, void* stream)
+{
+    if (!c) return LENIA_EINVAL;
+    if (!A_in || !A_out || (c->n_p && (!P_in || !P_out)))
+        return fail(c, LENIA_EINVAL, "host A (and P with localized genes) must be non-null");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ab = c->N * c->cfg.n_channels * sizeof(float);
+    const size_t pb = c->N * c->n_p * c->cfg.n_kernels * sizeof(float);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_A2, A_in, ab, cudaMemcpyHostToDevice, s));
+    if (pb) CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_P2, P_in, pb, cudaMemcpyHostToDevice, s));
+    lenia_status st = step_impl(c, c->d_A2, c->n_p ? c->d_P2 : nullptr, c->d_A3, c->n_p ? c->d_P3 : nullptr,
+                                stats_out ? c->d_stats : nullptr, nullptr, nullptr, s);
+    if (st != LENIA_OK) return st;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(A_out, c->d_A3, ab, cudaMemcpyDeviceToHost, s));
+    if (pb) CUDA_OR_FAIL(c, cudaMemcpyAsync(P_out, c->d_P3, pb, cudaMemcpyDeviceToHost, s));
+    if (stats_out)
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(stats_out, c->d_stats, c->cfg.n_channels * 3 * sizeof(float),
+                                        cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+    return LENIA_OK;
+}
+
+lenia_status lenia_profile_start(lenia_ctx* c, int32_t max_launches)
+{
+    if (!c || max_launches < 1 || max_launches > (1 << 20)) return LENIA_EINVAL;
+    const size_t need = 2 * (size_t)max_launches;
+    while (c->ev.size() < need) {
+        cudaEvent_t e;
+        CUDA_OR_FAIL(c, cudaEventCreate(&e));
+        c->ev.push_back(e);
+    }
+    c->ev_kind.assign(max_launches, 0);
+    c->ev_used = 0;
+    c->prof = true;
+    return LENIA_OK;
+}
+
+lenia_status lenia_profile_stop(lenia_ctx* c, float* total_ms, int32_t* counts)
+{
+    if (!c || !total_ms || !counts) return LENIA_EINVAL;
+    c->prof = false;
+    for (int k = 0; k < KIND_COUNT; k++) {
+        total_ms[k] = 0.f;
+        counts[k] = 0;
+    }
+    for (size_t i = 0; i < c->ev_used; i += 2) {
+        CUDA_OR_FAIL(c, cudaEventSynchronize(c->ev[i + 1]));
+        float ms = 0.f;
+        CUDA_OR_FAIL(c, cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+        const int k = c->ev_kind[i / 2];
+        total_ms[k] += ms;
+        counts[k] += 1;
+    }
+    c->ev_used = 0;
+    return LENIA_OK;
+}
+
+const char* lenia_profile_kind_name(int32_t kind)
+{
+    return (kind >= 0 && kind < KIND_COUNT) ? kKindNames[kind] : nullptr;
+}
+
+lenia_status lenia_kernel_weights(const lenia_ctx* c, int32_t k, double* out)
+{
+    if (!c || !out || k < 0 || k >= c->cfg.n_kernels) return LENIA_EINVAL;
+    memcpy(out, c->kw[k].data(), c->kw[k].size() * sizeof(double));
+    return LENIA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of liblenia.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lenia {
+
+constexpr int kMaxKernels = 64;
+constexpr int kMaxChannels = 8;
+constexpr int kMaxPlanes = 3;   // mu, sigma, h
+
+// Per-kernel scalars, passed by value to the kernels that need them.
+struct KernelTable {
+    int K, C;
+    int src[kMaxKernels], dst[kMaxKernels];
+    float h[kMaxKernels], mu[kMaxKernels], sigma[kMaxKernels];
+};
+
+// Growth, alpha mask, masking and clipped update (plus stats partials).
+struct EpiParams {
+    const float* A;
+    const float* P;
+    const float* U;
+    float* A_out;
+    float* P_out;
+    uint8_t* alpha_out;
+    double* partials;          // [n_blocks][C][5] or null
+    const float* sin_y;
+    const float* cos_y;
+    const float* sin_x;
+    const float* cos_x;
+    int H, W, n_p;
+    int p_mu, p_sigma, p_h;    // plane index of each localized gene or -1
+    int maintain, growth_form, alpha_on, r_diff;
+    float dt, eps_u, eps_p;
+    KernelTable kt;
+};
+
+// Direct periodic convolution of every kernel.
+struct ConvParams {
+    const float* A;
+    float* U;
+    const float* w;            // dense FP32 kernels, transposed [dx][dy], back to back
+    const int* w_off;          // offset of kernel k in w
+    const int* yr;             // per kernel, per dx: largest |dy| with a non-zero tap (-1: none)
+    const int* yr_off;         // offset of kernel k in yr
+    int H, W, C, K;
+    int R[kMaxKernels];
+    int kcount[kMaxChannels];
+    int klist[kMaxChannels][kMaxKernels];
+};
+
+// Spectral (FFT) convolution.
+struct FftParams {
+    const float* A;            // [C][H][W]
+    float2* Ahat;              // [C][H][M] row spectra, M = W/2, element 0 packs (DC, Nyquist)
+    float2* Uhat;              // [K][H][M] per-kernel column-inverse spectra, same packing
+    float* U;                  // [K][H][W] potentials
+    const float* S;            // [K][M+1][H/2+1] real kernel spectra / (H W)
+    const float2* tw_M;        // exp(-2 pi i m / M), m < M   (row transforms)
+    const float2* tw_W;        // exp(-2 pi i m / W), m <= M  (real-signal packing)
+    const float2* tw_H;        // exp(-2 pi i m / H), m < H   (column transforms)
+    int H, W, C, K;
+    int kcount[kMaxChannels];
+    int klist[kMaxChannels][kMaxKernels];
+};
+
+// Launchers (return the cudaError_t of the launch).
+cudaError_t launch_direct_conv(const ConvParams& p, int max_R, cudaStream_t s);
+cudaError_t launch_fft_rows_r2c(const FftParams& p, cudaStream_t s);
+cudaError_t launch_fft_cols(const FftParams& p, cudaStream_t s);
+cudaError_t launch_fft_rows_c2r(const FftParams& p, cudaStream_t s);
+cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks);
+cudaError_t launch_stats_partials(const float* A, int C, int H, int W, const float* sin_y,
+                                  const float* cos_y, const float* sin_x, const float* cos_x,
+                                  double* partials, cudaStream_t s, int* n_blocks);
+cudaError_t launch_stats_final(const double* partials, int n_blocks, int C, int H, int W,
+                               float* out, cudaStream_t s);
+cudaError_t launch_spectra(const double* Kd, int R, int H, int W, const double* cos_H,
+                           const double* cos_W, double* T_scratch, float* S_out, cudaStream_t s);
+bool fft_size_supported(int H, int W);
+int epilogue_blocks(int H, int W);
+
+}  // namespace lenia

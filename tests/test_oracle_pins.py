@@ -390,3 +390,22 @@ def test_inputs_deterministic_and_shaped():
     assert a.A.shape == (3, 64, 64) and a.P.shape == (2, 15, 64, 64)
     assert [(k.src, k.dst) for k in a.kernels][:3] == [(0, 0)] * 3
     assert len(a.kernels) == 15
+
+
+# --------------------------------------------- oracle entry points agree
+
+def test_update_and_sites_agree_with_step(oracle):
+    """The update-from-potentials and sampled-site entries reproduce the full
+    step exactly (same arithmetic, different drivers)."""
+    w = inputs.multi_channel(H=40, W=48, R=5, patch=12, n_geno=3, live=True)
+    A1, P1, U, al = oracle.step(w, return_u=True, return_alpha=True)
+    A2, P2, al2 = oracle.update(w, w.A, w.P, U, return_alpha=True)
+    np.testing.assert_array_equal(A1, A2)
+    np.testing.assert_array_equal(P1, P2)
+    np.testing.assert_array_equal(al, al2)
+    ys = np.array([0, 5, 39, 17, 20]); xs = np.array([0, 47, 3, 22, 30])
+    r = oracle.step_sites(w, ys, xs)
+    np.testing.assert_array_equal(r["A"], A1[:, ys, xs])
+    np.testing.assert_array_equal(r["P"], P1.reshape(-1, 40, 48)[:, ys, xs])
+    np.testing.assert_array_equal(r["U"], U[:, ys, xs])
+    np.testing.assert_array_equal(r["alpha"], al[ys, xs])
