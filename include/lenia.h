@@ -172,6 +172,33 @@ LENIA_API lenia_status lenia_profile_start(lenia_ctx* ctx, int32_t max_launches)
 LENIA_API lenia_status lenia_profile_stop(lenia_ctx* ctx, float* total_ms, int32_t* counts);
 LENIA_API const char* lenia_profile_kind_name(int32_t kind);
 
+/* lenia_stats without a context and without any allocation (the paper has
+ * no counterpart; this is a deployment aid).  Same output as lenia_stats:
+ * out (device, C*3 floats) = mass, circular-mean centre y, centre x of each
+ * channel of the device array A [C][H][W].
+ *
+ * For callers that cannot call cudaMalloc: code whose device memory is all
+ * owned by another allocator (a framework that reserves the GPU up front,
+ * so a raw cudaMalloc fails or fragments its pool), code that must not pay
+ * the device-wide synchronisation of cudaMalloc/cudaFree in the middle of
+ * its work, and host applications that forbid plug-ins from allocating.
+ *
+ * Scratch: a file-scope static __device__ array of 2.75 MB inside
+ * liblenia.so, held on every GPU that loads the library until the process
+ * exits.  Limits: 1 <= C <= 8, 1 <= H, W <= 8192 and
+ * ceil(W/32) * ceil(H/8) * C <= 65536 (for example 2048 x 2048 with 3
+ * channels); larger requests return LENIA_EINVAL with a message on stderr
+ * before any launch.
+ * The first call on each device (with that device current) looks up the
+ * array's device address with cudaGetSymbolAddress; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents; every value a call reads is written earlier in the
+ * same call, so nothing needs clearing.  Calls whose work overlaps on the
+ * GPU (different streams, or different host threads) race on the array:
+ * serialise them.  Returns LENIA_ECUDA if a launch fails. */
+LENIA_API lenia_status lenia_stats_noalloc(const float* A, int32_t n_channels, int32_t height,
+                                           int32_t width, float* out, void* stream);
+
 /* The normalised FP64 kernel k, (2R+1)^2 values row-major over dy, dx in
  * -R..R, copied to the HOST buffer out. */
 LENIA_API lenia_status lenia_kernel_weights(const lenia_ctx* ctx, int32_t k, double* out);

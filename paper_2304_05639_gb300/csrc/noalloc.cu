@@ -1,0 +1,113 @@
+// lenia_stats_noalloc: the per-channel mass / centroid reduction of
+// lenia_stats for callers that cannot allocate device memory.  Its scratch
+// (block partial sums and the sine/cosine tables) lives in one file-scope
+// static device array of fixed size instead of context-owned cudaMalloc
+// memory; nothing here allocates.
+#include <stdio.h>
+
+#include <mutex>
+
+#include "../../include/lenia.h"
+#include "lenia_internal.cuh"
+
+using namespace lenia;
+
+namespace {
+
+// Limits of the static scratch: (stats blocks x channels) partial records of
+// five doubles, and sine/cosine tables for H, W <= 8192.
+constexpr int kNoAllocMaxRecords = 65536;
+constexpr int kNoAllocMaxSide = 8192;
+constexpr size_t kPartialDoubles = (size_t)kNoAllocMaxRecords * 5;
+constexpr size_t kTrigFloats = 4 * (size_t)kNoAllocMaxSide;
+constexpr size_t kScratchDoubles = kPartialDoubles + kTrigFloats / 2;   // 2.75 MB
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device (set up once per device).
+cudaError_t scratch_address(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+// sin/cos of 2 pi y / H and 2 pi x / W, the tables the stats kernels read.
+__global__ void k_noalloc_trig(float* trig, int H, int W)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H + W; i += gridDim.x * blockDim.x) {
+        if (i < H) {
+            double s, c;
+            sincospi(2.0 * i / H, &s, &c);
+            trig[i] = (float)s;
+            trig[H + i] = (float)c;
+        } else {
+            const int x = i - H;
+            double s, c;
+            sincospi(2.0 * x / W, &s, &c);
+            trig[2 * H + x] = (float)s;
+            trig[2 * H + W + x] = (float)c;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" lenia_status lenia_stats_noalloc(const float* A, int32_t n_channels, int32_t height, int32_t width,
+                                            float* out, void* stream)
+{
+    if (!A || !out) {
+        fprintf(stderr, "lenia_stats_noalloc: A and out must be non-null\n");
+        return LENIA_EINVAL;
+    }
+    if (n_channels < 1 || n_channels > kMaxChannels || height < 1 || width < 1 ||
+        height > kNoAllocMaxSide || width > kNoAllocMaxSide) {
+        fprintf(stderr, "lenia_stats_noalloc: need 1 <= channels <= %d and 1 <= height, width <= %d\n",
+                kMaxChannels, kNoAllocMaxSide);
+        return LENIA_EINVAL;
+    }
+    const long long records = (long long)epilogue_blocks(height, width) * n_channels;
+    if (records > kNoAllocMaxRecords) {
+        fprintf(stderr,
+                "lenia_stats_noalloc: world too large for the static scratch "
+                "(ceil(W/32) * ceil(H/8) * channels = %lld > %d)\n",
+                records, kNoAllocMaxRecords);
+        return LENIA_EINVAL;
+    }
+    void* base = nullptr;
+    cudaError_t e = scratch_address(&base);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lenia_stats_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+        return LENIA_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double* partials = (double*)base;
+    float* trig = (float*)(partials + kPartialDoubles);
+    const int H = height, W = width, C = n_channels;
+    k_noalloc_trig<<<(H + W + 255) / 256, 256, 0, s>>>(trig, H, W);
+    e = cudaGetLastError();
+    int nb = 0;
+    if (e == cudaSuccess)
+        e = launch_stats_partials(A, C, H, W, trig, trig + H, trig + 2 * H, trig + 2 * H + W, partials, s, &nb);
+    if (e == cudaSuccess) e = launch_stats_final(partials, nb, C, H, W, out, s);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lenia_stats_noalloc: launch failed: %s\n", cudaGetErrorString(e));
+        return LENIA_ECUDA;
+    }
+    return LENIA_OK;
+}

@@ -25,7 +25,7 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_potentials", "lenia_update_from_potentials", "lenia_step_host",
            "lenia_kernel_weights", "lenia_conv_path", "lenia_launches_per_step",
            "lenia_last_error", "lenia_status_string", "lenia_destroy", "lenia_profile_start",
-           "lenia_profile_stop", "lenia_profile_kind_name")
+           "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc")
 PROFILE_KINDS = 7
 
 
@@ -106,6 +106,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_profile_stop.restype = st
     lib.lenia_profile_kind_name.argtypes = [ctypes.c_int32]
     lib.lenia_profile_kind_name.restype = ctypes.c_char_p
+    lib.lenia_stats_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp]
+    lib.lenia_stats_noalloc.restype = st
     lib.lenia_destroy.argtypes = [vp]
     lib.lenia_destroy.restype = None
     if path is None:
@@ -173,6 +175,14 @@ def lenia_backward(ctx, A0, P0, n_steps, gA_T, gA0=None, g_genes=None, stream=No
 
 def lenia_stats(ctx, A, out, stream=None):
     _check(ctx, load().lenia_stats(ctx, _ptr(A), _ptr(out), _stream(stream)))
+
+
+def lenia_stats_noalloc(A, n_channels, height, width, out, stream=None):
+    """lenia_stats for callers that cannot allocate device memory (static scratch)."""
+    st = load().lenia_stats_noalloc(_ptr(A), int(n_channels), int(height), int(width), _ptr(out),
+                                    _stream(stream))
+    if st != LENIA_OK:
+        raise LeniaError(st, f"lenia_stats_noalloc: {load().lenia_status_string(st).decode()}")
 
 
 def lenia_potentials(ctx, A_in, U_out, stream=None):
