@@ -154,6 +154,12 @@ LENIA_API lenia_status lenia_update_from_potentials(lenia_ctx* ctx, const float*
                                           const float* U_in, float* A_out, float* P_out,
                                           uint8_t* alpha_out, void* stream);
 
+/* Waits for `stream` and reads the context's device status word: returns
+ * LENIA_ETIMEOUT (and clears the word) if a kernel gave up a bounded
+ * device-side wait since the last check, else LENIA_OK.  lenia_step_host
+ * calls it before returning. */
+LENIA_API lenia_status lenia_check(lenia_ctx* ctx, void* stream);
+
 /* lenia_step with HOST buffers: copies A_in/P_in host->device into library
  * buffers, steps, and copies A_out/P_out (and stats_out, C*3 floats, nullable)
  * back; returns after the stream has finished.  Page-locked host memory

@@ -1,0 +1,435 @@
+// Streaming growth / gene-maintenance / update epilogue (the same per-site
+// rule as step_kernels.cu: Sections 2.2-2.4 and Algorithm 2 of arXiv
+// 2304.05639) for diffusion radius 1 and worlds whose width is a multiple of
+// 256.
+//
+// Persistent layout: CTA b owns the 256-column chunk (b mod n_chunks) of a
+// band of consecutive rows and walks down it.  Bulk asynchronous copies keep
+// the rows it needs in shared memory, ahead of use:
+//   - a 4-slot ring of gene rows: every gene plane, 256 columns plus a
+//     4-column halo on each side (periodic), rows y-1, y, y+1 and y+2 in
+//     flight;
+//   - a 2-slot ring of potential rows (K planes) and phenospace rows (C).
+// Each copy group completes on its slot's mbarrier; every wait is bounded.
+// Each thread computes one column; the 5-site diffusion disk is read from
+// the ring, so every gene value is fetched from global memory once.
+#include <cudaTypedefs.h>
+
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "lenia_internal.cuh"
+#include "ptx_util.cuh"
+
+namespace lenia {
+
+constexpr int ER_CH = 256;             // columns per CTA
+constexpr int ER_PW = ER_CH + 8;       // gene row with 4-column halos
+
+// 0.5 * log2(e): exp(-z^2 / 2) = exp2(-C_HALF_LOG2E * z^2)
+constexpr float C_HALF_LOG2E = 0.721347520444481703680f;
+constexpr int ER_GROUPS = 2;                  // consumer warp groups, alternate rows
+constexpr int ER_WPG = ER_CH / 32;            // warps per group, 32 columns each
+constexpr int ER_CONSUMERS = ER_GROUPS * ER_WPG;
+constexpr int ER_THREADS = ER_CONSUMERS * 32 + 32;   // plus one producer warp
+constexpr int ER_NP = 5;                      // gene-row ring: rows i-1 .. i+2 in use, one ahead
+constexpr int ER_NU = 3;                      // ring depth of potential / phenospace rows
+
+constexpr int ALIGN_F = 32;                   // 128-byte alignment of TMA destinations, in floats
+__host__ __device__ constexpr size_t round_f(size_t n) { return (n + ALIGN_F - 1) / ALIGN_F * ALIGN_F; }
+
+// Shared-memory layout.  A gene slot holds every gene plane's row, 264
+// floats each (4-column halos on both sides), as one TMA box of 132 8-byte
+// elements x 1 row x NPK planes; a halo slot holds the 4 columns beyond each
+// edge of the world (NPK x 4 floats per side) for the chunks at the edges.
+template <int KT, int CT, int LOC>
+struct ErLayout {
+    static constexpr int NP = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
+    static constexpr int NPK = NP * KT;
+    static constexpr size_t p_slot = round_f((size_t)NPK * ER_PW);
+    static constexpr size_t h_slot = round_f((size_t)NPK * 4);
+    static constexpr size_t u_slot = (size_t)KT * ER_CH;
+    static constexpr size_t a_slot = (size_t)CT * ER_CH;
+    static constexpr size_t p_floats = ER_NP * p_slot;
+    static constexpr size_t h_floats = ER_NP * 2 * h_slot;
+    static constexpr size_t u_floats = ER_NU * u_slot;
+    static constexpr size_t a_floats = ER_NU * a_slot;
+    // + 128 bytes to align the base of the dynamic shared memory to 128
+    static constexpr size_t bytes = (p_floats + h_floats + u_floats + a_floats) * 4 + 2 * (ER_NP + ER_NU) * 8 + 128;
+};
+
+// Destination channel of kernel k in the paper's 15-kernel topology: 3 self
+// kernels per channel, then (0,1), (1,0), (0,2), (2,0), (1,2), (2,1).
+__host__ __device__ constexpr int paper_dst(int k)
+{
+    return k < 9 ? k / 3 : (k == 9 ? 1 : k == 10 ? 0 : k == 11 ? 2 : k == 12 ? 0 : k == 13 ? 2 : 1);
+}
+
+// Warp-specialised pipeline.  The producer warp fills the rings with bulk
+// copies; each slot has a "full" barrier (copy bytes landed) and an "empty"
+// barrier (every consumer warp is done with it).  Two groups of consumer
+// warps take alternate rows; warp w of a group computes 32 columns of its
+// row, all kernels, and never waits for another consumer warp.  Local gene
+// row l (global row r0 - 1 + l) is used by rows l - 2, l - 1 and l; a group
+// releases rows i and i + 1 after computing row i, so each gene slot is
+// released once by each group.
+// TOPO = 1: kernels route to channels as in the paper's topology (checked on
+// the host).  EPS0 = 1: eps_p == 0, where a zero neighbour count forces a
+// non-positive sum and the saturated quotient is already 0.
+template <int KT, int CT, int LOC, int TOPO, int EPS0>
+__global__ void __launch_bounds__(ER_THREADS, 1)
+    k_epilogue_rows(EpiParams p, const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_u,
+                    const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_h, int n_chunks, int n_bands,
+                    int* status)
+{
+    using L = ErLayout<KT, CT, LOC>;
+    constexpr int NPK = L::NPK, NP = L::NP;
+    constexpr int PMU = (LOC & 1) ? 0 : -1;
+    constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
+    constexpr int PH = (LOC & 4) ? NP - 1 : -1;
+    static_assert(TOPO == 0 || (KT == 15 && CT == 3), "paper topology has 15 kernels, 3 channels");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
+    float* Pring = reinterpret_cast<float*>(smem);
+    float* Hring = Pring + L::p_floats;                   // [slot][left, right][NPK][4]
+    float* Uring = Hring + L::h_floats;
+    float* Aring = Uring + L::u_floats;
+    uint64_t* full_p = reinterpret_cast<uint64_t*>(Aring + L::a_floats);
+    uint64_t* empty_p = full_p + ER_NP;
+    uint64_t* full_u = empty_p + ER_NP;
+    uint64_t* empty_u = full_u + ER_NU;
+    __shared__ float red[ER_CONSUMERS][CT * 5];
+    __shared__ int blk_failed;
+
+    const int H = p.H, W = p.W;
+    const unsigned N = (unsigned)H * (unsigned)W;        // sites; n_p K N < 2^31 (host check)
+    const int chunk = blockIdx.x % n_chunks, band = blockIdx.x / n_chunks;
+    const int x0 = chunk * ER_CH;
+    const int r0 = (int)((long long)band * H / n_bands);
+    const int r1 = (int)((long long)(band + 1) * H / n_bands);
+    const int nrows = r1 - r0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (tid == 0) {
+        for (int b = 0; b < ER_NP; b++) {
+            mbar_init(&full_p[b], 1);
+            mbar_init(&empty_p[b], ER_CONSUMERS);
+        }
+        for (int b = 0; b < ER_NU; b++) {
+            mbar_init(&full_u[b], 1);
+            mbar_init(&empty_u[b], ER_WPG);
+        }
+        mbar_fence_init();
+        blk_failed = 0;
+    }
+    __syncthreads();
+
+    float st[CT * 5];
+#pragma unroll
+    for (int v = 0; v < CT * 5; v++) st[v] = 0.f;
+    int last_gene = -1, last_pot = -1;      // producer: last rows whose copies were issued
+
+    if (warp == ER_CONSUMERS) {
+        // ------------------------------------------------ producer warp
+        // One lane issues TMA boxes; x coordinates count 8-byte elements (two
+        // floats), so the gene box at x0/2 - 2 spans columns x0 - 4 .. x0 + 259.
+        const bool edge_l = x0 == 0, edge_r = x0 + ER_CH == W;
+        auto genes = [&](int l) -> bool {                      // local gene row l = global r0 - 1 + l
+            if (NPK == 0) return true;
+            const int slot = l % ER_NP;
+            if (l >= ER_NP && !mbar_wait_bounded(&empty_p[slot], ((l - ER_NP) / ER_NP) & 1)) return false;
+            int r = r0 - 1 + l;
+            r = r < 0 ? r + H : (r >= H ? r - H : r);
+            last_gene = l;
+            if (lane == 0) {
+                fence_proxy_async_shared();
+                const uint32_t bytes = NPK * ER_PW * 4 + (edge_l ? NPK * 16 : 0) + (edge_r ? NPK * 16 : 0);
+                mbar_arrive_expect_tx(&full_p[slot], bytes);
+                tma_load_3d(Pring + slot * L::p_slot, &tm_p, x0 / 2 - 2, r, 0, &full_p[slot]);
+                // periodic halos of the edge chunks (the main box reads zeros there)
+                if (edge_l) tma_load_3d(Hring + (slot * 2 + 0) * L::h_slot, &tm_h, W / 2 - 2, r, 0, &full_p[slot]);
+                if (edge_r) tma_load_3d(Hring + (slot * 2 + 1) * L::h_slot, &tm_h, 0, r, 0, &full_p[slot]);
+            }
+            return true;
+        };
+        auto pot = [&](int i) -> bool {                        // potentials + phenospace of local row i
+            const int slot = i % ER_NU;
+            if (i >= ER_NU && !mbar_wait_bounded(&empty_u[slot], ((i - ER_NU) / ER_NU) & 1)) return false;
+            const int r = r0 + i;
+            last_pot = i;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&full_u[slot], (KT + CT) * ER_CH * 4);
+                tma_load_3d(Uring + slot * L::u_slot, &tm_u, x0 / 2, r, 0, &full_u[slot]);
+                tma_load_3d(Aring + slot * L::a_slot, &tm_a, x0 / 2, r, 0, &full_u[slot]);
+            }
+            return true;
+        };
+        // issue in order of need: row i wants gene rows up to l = i + 2 and U/A row i
+        bool ok = nrows <= 0 || (genes(0) && genes(1));
+        for (int i = 0; ok && i < nrows; i++) ok = genes(i + 2) && pot(i);
+        if (!ok && lane == 0) {
+            blk_failed = 1;
+            atomicExch(status, kStatusWaitTimeout);
+        }
+        // on success no copy is left in flight: the consumers waited for all of them
+    } else {
+        // ------------------------------------------------ consumer warps
+        const int grp = warp / ER_WPG;
+        const int t = (warp % ER_WPG) * 32 + lane;       // column within the chunk
+        const bool edge_l = x0 == 0, edge_r = x0 + ER_CH == W;
+        const int x = x0 + t;
+        const float eps_p = p.eps_p, eps_u = p.eps_u;
+        const float sx = __ldg(&p.sin_x[x]), cx = __ldg(&p.cos_x[x]);
+        // gene row l = 0 is used by row 0 only: group 1 releases it up front
+        // so that its slot, like every other, collects one release per group
+        if (grp == 1 && lane == 0 && NPK > 0 && nrows > 0) mbar_arrive(&empty_p[0]);
+        for (int i = grp; i < nrows; i += ER_GROUPS) {
+            bool ok = true;
+            if (NPK > 0)
+                for (int l = i; l <= i + 2; l++) ok = ok && mbar_wait_bounded(&full_p[l % ER_NP], (l / ER_NP) & 1);
+            ok = ok && mbar_wait_bounded(&full_u[i % ER_NU], (i / ER_NU) & 1);
+            if (!ok) {
+                if (lane == 0) {
+                    blk_failed = 1;
+                    atomicExch(status, kStatusWaitTimeout);
+                }
+                break;
+            }
+            const int y = r0 + i;
+            const float* Pu = Pring + (size_t)(i % ER_NP) * L::p_slot;
+            float* Pcw = Pring + (size_t)((i + 1) % ER_NP) * L::p_slot;
+            const float* Pc = Pcw;
+            const float* Pd = Pring + (size_t)((i + 2) % ER_NP) * L::p_slot;
+            const float* Ur = Uring + (size_t)(i % ER_NU) * L::u_slot;
+            const float* Ar = Aring + (size_t)(i % ER_NU) * L::a_slot;
+            // The centre row's halo column beyond a world edge arrived in the
+            // halo slot; the one lane that reads it moves it into place.
+            if (NPK > 0 && p.maintain && ((edge_l && t == 0) || (edge_r && t == ER_CH - 1))) {
+                const int side = t == 0 ? 0 : 1;
+                const float* hs = Hring + (((i + 1) % ER_NP) * 2 + side) * L::h_slot;
+                for (int pk = 0; pk < NPK; pk++)
+                    Pcw[pk * ER_PW + (side == 0 ? 3 : 4 + ER_CH)] = hs[pk * 4 + (side == 0 ? 3 : 0)];
+                fence_proxy_async_shared();   // before the slot is refilled by TMA
+            }
+
+            float ph[NPK > 0 ? NPK : 1];
+            float pmin = 1.f;                  // min over the diffused genes
+            float tmin = 3.4e38f;              // min over the alpha tests (h g, or U)
+            float acc[CT];
+#pragma unroll
+            for (int c = 0; c < CT; c++) acc[c] = 0.f;
+#pragma unroll
+            for (int k = 0; k < KT; k++) {
+#pragma unroll
+                for (int pp = 0; pp < NP; pp++) {
+                    const int o = (pp * KT + k) * ER_PW + t + 4;
+                    float v;
+                    if (p.maintain) {
+                        // disk |d| <= 1 in the order (-1,0), (0,-1), (0,0), (0,1), (1,0)
+                        const float v0 = Pu[o], v1 = Pc[o - 1], v2 = Pc[o], v3 = Pc[o + 1], v4 = Pd[o];
+                        const float s = (((v0 + v1) + v2) + v3) + v4;
+                        const float n = (float)(v0 > eps_p) + (float)(v1 > eps_p) + (float)(v2 > eps_p) +
+                                        (float)(v3 > eps_p) + (float)(v4 > eps_p);
+                        v = __saturatef(s * rcp_approx(n));
+                        if (!EPS0) v = n > 0.f ? v : 0.f;
+                        pmin = fminf(pmin, v);
+                    } else {
+                        v = Pc[o];
+                    }
+                    ph[pp * KT + k] = v;
+                }
+                const float u = Ur[k * ER_CH + t];
+                const float m = PMU >= 0 ? ph[(PMU >= 0 ? PMU : 0) * KT + k] : p.kt.mu[k];
+                const float sg = PSG >= 0 ? ph[(PSG >= 0 ? PSG : 0) * KT + k] : p.kt.sigma[k];
+                const float hh = PH >= 0 ? ph[(PH >= 0 ? PH : 0) * KT + k] : p.kt.h[k];
+                const float z = (u - m) * rcp_approx(sg);
+                const float gk = sg > 0.f ? ex2_approx(-C_HALF_LOG2E * (z * z)) : 0.f;
+                tmin = fminf(tmin, p.alpha_on ? u : hh * gk);
+                const float G = p.growth_form == 0 ? fmaf(2.f * gk, hh, -hh) : hh * gk;
+                const int d = TOPO ? paper_dst(k) : p.kt.dst[k];
+#pragma unroll
+                for (int c = 0; c < CT; c++)
+                    if (c == d) acc[c] += G;
+            }
+            const bool alpha = !p.maintain || ((NPK == 0 || pmin > eps_p) && tmin > eps_u);
+            const unsigned gi = (unsigned)y * (unsigned)W + (unsigned)x;
+            const float sy = __ldg(&p.sin_y[y]), cy = __ldg(&p.cos_y[y]);
+#pragma unroll
+            for (int c = 0; c < CT; c++) {
+                const float an = __saturatef(Ar[c * ER_CH + t] + p.dt * (alpha ? acc[c] : p.acc0[c]));
+                p.A_out[(unsigned)c * N + gi] = an;
+                st[c * 5 + 0] += an;
+                st[c * 5 + 1] += an * sy;
+                st[c * 5 + 2] += an * cy;
+                st[c * 5 + 3] += an * sx;
+                st[c * 5 + 4] += an * cx;
+            }
+            if (p.alpha_out) p.alpha_out[gi] = alpha ? 1 : 0;
+            if (p.P_out) {
+                const bool keep = !p.maintain || alpha;
+#pragma unroll
+                for (int pk = 0; pk < NPK; pk++) p.P_out[(unsigned)pk * N + gi] = keep ? ph[pk] : 0.f;
+            }
+            // this warp is done with gene rows l = i, i + 1 and U/A row i
+            __syncwarp();
+            if (lane == 0) {
+                if (NPK > 0) {
+                    mbar_arrive(&empty_p[i % ER_NP]);
+                    mbar_arrive(&empty_p[(i + 1) % ER_NP]);
+                }
+                mbar_arrive(&empty_u[i % ER_NU]);
+            }
+        }
+    }
+
+    // Every warp reaches this point (all waits are bounded).  After a failure
+    // the producer gives the copies it issued last a bounded chance to land
+    // before the block exits.
+    __syncthreads();
+    if (blk_failed) {
+        if (warp == ER_CONSUMERS && lane == 0) {
+            for (int l = last_gene - (ER_NP - 1) < 0 ? 0 : last_gene - (ER_NP - 1); l <= last_gene; l++)
+                mbar_wait_bounded(&full_p[l % ER_NP], (l / ER_NP) & 1);
+            for (int i = last_pot - (ER_NU - 1) < 0 ? 0 : last_pot - (ER_NU - 1); i <= last_pot; i++)
+                mbar_wait_bounded(&full_u[i % ER_NU], (i / ER_NU) & 1);
+        }
+        return;
+    }
+    if (p.partials) {
+        if (warp < ER_CONSUMERS) {
+#pragma unroll
+            for (int v = 0; v < CT * 5; v++) {
+                float s = st[v];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+                if (lane == 0) red[warp][v] = s;
+            }
+        }
+        __syncthreads();
+        if (tid < CT * 5) {
+            double s = 0.0;
+            for (int w = 0; w < ER_CONSUMERS; w++) s += (double)red[w][tid];
+            p.partials[(size_t)blockIdx.x * CT * 5 + tid] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------ tensor maps
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+struct MapKey {
+    const void* base;
+    int W, H, planes, box_x, box_planes;
+    bool operator==(const MapKey& o) const
+    {
+        return base == o.base && W == o.W && H == o.H && planes == o.planes && box_x == o.box_x &&
+               box_planes == o.box_planes;
+    }
+};
+
+// A plane stack [planes][H][W] of floats viewed as (W/2 8-byte elements, H
+// rows, planes); boxes of box_x elements x 1 row x box_planes.  Encoded maps
+// are cached by argument (most recent first).
+bool plane_map(CUtensorMap* out, const float* base, int W, int H, int planes, int box_x, int box_planes)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<MapKey, CUtensorMap>> cache;
+    const MapKey key{base, W, H, planes, box_x, box_planes};
+    std::lock_guard<std::mutex> lock(mu);
+    for (size_t i = 0; i < cache.size(); i++)
+        if (cache[i].first == key) {
+            *out = cache[i].second;
+            return true;
+        }
+    auto fn = encode_fn();
+    if (!fn) return false;
+    CUtensorMap m;
+    const cuuint64_t dims[3] = {(cuuint64_t)W / 2, (cuuint64_t)H, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)W * H * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, 1, (cuuint32_t)box_planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float*>(base), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    cache.insert(cache.begin(), {key, m});
+    if (cache.size() > 32) cache.pop_back();
+    *out = m;
+    return true;
+}
+
+}  // namespace
+
+template <int KT, int CT, int LOC, int TOPO = 0>
+static cudaError_t launch_rows(const EpiParams& p, int num_sms, int* status, cudaStream_t s, int* n_blocks)
+{
+    using L = ErLayout<KT, CT, LOC>;
+    auto kern = p.eps_p == 0.f ? k_epilogue_rows<KT, CT, LOC, TOPO, 1> : k_epilogue_rows<KT, CT, LOC, TOPO, 0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ER_THREADS, L::bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int n_chunks = p.W / ER_CH;
+    int n_bands = (num_sms * per_sm) / n_chunks;
+    if (n_bands < 1) n_bands = 1;
+    if (n_bands > p.H) n_bands = p.H;
+    if (n_blocks) *n_blocks = n_chunks * n_bands;
+    CUtensorMap tp, tu, ta, th;
+    memset(&tp, 0, sizeof(tp));
+    memset(&th, 0, sizeof(th));
+    if (L::NPK > 0 && (!plane_map(&tp, p.P, p.W, p.H, L::NPK, ER_PW / 2, L::NPK) ||
+                       !plane_map(&th, p.P, p.W, p.H, L::NPK, 2, L::NPK)))
+        return cudaErrorInvalidValue;
+    if (!plane_map(&tu, p.U, p.W, p.H, KT, ER_CH / 2, KT) || !plane_map(&ta, p.A, p.W, p.H, CT, ER_CH / 2, CT))
+        return cudaErrorInvalidValue;
+    kern<<<n_chunks * n_bands, ER_THREADS, L::bytes, s>>>(p, tp, tu, ta, th, n_chunks, n_bands, status);
+    return cudaGetLastError();
+}
+
+bool epilogue_rows_supported(const EpiParams& p)
+{
+    if (p.W % ER_CH != 0 || (p.maintain && p.r_diff != 1)) return false;
+    // 32-bit site indexing of every plane
+    const long long N = (long long)p.H * p.W;
+    if (N * (p.n_p * p.kt.K > p.kt.K ? p.n_p * p.kt.K : p.kt.K) >= (1LL << 31) || N * p.kt.C >= (1LL << 31))
+        return false;
+    const int loc = (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
+    const int K = p.kt.K, C = p.kt.C;
+    return (K == 15 && C == 3 && (loc == 3 || loc == 0)) || (K == 1 && C == 1 && (loc == 3 || loc == 0));
+}
+
+cudaError_t launch_epilogue_rows(const EpiParams& p, int num_sms, int* status, cudaStream_t s, int* n_blocks)
+{
+    const int loc = (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
+    const int K = p.kt.K, C = p.kt.C;
+    bool paper = K == 15 && C == 3;
+    for (int k = 0; paper && k < K; k++) paper = p.kt.dst[k] == paper_dst(k);
+    if (paper && loc == 3) return launch_rows<15, 3, 3, 1>(p, num_sms, status, s, n_blocks);
+    if (paper && loc == 0) return launch_rows<15, 3, 0, 1>(p, num_sms, status, s, n_blocks);
+    if (K == 15 && C == 3 && loc == 3) return launch_rows<15, 3, 3>(p, num_sms, status, s, n_blocks);
+    if (K == 15 && C == 3 && loc == 0) return launch_rows<15, 3, 0>(p, num_sms, status, s, n_blocks);
+    if (K == 1 && C == 1 && loc == 3) return launch_rows<1, 1, 3>(p, num_sms, status, s, n_blocks);
+    if (K == 1 && C == 1 && loc == 0) return launch_rows<1, 1, 0>(p, num_sms, status, s, n_blocks);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lenia

@@ -41,6 +41,8 @@ struct lenia_ctx {
     float* d_A3 = nullptr;
     float* d_P3 = nullptr;
     float* d_stats = nullptr;
+    int* d_status = nullptr;               // device status word (bounded-wait failures)
+    int num_sms = 0;
     int n_part_blocks = 0;
     ConvParams cp;
     FftParams fp;
@@ -261,6 +263,13 @@ EpiParams epi_params(lenia_ctx* c)
     ep.eps_u = c->cfg.eps_u;
     ep.eps_p = c->cfg.eps_p;
     ep.kt = c->kt;
+    for (int ch = 0; ch < c->cfg.n_channels; ch++) {
+        float a0 = 0.f;
+        if (c->cfg.growth_form == LENIA_GROWTH_SIGNED && c->p_h < 0)
+            for (int k = 0; k < c->cfg.n_kernels; k++)
+                if (c->kd[k].dst_channel == ch) a0 -= c->kd[k].h;   // h (2*0 - 1), in kernel order
+        ep.acc0[ch] = a0;
+    }
     return ep;
 }
 
@@ -300,7 +309,12 @@ lenia_status step_impl(lenia_ctx* c, const float* A_in, const float* P_in, float
     int nb = 0;
     {
         ProfScope ps(c, KIND_EPI, s);
-        CUDA_OR_FAIL(c, launch_epilogue(ep, s, &nb));
+        const bool aligned = ((uintptr_t)ep.A % 16 == 0) && ((uintptr_t)ep.U % 16 == 0) &&
+                             (!ep.P || (uintptr_t)ep.P % 16 == 0);
+        if (aligned && epilogue_rows_supported(ep))
+            CUDA_OR_FAIL(c, launch_epilogue_rows(ep, c->num_sms, c->d_status, s, &nb));
+        else
+            CUDA_OR_FAIL(c, launch_epilogue(ep, s, &nb));
     }
     if (stats_out) {
         ProfScope ps(c, KIND_STATS_F, s);
@@ -342,7 +356,7 @@ void lenia_destroy(lenia_ctx* c)
     if (!c) return;
     void* ptrs[] = {c->d_w, c->d_w_off, c->d_yr, c->d_yr_off, c->d_S, c->d_twM, c->d_twW, c->d_twH,
                     c->d_Ahat, c->d_Uhat, c->d_U, c->d_partials, c->d_trig, c->d_A2, c->d_P2,
-                    c->d_A3, c->d_P3, c->d_stats};
+                    c->d_A3, c->d_P3, c->d_stats, c->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -432,7 +446,15 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         ALLOC(c->d_P3, nP);
     }
     ALLOC(c->d_stats, (size_t)C * 3);
-    c->n_part_blocks = epilogue_blocks(H, W);
+    ALLOC(c->d_status, 1);
+    CK_INIT(cudaMemset(c->d_status, 0, sizeof(int)));
+    {
+        int dev = 0;
+        CK_INIT(cudaGetDevice(&dev));
+        CK_INIT(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    // stats records: the larger of the tiled epilogue's blocks and one per SM-resident CTA
+    c->n_part_blocks = std::max(epilogue_blocks(H, W), 8 * c->num_sms);
     ALLOC(c->d_partials, (size_t)c->n_part_blocks * C * 5);
 
     // circular-mean tables
@@ -628,6 +650,20 @@ lenia_status lenia_update_from_potentials(lenia_ctx* c, const float* A_in, const
     return step_impl(c, A_in, P_in, A_out, P_out, nullptr, alpha_out, U_in, (cudaStream_t)stream);
 }
 
+lenia_status lenia_check(lenia_ctx* c, void* stream)
+{
+    if (!c) return LENIA_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+    int st = 0;
+    CUDA_OR_FAIL(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        CUDA_OR_FAIL(c, cudaMemset(c->d_status, 0, sizeof(int)));
+        return fail(c, LENIA_ETIMEOUT, "a device-side wait gave up (status " + std::to_string(st) + ")");
+    }
+    return LENIA_OK;
+}
+
 lenia_status lenia_step_host(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
                              float* stats_out, void* stream)
 {
@@ -647,8 +683,7 @@ lenia_status lenia_step_host(lenia_ctx* c, const float* A_in, const float* P_in,
     if (stats_out)
         CUDA_OR_FAIL(c, cudaMemcpyAsync(stats_out, c->d_stats, c->cfg.n_channels * 3 * sizeof(float),
                                         cudaMemcpyDeviceToHost, s));
-    CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
-    return LENIA_OK;
+    return lenia_check(c, stream);
 }
 
 lenia_status lenia_profile_start(lenia_ctx* c, int32_t max_launches)

@@ -33,6 +33,9 @@ struct EpiParams {
     int p_mu, p_sigma, p_h;    // plane index of each localized gene or -1
     int maintain, growth_form, alpha_on, r_diff;
     float dt, eps_u, eps_p;
+    // growth sum of channel c at sites where alpha = 0 (genes masked to zero):
+    // -sum_{dst(k)=c} h_k for the signed form with global h, else 0
+    float acc0[kMaxChannels];
     KernelTable kt;
 };
 
@@ -78,6 +81,8 @@ cudaError_t launch_stats_final(const double* partials, int n_blocks, int C, int 
                                float* out, cudaStream_t s);
 cudaError_t launch_spectra(const double* Kd, int R, int H, int W, const double* cos_H,
                            const double* cos_W, double* T_scratch, float* S_out, cudaStream_t s);
+bool epilogue_rows_supported(const EpiParams& p);
+cudaError_t launch_epilogue_rows(const EpiParams& p, int num_sms, int* status, cudaStream_t s, int* n_blocks);
 bool fft_size_supported(int H, int W);
 int epilogue_blocks(int H, int W);
 

@@ -7,6 +7,7 @@
 
 namespace lenia {
 
+// Periodic index for any integer i (modulo; used off the per-site hot loops).
 __device__ __forceinline__ int wrapi(int i, int n)
 {
     int r = i % n;
@@ -90,67 +91,187 @@ cudaError_t launch_direct_conv(const ConvParams& p, int max_R, cudaStream_t s)
 //   P' = P^ . alpha;
 //   A'_c = clip(A_c + dt sum_{k: dst(k)=c} h'_k G(g'_k), 0, 1) with the
 //     masked genes (g' = 0 and localized h' = 0 where alpha = 0) and
-//     G = 2g - 1 (signed) or g (paper form).
-// Block: 32 x 8 sites, one per thread.  Optional per-block stats partials
-// (sum A, sum A sin/cos of the y and x angles) in a fixed reduction order.
-constexpr int EP_TX = 32, EP_TY = 8;
+//     G = 2g - 1 (signed) or g (paper form).  Where alpha = 0 the sum is the
+//     per-channel constant acc0 computed on the host.
+// Optional per-block stats partials: sum A, sum A sin/cos(2 pi y/H), sum A
+// sin/cos(2 pi x/W) per channel, reduced in a fixed order.
+constexpr int EP_TX = 32, EP_TY = 8, EP_RY = 4;    // block: 32 x 8 threads, 4 rows each
 
-template <int KT, int CT, int NPT>
-__global__ void __launch_bounds__(256) k_epilogue(EpiParams p)
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Block reduction of per-thread stats (CA channels x 5 sums) into one record
+// per block; every thread of the block must call it.
+template <int CA>
+__device__ __forceinline__ void block_stats(const float* st, int C, double* partials)
 {
-    const int K = KT ? KT : p.kt.K;
-    const int C = CT ? CT : p.kt.C;
-    const int n_p = NPT >= 0 ? NPT : p.n_p;
-    constexpr int KA = KT ? KT : kMaxKernels;
-    constexpr int CA = CT ? CT : kMaxChannels;
-    constexpr int PA = (NPT >= 0 ? NPT : kMaxPlanes) * KA;
-
-    const int x = blockIdx.x * EP_TX + threadIdx.x;
-    const int y = blockIdx.y * EP_TY + threadIdx.y;
-    const bool valid = x < p.W && y < p.H;
-    const size_t N = (size_t)p.H * p.W;
-    const size_t i = (size_t)y * p.W + x;
-
-    float acc[CA];
+    __shared__ float red[EP_TY][kMaxChannels * 5];
+    const int lane = threadIdx.x;
 #pragma unroll
-    for (int c = 0; c < CA; c++) acc[c] = 0.f;
-    float anew[CA];
+    for (int v = 0; v < CA * 5; v++) {
+        if (v >= C * 5) break;
+        float t = st[v];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+        if (lane == 0) red[threadIdx.y][v] = t;
+    }
+    __syncthreads();
+    const int tid = threadIdx.y * EP_TX + threadIdx.x;
+    if (tid < C * 5) {
+        double s = 0.0;
+        for (int w = 0; w < EP_TY; w++) s += (double)red[w][tid];
+        const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        partials[blk * C * 5 + tid] = s;
+    }
+}
 
-    if (valid) {
-        float ph[PA > 0 ? PA : 1];
+// Fast path: diffusion radius 1 (the 5-site plus), compile-time kernel count,
+// channel count and gene layout.  Each thread owns one column x and rows
+// y0 + 8 j (j < EP_RY); wrapped neighbour indices are formed once per row.
+template <int KT, int CT, int LOC>
+__global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
+{
+    constexpr int NP = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
+    constexpr int PMU = (LOC & 1) ? 0 : -1;
+    constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
+    constexpr int PH = (LOC & 4) ? NP - 1 : -1;
+    constexpr int NPK = NP * KT;
+    const int H = p.H, W = p.W;
+    const size_t N = (size_t)H * W;
+    const int x = blockIdx.x * EP_TX + threadIdx.x;
+    const bool xin = x < W;
+    const int xc = xin ? x : W - 1;
+    const int xm = xc == 0 ? W - 1 : xc - 1;
+    const int xp = xc == W - 1 ? 0 : xc + 1;
+    const float eps_p = p.eps_p, eps_u = p.eps_u;
+
+    float st[CT * 5];
+#pragma unroll
+    for (int v = 0; v < CT * 5; v++) st[v] = 0.f;
+
+    for (int j = 0; j < EP_RY; j++) {
+        const int y = blockIdx.y * (EP_TY * EP_RY) + j * EP_TY + threadIdx.y;
+        if (y >= H) break;
+        const size_t rc = (size_t)y * W;
+        const size_t ru = (size_t)(y == 0 ? H - 1 : y - 1) * W;
+        const size_t rd = (size_t)(y == H - 1 ? 0 : y + 1) * W;
+        const size_t i = rc + xc;
+
+        float ph[NPK > 0 ? NPK : 1];
+        bool alpha = true;
+#pragma unroll
+        for (int pk = 0; pk < NPK; pk++) {
+            const float* pl = p.P + (size_t)pk * N;
+            if (p.maintain) {
+                // disk |d| <= 1 in the order (-1,0), (0,-1), (0,0), (0,1), (1,0)
+                const float v0 = __ldg(pl + ru + xc);
+                const float v1 = __ldg(pl + rc + xm);
+                const float v2 = __ldg(pl + rc + xc);
+                const float v3 = __ldg(pl + rc + xp);
+                const float v4 = __ldg(pl + rd + xc);
+                const float s = (((v0 + v1) + v2) + v3) + v4;
+                const int n = (v0 > eps_p) + (v1 > eps_p) + (v2 > eps_p) + (v3 > eps_p) + (v4 > eps_p);
+                const float v = n > 0 ? fminf(fmaxf(s / (float)n, 0.f), 1.f) : 0.f;
+                alpha = alpha && (v > eps_p);
+                ph[pk] = v;
+            } else {
+                ph[pk] = __ldg(pl + i);
+            }
+        }
+        float acc[CT];
+#pragma unroll
+        for (int c = 0; c < CT; c++) acc[c] = 0.f;
+#pragma unroll
+        for (int k = 0; k < KT; k++) {
+            const float u = __ldg(&p.U[(size_t)k * N + i]);
+            const float m = PMU >= 0 ? ph[(PMU >= 0 ? PMU : 0) * KT + k] : p.kt.mu[k];
+            const float sg = PSG >= 0 ? ph[(PSG >= 0 ? PSG : 0) * KT + k] : p.kt.sigma[k];
+            const float hh = PH >= 0 ? ph[(PH >= 0 ? PH : 0) * KT + k] : p.kt.h[k];
+            float gk = 0.f;
+            if (sg > 0.f) {
+                const float z = (u - m) / sg;
+                gk = expf(-0.5f * z * z);
+            }
+            if (p.maintain) alpha = alpha && ((p.alpha_on ? u : hh * gk) > eps_u);
+            const float G = p.growth_form == 0 ? hh * (2.f * gk - 1.f) : hh * gk;
+            const int d = p.kt.dst[k];
+#pragma unroll
+            for (int c = 0; c < CT; c++)
+                if (c == d) acc[c] += G;
+        }
+        if (!p.maintain) alpha = true;
+        if (xin) {
+#pragma unroll
+            for (int c = 0; c < CT; c++) {
+                const float a = __ldg(&p.A[(size_t)c * N + i]) + p.dt * (alpha ? acc[c] : p.acc0[c]);
+                const float an = fminf(fmaxf(a, 0.f), 1.f);
+                p.A_out[(size_t)c * N + i] = an;
+                if (p.partials) {
+                    const float sy = __ldg(&p.sin_y[y]), cy = __ldg(&p.cos_y[y]);
+                    const float sx = __ldg(&p.sin_x[x]), cx = __ldg(&p.cos_x[x]);
+                    st[c * 5 + 0] += an;
+                    st[c * 5 + 1] += an * sy;
+                    st[c * 5 + 2] += an * cy;
+                    st[c * 5 + 3] += an * sx;
+                    st[c * 5 + 4] += an * cx;
+                }
+            }
+            if (p.P_out) {
+#pragma unroll
+                for (int pk = 0; pk < NPK; pk++)
+                    p.P_out[(size_t)pk * N + i] = (p.maintain && !alpha) ? 0.f : ph[pk];
+            }
+            if (p.alpha_out) p.alpha_out[i] = alpha ? 1 : 0;
+        }
+    }
+    if (p.partials) block_stats<CT>(st, CT, p.partials);
+}
+
+// General path: any diffusion radius, kernel count, channel count and gene
+// layout (runtime loops; per-site arrays may live in local memory).
+__global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
+{
+    const int K = p.kt.K, C = p.kt.C, n_p = p.n_p;
+    const int H = p.H, W = p.W;
+    const size_t N = (size_t)H * W;
+    const int x = blockIdx.x * EP_TX + threadIdx.x;
+    const bool xin = x < W;
+    const int xc = xin ? x : W - 1;
+    const int r = p.r_diff;
+    float st[kMaxChannels * 5];
+    for (int v = 0; v < kMaxChannels * 5; v++) st[v] = 0.f;
+
+    for (int j = 0; j < EP_RY; j++) {
+        const int y = blockIdx.y * (EP_TY * EP_RY) + j * EP_TY + threadIdx.y;
+        if (y >= H) break;
+        const size_t i = (size_t)y * W + xc;
+        float ph[kMaxPlanes * kMaxKernels];
         bool alpha = true;
         const int npk = n_p * K;
-#pragma unroll
-        for (int pk = 0; pk < PA; pk++) {
-            if (pk >= npk) break;
+        for (int pk = 0; pk < npk; pk++) {
             const float* pl = p.P + (size_t)pk * N;
             float v;
             if (p.maintain) {
                 float s = 0.f;
                 int cnt = 0;
-                const int r = p.r_diff;
                 for (int dy = -r; dy <= r; dy++) {
-                    const float* row = pl + (size_t)wrapi(y + dy, p.H) * p.W;
+                    const float* row = pl + (size_t)wrap1(y + dy, H) * W;
                     for (int dx = -r; dx <= r; dx++) {
                         if (dy * dy + dx * dx > r * r) continue;
-                        const float q = __ldg(&row[wrapi(x + dx, p.W)]);
+                        const float q = __ldg(&row[wrap1(xc + dx, W)]);
                         s += q;
                         cnt += q > p.eps_p;
                     }
                 }
-                v = 0.f;
-                if (cnt > 0) v = fminf(fmaxf(s / (float)cnt, 0.f), 1.f);
+                v = cnt > 0 ? fminf(fmaxf(s / (float)cnt, 0.f), 1.f) : 0.f;
                 alpha = alpha && (v > p.eps_p);
             } else {
                 v = __ldg(&pl[i]);
             }
             ph[pk] = v;
         }
-        float g[KA];
-        float hk[KA];
-#pragma unroll
-        for (int k = 0; k < KA; k++) {
-            if (k >= K) break;
+        float acc[kMaxChannels];
+        for (int c = 0; c < C; c++) acc[c] = 0.f;
+        for (int k = 0; k < K; k++) {
             const float u = __ldg(&p.U[(size_t)k * N + i]);
             const float m = p.p_mu >= 0 ? ph[p.p_mu * K + k] : p.kt.mu[k];
             const float sg = p.p_sigma >= 0 ? ph[p.p_sigma * K + k] : p.kt.sigma[k];
@@ -160,86 +281,50 @@ __global__ void __launch_bounds__(256) k_epilogue(EpiParams p)
                 const float z = (u - m) / sg;
                 gk = expf(-0.5f * z * z);
             }
-            if (p.maintain) {
-                const float t = p.alpha_on ? u : hh * gk;
-                alpha = alpha && (t > p.eps_u);
-            }
-            g[k] = gk;
-            hk[k] = hh;
+            if (p.maintain) alpha = alpha && ((p.alpha_on ? u : hh * gk) > p.eps_u);
+            acc[p.kt.dst[k]] += p.growth_form == 0 ? hh * (2.f * gk - 1.f) : hh * gk;
         }
         if (!p.maintain) alpha = true;
-#pragma unroll
-        for (int k = 0; k < KA; k++) {
-            if (k >= K) break;
-            const float gm = alpha ? g[k] : 0.f;
-            const float hm = (p.p_h >= 0 && !alpha) ? 0.f : hk[k];
-            const float G = p.growth_form == 0 ? hm * (2.f * gm - 1.f) : hm * gm;
-            const int d = p.kt.dst[k];
-#pragma unroll
-            for (int c = 0; c < CA; c++)
-                if (c == d) acc[c] += G;
-        }
-#pragma unroll
-        for (int c = 0; c < CA; c++) {
-            if (c >= C) break;
-            const float a = __ldg(&p.A[(size_t)c * N + i]) + p.dt * acc[c];
-            anew[c] = fminf(fmaxf(a, 0.f), 1.f);
-            p.A_out[(size_t)c * N + i] = anew[c];
-        }
-        if (p.P_out) {
-#pragma unroll
-            for (int pk = 0; pk < PA; pk++) {
-                if (pk >= npk) break;
-                p.P_out[(size_t)pk * N + i] = (p.maintain && !alpha) ? 0.f : ph[pk];
+        if (xin) {
+            for (int c = 0; c < C; c++) {
+                const float a = __ldg(&p.A[(size_t)c * N + i]) + p.dt * (alpha ? acc[c] : p.acc0[c]);
+                const float an = fminf(fmaxf(a, 0.f), 1.f);
+                p.A_out[(size_t)c * N + i] = an;
+                if (p.partials) {
+                    st[c * 5 + 0] += an;
+                    st[c * 5 + 1] += an * __ldg(&p.sin_y[y]);
+                    st[c * 5 + 2] += an * __ldg(&p.cos_y[y]);
+                    st[c * 5 + 3] += an * __ldg(&p.sin_x[x]);
+                    st[c * 5 + 4] += an * __ldg(&p.cos_x[x]);
+                }
             }
-        }
-        if (p.alpha_out) p.alpha_out[i] = alpha ? 1 : 0;
-    }
-
-    if (p.partials) {
-        // five sums per channel, reduced warp by warp then across warps
-        __shared__ float red[EP_TY][kMaxChannels * 5];
-        const int lane = threadIdx.x;
-        for (int c = 0; c < C; c++) {
-            float a = valid ? anew[c] : 0.f;
-            float sy = valid ? __ldg(&p.sin_y[y]) : 0.f, cy = valid ? __ldg(&p.cos_y[y]) : 0.f;
-            float sx = valid ? __ldg(&p.sin_x[x]) : 0.f, cx = valid ? __ldg(&p.cos_x[x]) : 0.f;
-            float v[5] = {a, a * sy, a * cy, a * sx, a * cx};
-#pragma unroll
-            for (int j = 0; j < 5; j++) {
-                float t = v[j];
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-                if (lane == 0) red[threadIdx.y][c * 5 + j] = t;
-            }
-        }
-        __syncthreads();
-        const int tid = threadIdx.y * EP_TX + threadIdx.x;
-        if (tid < C * 5) {
-            double s = 0.0;
-            for (int w = 0; w < EP_TY; w++) s += (double)red[w][tid];
-            const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-            p.partials[blk * C * 5 + tid] = s;
+            if (p.P_out)
+                for (int pk = 0; pk < npk; pk++)
+                    p.P_out[(size_t)pk * N + i] = (p.maintain && !alpha) ? 0.f : ph[pk];
+            if (p.alpha_out) p.alpha_out[i] = alpha ? 1 : 0;
         }
     }
+    if (p.partials) block_stats<kMaxChannels>(st, C, p.partials);
 }
 
 int epilogue_blocks(int H, int W)
 {
-    return ((W + EP_TX - 1) / EP_TX) * ((H + EP_TY - 1) / EP_TY);
+    return ((W + EP_TX - 1) / EP_TX) * ((H + EP_TY * EP_RY - 1) / (EP_TY * EP_RY));
 }
 
 cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks)
 {
-    dim3 grid((p.W + EP_TX - 1) / EP_TX, (p.H + EP_TY - 1) / EP_TY);
+    dim3 grid((p.W + EP_TX - 1) / EP_TX, (p.H + EP_TY * EP_RY - 1) / (EP_TY * EP_RY));
     dim3 block(EP_TX, EP_TY);
     if (n_blocks) *n_blocks = grid.x * grid.y;
     const int K = p.kt.K, C = p.kt.C;
-    if (K == 1 && C == 1 && p.n_p == 2) k_epilogue<1, 1, 2><<<grid, block, 0, s>>>(p);
-    else if (K == 1 && C == 1 && p.n_p == 0) k_epilogue<1, 1, 0><<<grid, block, 0, s>>>(p);
-    else if (K == 15 && C == 3 && p.n_p == 2) k_epilogue<15, 3, 2><<<grid, block, 0, s>>>(p);
-    else if (K == 15 && C == 3 && p.n_p == 0) k_epilogue<15, 3, 0><<<grid, block, 0, s>>>(p);
-    else k_epilogue<0, 0, -1><<<grid, block, 0, s>>>(p);
+    const int loc = (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
+    const bool r1 = p.r_diff == 1 || !p.maintain;
+    if (r1 && K == 15 && C == 3 && loc == 3) k_epilogue_r1<15, 3, 3><<<grid, block, 0, s>>>(p);
+    else if (r1 && K == 15 && C == 3 && loc == 0) k_epilogue_r1<15, 3, 0><<<grid, block, 0, s>>>(p);
+    else if (r1 && K == 1 && C == 1 && loc == 3) k_epilogue_r1<1, 1, 3><<<grid, block, 0, s>>>(p);
+    else if (r1 && K == 1 && C == 1 && loc == 0) k_epilogue_r1<1, 1, 0><<<grid, block, 0, s>>>(p);
+    else k_epilogue_generic<<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -252,62 +337,58 @@ __global__ void __launch_bounds__(256) k_stats_partials(const float* A, int C, i
                                                         const float* sin_x, const float* cos_x,
                                                         double* partials)
 {
-    __shared__ float red[EP_TY][kMaxChannels * 5];
     const int x = blockIdx.x * EP_TX + threadIdx.x;
-    const int y = blockIdx.y * EP_TY + threadIdx.y;
-    const bool valid = x < W && y < H;
-    const int lane = threadIdx.x;
-    for (int c = 0; c < C; c++) {
-        float a = valid ? __ldg(&A[((size_t)c * H + y) * W + x]) : 0.f;
-        float sy = valid ? __ldg(&sin_y[y]) : 0.f, cy = valid ? __ldg(&cos_y[y]) : 0.f;
-        float sx = valid ? __ldg(&sin_x[x]) : 0.f, cx = valid ? __ldg(&cos_x[x]) : 0.f;
-        float v[5] = {a, a * sy, a * cy, a * sx, a * cx};
-#pragma unroll
-        for (int j = 0; j < 5; j++) {
-            float t = v[j];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-            if (lane == 0) red[threadIdx.y][c * 5 + j] = t;
+    float st[kMaxChannels * 5];
+    for (int v = 0; v < kMaxChannels * 5; v++) st[v] = 0.f;
+    if (x < W) {
+        for (int j = 0; j < EP_RY; j++) {
+            const int y = blockIdx.y * (EP_TY * EP_RY) + j * EP_TY + threadIdx.y;
+            if (y >= H) break;
+            for (int c = 0; c < C; c++) {
+                const float a = __ldg(&A[((size_t)c * H + y) * W + x]);
+                st[c * 5 + 0] += a;
+                st[c * 5 + 1] += a * __ldg(&sin_y[y]);
+                st[c * 5 + 2] += a * __ldg(&cos_y[y]);
+                st[c * 5 + 3] += a * __ldg(&sin_x[x]);
+                st[c * 5 + 4] += a * __ldg(&cos_x[x]);
+            }
         }
     }
-    __syncthreads();
-    const int tid = threadIdx.y * EP_TX + threadIdx.x;
-    if (tid < C * 5) {
-        double s = 0.0;
-        for (int w = 0; w < EP_TY; w++) s += (double)red[w][tid];
-        const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-        partials[blk * C * 5 + tid] = s;
-    }
+    block_stats<kMaxChannels>(st, C, partials);
 }
 
 cudaError_t launch_stats_partials(const float* A, int C, int H, int W, const float* sin_y,
                                   const float* cos_y, const float* sin_x, const float* cos_x,
                                   double* partials, cudaStream_t s, int* n_blocks)
 {
-    dim3 grid((W + EP_TX - 1) / EP_TX, (H + EP_TY - 1) / EP_TY);
+    dim3 grid((W + EP_TX - 1) / EP_TX, (H + EP_TY * EP_RY - 1) / (EP_TY * EP_RY));
     if (n_blocks) *n_blocks = grid.x * grid.y;
     k_stats_partials<<<grid, dim3(EP_TX, EP_TY), 0, s>>>(A, C, H, W, sin_y, cos_y, sin_x, cos_x, partials);
     return cudaGetLastError();
 }
 
-// Final reduction: one block; thread t sums blocks t, t+256, ... in FP64, then
-// a fixed tree.  out[c] = (mass, centre y, centre x), centres from the
-// circular mean atan2(sum A sin, sum A cos) scaled to [0, n).
-__global__ void __launch_bounds__(256) k_stats_final(const double* partials, int n_blocks, int C,
-                                                     int H, int W, float* out)
+// Final reduction, one block of 1024 threads: for each of the C*5 sums,
+// 64 threads stride over the block records in FP64 (fixed order), then two
+// fixed shuffle trees and one add.  out[c] = (mass, centre y, centre x),
+// centres from the circular mean atan2(sum A sin, sum A cos) scaled to [0, n).
+__global__ void __launch_bounds__(1024) k_stats_final(const double* partials, int n_blocks, int C,
+                                                      int H, int W, float* out)
 {
-    __shared__ double red[256];
+    __shared__ double part[32];
     __shared__ double tot[kMaxChannels * 5];
-    for (int v = 0; v < C * 5; v++) {
+    const int nv = C * 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v0 = 0; v0 < nv; v0 += 16) {
+        const int v = v0 + (threadIdx.x >> 6);     // 16 values per pass, 64 threads each
+        const int stripe = threadIdx.x & 63;
         double s = 0.0;
-        for (int b = threadIdx.x; b < n_blocks; b += 256) s += partials[(size_t)b * C * 5 + v];
-        red[threadIdx.x] = s;
+        if (v < nv)
+            for (int b = stripe; b < n_blocks; b += 64) s += partials[(size_t)b * nv + v];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) part[warp] = s;
         __syncthreads();
-        for (int w = 128; w > 0; w >>= 1) {
-            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) tot[v] = red[0];
+        if (threadIdx.x < 16 && v0 + threadIdx.x < nv)
+            tot[v0 + threadIdx.x] = part[2 * threadIdx.x] + part[2 * threadIdx.x + 1];
         __syncthreads();
     }
     if (threadIdx.x < C) {
@@ -327,7 +408,7 @@ __global__ void __launch_bounds__(256) k_stats_final(const double* partials, int
 cudaError_t launch_stats_final(const double* partials, int n_blocks, int C, int H, int W,
                                float* out, cudaStream_t s)
 {
-    k_stats_final<<<1, 256, 0, s>>>(partials, n_blocks, C, H, W, out);
+    k_stats_final<<<1, 1024, 0, s>>>(partials, n_blocks, C, H, W, out);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_potentials", "lenia_update_from_potentials", "lenia_step_host",
            "lenia_kernel_weights", "lenia_conv_path", "lenia_launches_per_step",
            "lenia_last_error", "lenia_status_string", "lenia_destroy", "lenia_profile_start",
-           "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc")
+           "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check")
 PROFILE_KINDS = 7
 
 
@@ -108,6 +108,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_profile_kind_name.restype = ctypes.c_char_p
     lib.lenia_stats_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp]
     lib.lenia_stats_noalloc.restype = st
+    lib.lenia_check.argtypes = [vp, vp]
+    lib.lenia_check.restype = st
     lib.lenia_destroy.argtypes = [vp]
     lib.lenia_destroy.restype = None
     if path is None:
@@ -183,6 +185,10 @@ def lenia_stats_noalloc(A, n_channels, height, width, out, stream=None):
                                     _stream(stream))
     if st != LENIA_OK:
         raise LeniaError(st, f"lenia_stats_noalloc: {load().lenia_status_string(st).decode()}")
+
+
+def lenia_check(ctx, stream=None):
+    _check(ctx, load().lenia_check(ctx, _stream(stream)))
 
 
 def lenia_potentials(ctx, A_in, U_out, stream=None):

@@ -70,8 +70,22 @@ def w_ragged():
     return inputs.multi_channel(H=72, W=100, R=5, patch=20, n_geno=3, live=True)
 
 
+def w_c3_wide():
+    # width a multiple of 256: the streaming epilogue (bands of 1-2 rows here)
+    return inputs.multi_channel(H=128, W=512, R=18, patch=40, n_geno=4, live=True)
+
+
+def w_c2_wide():
+    return inputs.localized_single_channel(H=64, W=768, R=12, patch=32, n_geno=4, live=True)
+
+
+def w_c5_wide():
+    return inputs.global_multi_channel(H=64, W=256, R=13, patch=24)
+
+
 WORLDS = {"c1": w_c1, "c2s": w_c2_small, "c3s": w_c3_small, "c3rect": w_c3_rect,
-          "c5s": w_c5_small, "ragged": w_ragged}
+          "c5s": w_c5_small, "ragged": w_ragged, "c3w": w_c3_wide, "c2w": w_c2_wide,
+          "c5w": w_c5_wide}
 
 
 # ----------------------------------------------------------------- kernels
@@ -125,7 +139,7 @@ def test_potentials_uniform_and_impulse():
 
 # ------------------------------------------- epilogue from identical inputs
 
-@pytest.mark.parametrize("name", ["c2s", "c3s", "ragged"])
+@pytest.mark.parametrize("name", ["c2s", "c3s", "ragged", "c3w", "c2w"])
 def test_update_from_identical_potentials(name):
     """Both sides take the same FP32 potentials: alpha and P' agree exactly up
     to rounding; A' differs only by FP32 rounding."""
@@ -155,7 +169,8 @@ def test_update_from_identical_potentials(name):
 
 @pytest.mark.parametrize("name,path", [("c1", 1), ("c1", 2), ("c2s", 1), ("c2s", 2), ("c3s", 1),
                                        ("c3s", 2), ("c3rect", 1), ("c5s", 1), ("c5s", 2),
-                                       ("ragged", 2)])
+                                       ("ragged", 2), ("c3w", 1), ("c3w", 2), ("c2w", 2),
+                                       ("c5w", 1)])
 def test_step_parity(name, path):
     w = WORLDS[name]()
     A1, P1, U, al, margin = _oracle_step(w)
@@ -260,6 +275,19 @@ def test_rollout_equals_repeated_steps_and_is_deterministic():
         lenia.lenia_rollout(ctx, Ar2, Pr2, 3)
         torch.cuda.synchronize()
         assert torch.equal(Ar, Ar2) and torch.equal(Pr, Pr2)
+    finally:
+        lenia.lenia_destroy(ctx)
+
+
+def test_check_reports_ok_after_steps():
+    torch = torch_mod()
+    w = w_c3_wide()
+    cfg, ks = lenia.config_from_world(w, 1)
+    ctx = lenia.lenia_init(cfg, ks)
+    try:
+        A, P = to_dev(w.A), to_dev(w.P)
+        lenia.lenia_rollout(ctx, A, P, 4)
+        lenia.lenia_check(ctx)                    # raises on a device-side timeout
     finally:
         lenia.lenia_destroy(ctx)
 
