@@ -4,16 +4,17 @@
 //
 // Three passes over the world, each a set of shared-memory FFTs:
 //   rows_r2c  : real row FFT of every channel row (length-W real signal as a
-//               length-W/2 complex FFT plus the standard even/odd split).
-//               Output row: W/2 complex values; element 0 packs the two real
+//               length-W/2 complex FFT plus the standard even/odd split),
+//               NB rows per block.  Spectra are stored column-major,
+//               [channel][kx][y], kx < W/2; element kx = 0 packs the two real
 //               values X[0] (DC) and X[W/2] (Nyquist) as (re, im).
-//   cols_conv : for a tile of TC spectrum columns of one channel, forward
-//               column FFT, then for each kernel reading that channel the
-//               product with the real kernel spectrum and the inverse column
-//               FFT, written per kernel.  Column 0 holds the packed DC and
-//               Nyquist columns (both real along y), which are separated,
-//               multiplied by their own spectra and re-packed in one step.
-//   rows_c2r  : inverse real row FFT of every kernel row -> U_k.
+//   cols_conv : one spectrum column per block: forward column FFT, then for
+//               each kernel reading that channel the product with the real
+//               kernel spectrum and the inverse column FFT, stored
+//               [kernel][kx][y].  Column 0 holds the packed DC and Nyquist
+//               columns (both real along y), which are separated, multiplied
+//               by their own spectra and re-packed in one step.
+//   rows_c2r  : inverse real row FFT of every kernel row -> U_k, NB rows per block.
 // Forward and inverse transforms are unnormalised; 1/(H W) is folded into
 // the stored kernel spectra.
 #include "fft_core.cuh"
@@ -37,13 +38,14 @@ __global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
     fft_run<M, NB, T, false, false>(p.tw_M, ld_g, sld, sst, sst);
 
     // X[k] = E[k] + w_W^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i
+    // Output column kx holds rows y0 .. y0 + NB - 1 contiguously (b fastest).
+    float2* outc = p.Ahat + (size_t)c * M * p.H + y0;
     for (int u = threadIdx.x; u < NB * (M / 2 + 1); u += T) {
-        const int b = u / (M / 2 + 1);
-        const int k = u % (M / 2 + 1);
-        float2* out = p.Ahat + ((size_t)c * p.H + y0 + b) * M;
+        const int b = u % NB;
+        const int k = u / NB;
         if (k == 0) {
             float2 z = sm[b * SZ + swz(0)];
-            out[0] = make_float2(z.x + z.y, z.x - z.y);
+            outc[b] = make_float2(z.x + z.y, z.x - z.y);
             continue;
         }
         const float2 zk = sm[b * SZ + swz(k)];
@@ -52,13 +54,13 @@ __global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
             float2 e = cscale(cadd(zk, cconj(zm)), 0.5f);
             float2 d = cscale(csub(zk, cconj(zm)), 0.5f);
             float2 o = make_float2(d.y, -d.x);               // d / i
-            out[k] = cadd(e, cmul(__ldg(&p.tw_W[k]), o));
+            outc[(size_t)k * p.H + b] = cadd(e, cmul(__ldg(&p.tw_W[k]), o));
         }
         if (k != M - k) {
             float2 e = cscale(cadd(zm, cconj(zk)), 0.5f);
             float2 d = cscale(csub(zm, cconj(zk)), 0.5f);
             float2 o = make_float2(d.y, -d.x);
-            out[M - k] = cadd(e, cmul(__ldg(&p.tw_W[M - k]), o));
+            outc[(size_t)(M - k) * p.H + b] = cadd(e, cmul(__ldg(&p.tw_W[M - k]), o));
         }
     }
 }
@@ -72,28 +74,40 @@ __global__ void __launch_bounds__(T) k_rows_c2r(FftParams p)
     const int k = blockIdx.y;
     const int y0 = blockIdx.x * NB;
     const int W = 2 * M;
-    const float2* in = p.Uhat + ((size_t)k * p.H + y0) * M;
+    const float2* in = p.Uhat + (size_t)k * M * p.H + y0;     // column-major [k][kx][y]
 
     // Z'[k] = (X[k] + conj X[M-k]) + i w_W^{-k} (X[k] - conj X[M-k])  (= 2 Z[k])
-    for (int u = threadIdx.x; u < NB * (M / 2 + 1); u += T) {
-        const int b = u / (M / 2 + 1);
-        const int q = u % (M / 2 + 1);
-        const float2* row = in + (size_t)b * M;
+    // All of a thread's input pairs are loaded before any is combined.
+    constexpr int PAIRS = NB * (M / 2 + 1);
+    constexpr int PER = (PAIRS + T - 1) / T;
+    float2 xk[PER], xm[PER];
+#pragma unroll
+    for (int it = 0; it < PER; it++) {
+        const int u = threadIdx.x + it * T;
+        if (u < PAIRS) {
+            const int b = u % NB, q = u / NB;
+            xk[it] = __ldg(&in[(size_t)q * p.H + b]);
+            xm[it] = __ldg(&in[(size_t)(q == 0 ? 0 : M - q) * p.H + b]);
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < PER; it++) {
+        const int u = threadIdx.x + it * T;
+        if (u >= PAIRS) break;
+        const int b = u % NB, q = u / NB;
         if (q == 0) {
-            float2 x = __ldg(&row[0]);                       // (DC, Nyquist)
+            const float2 x = xk[it];                          // (DC, Nyquist)
             sm[b * SZ + swz(0)] = make_float2(x.x + x.y, x.x - x.y);
             continue;
         }
-        const float2 xk = __ldg(&row[q]);
-        const float2 xm = __ldg(&row[M - q]);
         {
-            float2 s = cadd(xk, cconj(xm));
-            float2 d = cmulc(csub(xk, cconj(xm)), __ldg(&p.tw_W[q]));
+            float2 s = cadd(xk[it], cconj(xm[it]));
+            float2 d = cmulc(csub(xk[it], cconj(xm[it])), __ldg(&p.tw_W[q]));
             sm[b * SZ + swz(q)] = make_float2(s.x - d.y, s.y + d.x);   // s + i d
         }
         if (q != M - q) {
-            float2 s = cadd(xm, cconj(xk));
-            float2 d = cmulc(csub(xm, cconj(xk)), __ldg(&p.tw_W[M - q]));
+            float2 s = cadd(xm[it], cconj(xk[it]));
+            float2 d = cmulc(csub(xm[it], cconj(xk[it])), __ldg(&p.tw_W[M - q]));
             sm[b * SZ + swz(M - q)] = make_float2(s.x - d.y, s.y + d.x);
         }
     }
@@ -106,49 +120,48 @@ __global__ void __launch_bounds__(T) k_rows_c2r(FftParams p)
 }
 
 // ------------------------------------------------------- columns: fwd, x K^, inv
-template <int H, int TC, int T>
-__global__ void __launch_bounds__(T) k_cols_conv(FftParams p)
+template <int H, int T>
+__global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(FftParams p)
 {
     extern __shared__ float2 sm[];
-    constexpr int SZ = swz_size(H * TC);
+    constexpr int SZ = swz_size(H);
     float2* F = sm;
     float2* Wk = sm + SZ;
     const int c = blockIdx.y;
-    const int kx0 = blockIdx.x * TC;
+    const int kx = blockIdx.x;
     const int M = p.W / 2;
     const int HS = H / 2 + 1;
 
-    const float2* src = p.Ahat + (size_t)c * H * M + kx0;
-    auto ld_g = [&](int b, int i) { return __ldg(&src[(size_t)i * M + b]); };
-    auto sldF = [&](int b, int i) { return F[swz(i * TC + b)]; };
-    auto sstF = [&](int b, int i, float2 v) { F[swz(i * TC + b)] = v; };
-    fft_run<H, TC, T, false, true>(p.tw_H, ld_g, sldF, sstF, sstF);
+    const float2* src = p.Ahat + ((size_t)c * M + kx) * H;
+    auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
+    auto sldF = [&](int, int i) { return F[swz(i)]; };
+    auto sstF = [&](int, int i, float2 v) { F[swz(i)] = v; };
+    fft_run<H, 1, T, false, false>(p.tw_H, ld_g, sldF, sstF, sstF);
 
     const int nk = p.kcount[c];
     for (int t = 0; t < nk; t++) {
         const int k = p.klist[c][t];
         const float* Sk = p.S + (size_t)k * (M + 1) * HS;
-        auto ld_mul = [&](int b, int i) {
-            const int kx = kx0 + b;
+        auto ld_mul = [&](int, int i) {
             const int ky = i;
             const int kyr = ky <= H / 2 ? ky : H - ky;
-            const float2 f = F[swz(i * TC + b)];
+            const float2 f = F[swz(i)];
             if (kx == 0) {
                 // packed (DC, Nyquist) column: out = f a + conj(f(-ky)) b
                 const float s0 = __ldg(&Sk[kyr]);
                 const float sn = __ldg(&Sk[(size_t)M * HS + kyr]);
-                const float2 fm = cconj(F[swz(((H - ky) & (H - 1)) * TC + b)]);
+                const float2 fm = cconj(F[swz((H - ky) & (H - 1))]);
                 const float a = 0.5f * (s0 + sn), bb = 0.5f * (s0 - sn);
                 return make_float2(f.x * a + fm.x * bb, f.y * a + fm.y * bb);
             }
             const float s = __ldg(&Sk[(size_t)kx * HS + kyr]);
             return cscale(f, s);
         };
-        float2* dst = p.Uhat + (size_t)k * H * M + kx0;
-        auto sldW = [&](int b, int i) { return Wk[swz(i * TC + b)]; };
-        auto sstW = [&](int b, int i, float2 v) { Wk[swz(i * TC + b)] = v; };
-        auto st_g = [&](int b, int i, float2 v) { dst[(size_t)i * M + b] = v; };
-        fft_run<H, TC, T, true, true>(p.tw_H, ld_mul, sldW, sstW, st_g);
+        float2* dst = p.Uhat + ((size_t)k * M + kx) * H;
+        auto sldW = [&](int, int i) { return Wk[swz(i)]; };
+        auto sstW = [&](int, int i, float2 v) { Wk[swz(i)] = v; };
+        auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
+        fft_run<H, 1, T, true, false>(p.tw_H, ld_mul, sldW, sstW, st_g);
     }
 }
 
@@ -156,9 +169,11 @@ __global__ void __launch_bounds__(T) k_cols_conv(FftParams p)
 template <int M>
 static cudaError_t rows_launch(const FftParams& p, cudaStream_t s, bool inverse)
 {
-    // 4096 complex values per block (NB rows), one radix-16 butterfly per thread
-    constexpr int NB = (4096 / M) < 64 ? (4096 / M) : 64;
-    constexpr int T = (NB * M / 16) < 256 ? (NB * M / 16) : 256;
+    // at least 8 rows per block (64-byte runs of the column-major spectra) and
+    // at least 4096 complex values; one radix-16 butterfly per thread
+    constexpr int NB0 = (4096 / M) > 8 ? (4096 / M) : 8;
+    constexpr int NB = NB0 < 64 ? NB0 : 64;
+    constexpr int T = (NB * M / 16) < 512 ? (NB * M / 16) : 512;
     const size_t smem = (size_t)NB * swz_size(M) * sizeof(float2);
     if (p.H % NB) return cudaErrorInvalidValue;
     if (!inverse) {
@@ -176,14 +191,12 @@ static cudaError_t rows_launch(const FftParams& p, cudaStream_t s, bool inverse)
 template <int H>
 static cudaError_t cols_launch(const FftParams& p, cudaStream_t s)
 {
-    constexpr int TC = H >= 4096 ? 2 : 4;
-    constexpr int T = (H * TC / 16) >= 512 ? 512 : (H * TC / 16 >= 128 ? H * TC / 16 : 128);
-    const size_t smem = 2 * (size_t)swz_size(H * TC) * sizeof(float2);
+    constexpr int T = H / 16 >= 64 ? H / 16 : 64;
+    const size_t smem = 2 * (size_t)swz_size(H) * sizeof(float2);
     const int M = p.W / 2;
-    if (M % TC) return cudaErrorInvalidValue;
-    auto kern = k_cols_conv<H, TC, T>;
+    auto kern = k_cols_conv<H, T>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<dim3(M / TC, p.C), T, smem, s>>>(p);
+    kern<<<dim3(M, p.C), T, smem, s>>>(p);
     return cudaGetLastError();
 }
 

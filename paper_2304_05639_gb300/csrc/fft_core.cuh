@@ -15,8 +15,11 @@
 // (global memory, or a spectral product) and the last pass can write through
 // one, which saves two shared-memory round trips per transform.
 //
-// Twiddles come from FP32 tables built in FP64 on the host and rounded once:
-// tw[m] = exp(-2 pi i m / N), m < N.
+// Twiddles come from FP32 tables built in FP64 on the host and rounded once.
+// Each pass with Ns > 1 has its own table laid out [r - 1][k]:
+// tw[(r - 1) Ns + k] = exp(-2 pi i r k / (Ns R)), so the lanes of a warp
+// (consecutive k) read consecutive entries.  The passes' tables are stored
+// back to back in plan order (fft_tw_offset).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -111,19 +114,28 @@ struct DFT<1, INV> {
 
 __host__ __device__ constexpr int fft_radix(int remaining) { return remaining >= 16 ? 16 : remaining; }
 
+// Offset of the twiddle table of the pass with sub-transform size NS in the
+// concatenated per-pass tables of a length-N transform; fft_tw_offset(N, N)
+// is the total length.
+__host__ __device__ constexpr int fft_tw_offset(int N, int NS)
+{
+    int off = 0;
+    for (int ns = 1; ns < NS && ns < N; ns *= fft_radix(N / ns))
+        if (ns > 1) off += (fft_radix(N / ns) - 1) * ns;
+    return off;
+}
+
 // One Stockham pass over NB independent length-N transforms held by a block of
 // T threads.  Element i of transform b is read with ld(b, i) and written with
 // st(b, i, v).  BFAST: consecutive threads take consecutive transforms b
 // (interleaved layouts), else consecutive butterflies j.
 template <int N, int R, int NB, int T, bool INV, bool BFAST, class LD, class ST>
-__device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ tw, LD ld, ST st)
+__device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp, LD ld, ST st)
 {
     constexpr int NBF = NB * (N / R);
     constexpr int PER = (NBF + T - 1) / T;
     float2 v[PER][R];
     const int tstep = N / R;
-    // exponent step for w^{rk}: table index r*k*(N/(Ns R))
-    const int tws = N / (Ns * R);
 #pragma unroll
     for (int p = 0; p < PER; p++) {
         const int u = threadIdx.x + p * T;
@@ -136,7 +148,7 @@ __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ tw, 
             if (Ns > 1) {
 #pragma unroll
                 for (int r = 1; r < R; r++) {
-                    float2 w = __ldg(&tw[r * k * tws]);
+                    float2 w = __ldg(&twp[(r - 1) * Ns + k]);
                     v[p][r] = INV ? cmulc(v[p][r], w) : cmul(v[p][r], w);
                 }
             }
@@ -168,15 +180,16 @@ __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_fir
     constexpr int R = fft_radix(N / NS);
     constexpr bool first = (NS == 1);
     constexpr bool last = (NS * R == N);
+    const float2* twp = tw + fft_tw_offset(N, NS);
     if constexpr (first && last) {
-        fft_pass<N, R, NB, T, INV, BFAST>(NS, tw, ld_first, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, ld_first, st_last);
     } else if constexpr (first) {
-        fft_pass<N, R, NB, T, INV, BFAST>(NS, tw, ld_first, sst);
+        fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, ld_first, sst);
         fft_run<N, NB, T, INV, BFAST, NS * R>(tw, ld_first, sld, sst, st_last);
     } else if constexpr (last) {
-        fft_pass<N, R, NB, T, INV, BFAST>(NS, tw, sld, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, sld, st_last);
     } else {
-        fft_pass<N, R, NB, T, INV, BFAST>(NS, tw, sld, sst);
+        fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, sld, sst);
         fft_run<N, NB, T, INV, BFAST, NS * R>(tw, ld_first, sld, sst, st_last);
     }
 }

@@ -181,6 +181,26 @@ lenia_status dalloc(lenia_ctx* c, T** p, size_t n)
     return LENIA_OK;
 }
 
+// Per-pass Stockham twiddle tables of a length-n transform (radix-16 passes
+// and a final smaller radix), each laid out [r - 1][k]:
+// exp(-2 pi i r k / (Ns R)), computed in FP64 and rounded once.
+std::vector<float2> pass_twiddles(int n)
+{
+    std::vector<float2> t;
+    for (int ns = 1; ns < n;) {
+        const int R = n / ns >= 16 ? 16 : n / ns;
+        if (ns > 1)
+            for (int r = 1; r < R; r++)
+                for (int k = 0; k < ns; k++) {
+                    const double a = kTwoPi * (double)r * k / ((double)ns * R);
+                    t.push_back(make_float2((float)cos(a), (float)-sin(a)));
+                }
+        ns *= R;
+    }
+    if (t.empty()) t.push_back(make_float2(1.f, 0.f));
+    return t;
+}
+
 std::vector<float2> twiddles(int n, int count)
 {
     std::vector<float2> t((size_t)count);
@@ -522,7 +542,7 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         ALLOC(c->d_Ahat, (size_t)C * H * M);
         ALLOC(c->d_Uhat, (size_t)K * H * M);
         ALLOC(c->d_S, (size_t)K * (M + 1) * HS);
-        std::vector<float2> twM = twiddles(M, M), twW = twiddles(W, M + 1), twH = twiddles(H, H);
+        std::vector<float2> twM = pass_twiddles(M), twW = twiddles(W, M + 1), twH = pass_twiddles(H);
         ALLOC(c->d_twM, twM.size());
         ALLOC(c->d_twW, twW.size());
         ALLOC(c->d_twH, twH.size());

@@ -56,13 +56,13 @@ struct ConvParams {
 // Spectral (FFT) convolution.
 struct FftParams {
     const float* A;            // [C][H][W]
-    float2* Ahat;              // [C][H][M] row spectra, M = W/2, element 0 packs (DC, Nyquist)
-    float2* Uhat;              // [K][H][M] per-kernel column-inverse spectra, same packing
+    float2* Ahat;              // [C][M][H] row spectra, column-major, M = W/2, kx = 0 packs (DC, Nyquist)
+    float2* Uhat;              // [K][M][H] per-kernel column-inverse spectra, same layout and packing
     float* U;                  // [K][H][W] potentials
     const float* S;            // [K][M+1][H/2+1] real kernel spectra / (H W)
-    const float2* tw_M;        // exp(-2 pi i m / M), m < M   (row transforms)
+    const float2* tw_M;        // per-pass twiddle tables of the length-M row transforms
     const float2* tw_W;        // exp(-2 pi i m / W), m <= M  (real-signal packing)
-    const float2* tw_H;        // exp(-2 pi i m / H), m < H   (column transforms)
+    const float2* tw_H;        // per-pass twiddle tables of the length-H column transforms
     int H, W, C, K;
     int kcount[kMaxChannels];
     int klist[kMaxChannels][kMaxKernels];
