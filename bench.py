@@ -34,6 +34,24 @@ WORKLOAD = "lenia 2048x2048, 3 channels, 15 shell kernels R=18, localized mu/sig
 ALG_BYTES_PER_SITE = 3 * 4 * 2 + 30 * 4 * 2
 
 
+def _traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or
+    None when the kernel's sources changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "epilogue_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("kernel") != kernel:
+            return None
+        h = hashlib.sha256()
+        for src in d["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return int(d["dram_bytes_per_launch"]) if h.hexdigest() == d["sources_sha256"] else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -256,8 +274,11 @@ def run_ours(args):
     # dominant kernel: the largest share of the timed region
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
     dom_ms = dom[1][0] / max(1, dom[1][1])
-    alg_bytes = ALG_BYTES_PER_SITE * sites
+    # the epilogue moves all of the method's bytes (A and P in and out); the
+    # FFT passes move only implementation intermediates
+    alg_bytes = ALG_BYTES_PER_SITE * sites if dom[0] == "epilogue" else 0
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    traffic = _traffic(dom[0]) if args.size == 2048 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -270,7 +291,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (A + P = 551 MB per world)"},
         "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None,
+                     "traffic": traffic,
+                     "traffic_gbs": (traffic / (dom_ms / 1e3) / 1e9) if traffic else None,
                      "alg_bytes_per_site": ALG_BYTES_PER_SITE,
                      "step_frac": (ALG_BYTES_PER_SITE * sites * args.steps / (t_max / 1e3) / 1e9) / hbm},
         "kernels_ms": {k: {"avg_ms": v[0] / max(1, v[1]), "launches": v[1],

@@ -27,7 +27,7 @@ template <int M, int T, int NB>
 __global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
 {
     extern __shared__ float2 sm[];
-    constexpr int SZ = swz_size(M);
+    constexpr int SZ = row_pitch(M);
     const int c = blockIdx.y;
     const int y0 = blockIdx.x * NB;
     const int W = 2 * M;
@@ -70,7 +70,7 @@ template <int M, int T, int NB>
 __global__ void __launch_bounds__(T) k_rows_c2r(FftParams p)
 {
     extern __shared__ float2 sm[];
-    constexpr int SZ = swz_size(M);
+    constexpr int SZ = row_pitch(M);
     const int k = blockIdx.y;
     const int y0 = blockIdx.x * NB;
     const int W = 2 * M;
@@ -174,7 +174,7 @@ static cudaError_t rows_launch(const FftParams& p, cudaStream_t s, bool inverse)
     constexpr int NB0 = (4096 / M) > 8 ? (4096 / M) : 8;
     constexpr int NB = NB0 < 64 ? NB0 : 64;
     constexpr int T = (NB * M / 16) < 512 ? (NB * M / 16) : 512;
-    const size_t smem = (size_t)NB * swz_size(M) * sizeof(float2);
+    const size_t smem = (size_t)NB * row_pitch(M) * sizeof(float2);
     if (p.H % NB) return cudaErrorInvalidValue;
     if (!inverse) {
         auto kern = k_rows_r2c<M, T, NB>;

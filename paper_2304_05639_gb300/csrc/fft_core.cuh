@@ -198,5 +198,9 @@ __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_fir
 // power-of-two strides of the first passes off a single bank.
 __device__ __forceinline__ int swz(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int swz_size(int n) { return n + (n >> 4) + 1; }
+// Pitch of one transform's row when several rows are walked row-fastest
+// (8 rows x 4 columns per warp): a pitch of 4 (mod 16) float2 puts the rows
+// on distinct bank groups.
+__host__ __device__ constexpr int row_pitch(int n) { return (swz_size(n) + 15) / 16 * 16 + 4; }
 
 }  // namespace lenia
