@@ -98,7 +98,8 @@ typedef struct {
  *   eps_p: gene threshold of Delta_same / Delta_all (strict '>').
  *   r_diff: radius of the diffusion disk |d|_2 <= r_diff, 0..8.
  *   conv_path: LENIA_CONV_* (AUTO picks FFT for power-of-two worlds).
- *   max_rollout_steps, ckpt_every: reserved for the adjoint (set 0). */
+ *   max_rollout_steps, ckpt_every: adjoint buffers for lenia_backward (0 = none;
+ *     global genes only); states kept every ckpt_every steps (0 -> 8). */
 typedef struct {
     int32_t height, width, n_channels, n_kernels;
     float dt;
@@ -134,9 +135,25 @@ LENIA_API lenia_status lenia_step(lenia_ctx* ctx, const float* A_in, const float
 LENIA_API lenia_status lenia_rollout(lenia_ctx* ctx, float* A, float* P, int32_t n_steps,
                            float* stats_out, void* stream);
 
-/* Adjoint of a rollout (reserved): returns LENIA_ENOTSUP in this build. */
+/* Adjoint of an n_steps rollout from A0 for worlds with global genes
+ * (localized == 0; no gene maps, so no alpha decisions).  Needs a context made
+ * with max_rollout_steps >= n_steps; states are checkpointed every
+ * ckpt_every steps (default 8) and recomputed segment by segment.
+ * Given gA_T = dL/dA_T (device, [C][H][W]) it writes gA0 = dL/dA_0 (device,
+ * nullable) and g_genes = [K][3] (device, nullable): dL/dmu_k, dL/dsigma_k,
+ * dL/dh_k.  Per step (Section 2.1 update, Algorithm 2 growth and clip):
+ * clip subgradient 1 iff 0 < pre-clip < 1, growth derivative, and the
+ * transposed convolution, which for the point-symmetric K~ is the same
+ * convolution.  P0 must be NULL.  Returns LENIA_ENOTSUP when the context has
+ * no adjoint buffers or has gene maps. */
 LENIA_API lenia_status lenia_backward(lenia_ctx* ctx, const float* A0, const float* P0, int32_t n_steps,
                             const float* gA_T, float* gA0, float* g_genes, void* stream);
+
+/* Replace the global growth genes: genes is a HOST array [K][3] of
+ * (mu, sigma, h) per kernel (sigma > 0 unless sigma is localized).  The
+ * kernels' shapes and spectra are unchanged.  Takes effect for work
+ * enqueued after the call. */
+LENIA_API lenia_status lenia_set_genes(lenia_ctx* ctx, const float* genes);
 
 /* Mass, circular-mean centre y, centre x of each channel of A: out is a
  * device array of C*3 floats.  Sums run in a fixed order (deterministic). */

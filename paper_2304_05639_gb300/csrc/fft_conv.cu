@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
             const float s = __ldg(&Sk[(size_t)kx * HS + kyr]);
             return cscale(f, s);
         };
-        float2* dst = p.Uhat + ((size_t)k * M + kx) * H;
+        float2* dst = p.Uhat + ((size_t)(k - p.k_base) * M + kx) * H;
         auto sldW = [&](int, int i) { return Wk[swz(i)]; };
         auto sstW = [&](int, int i, float2 v) { Wk[swz(i)] = v; };
         auto st_g = [&](int, int i, float2 v) { dst[i] = v; };

@@ -48,6 +48,19 @@ struct lenia_ctx {
     FftParams fp;
     KernelTable kt;
     std::string err;
+    // adjoint (lenia_backward): checkpoints, segment states, gradients
+    bool adj = false;
+    int ckpt = 0, max_steps = 0;
+    float* d_ckpt = nullptr;               // [n_ckpt][C][H][W]
+    float* d_seg = nullptr;                // [max(ckpt, 2)][C][H][W]
+    float* d_gA[2] = {nullptr, nullptr};
+    float* d_gpre = nullptr;
+    float* d_gU = nullptr;
+    float* d_V = nullptr;
+    double* d_gene_part = nullptr;
+    double* d_gene_acc = nullptr;
+    float2* d_Ahat_t = nullptr;            // spectra of up to 8 gradient planes (transposed conv)
+    float2* d_Uhat_t = nullptr;
     // optional per-launch timing (lenia_profile_start / lenia_profile_stop)
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -344,6 +357,47 @@ lenia_status step_impl(lenia_ctx* c, const float* A_in, const float* P_in, float
     return LENIA_OK;
 }
 
+// V_k = K~_k (x) gU_k for every kernel (the transpose of the convolution;
+// the kernels are point symmetric), in groups of at most kMaxChannels
+// kernels that the forward convolution kernels treat as channels.
+lenia_status transposed_conv(lenia_ctx* c, const float* gU, float* V, cudaStream_t s)
+{
+    const int K = c->cfg.n_kernels;
+    for (int k0 = 0; k0 < K; k0 += kMaxChannels) {
+        const int g = std::min(kMaxChannels, K - k0);
+        if (c->path == LENIA_CONV_FFT) {
+            FftParams fp = c->fp;
+            fp.A = gU + (size_t)k0 * c->N;
+            fp.U = V + (size_t)k0 * c->N;
+            fp.Ahat = c->d_Ahat_t;
+            fp.Uhat = c->d_Uhat_t;
+            fp.C = g;
+            fp.K = g;
+            for (int j = 0; j < kMaxChannels; j++) fp.kcount[j] = 0;
+            for (int j = 0; j < g; j++) {
+                fp.kcount[j] = 1;
+                fp.klist[j][0] = k0 + j;
+            }
+            fp.k_base = k0;   // the group's spectra and outputs are planes 0 .. g-1
+            CUDA_OR_FAIL(c, launch_fft_rows_r2c(fp, s));
+            CUDA_OR_FAIL(c, launch_fft_cols(fp, s));
+            CUDA_OR_FAIL(c, launch_fft_rows_c2r(fp, s));
+        } else {
+            ConvParams cp = c->cp;
+            cp.A = gU + (size_t)k0 * c->N;
+            cp.U = V;   // kernel k writes plane k
+            cp.C = g;
+            for (int j = 0; j < kMaxChannels; j++) cp.kcount[j] = 0;
+            for (int j = 0; j < g; j++) {
+                cp.kcount[j] = 1;
+                cp.klist[j][0] = k0 + j;
+            }
+            CUDA_OR_FAIL(c, launch_direct_conv(cp, c->max_R, s));
+        }
+    }
+    return LENIA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -376,7 +430,9 @@ void lenia_destroy(lenia_ctx* c)
     if (!c) return;
     void* ptrs[] = {c->d_w, c->d_w_off, c->d_yr, c->d_yr_off, c->d_S, c->d_twM, c->d_twW, c->d_twH,
                     c->d_Ahat, c->d_Uhat, c->d_U, c->d_partials, c->d_trig, c->d_A2, c->d_P2,
-                    c->d_A3, c->d_P3, c->d_stats, c->d_status};
+                    c->d_A3, c->d_P3, c->d_stats, c->d_status, c->d_ckpt, c->d_seg, c->d_gA[0],
+                    c->d_gA[1], c->d_gpre, c->d_gU, c->d_V, c->d_gene_part, c->d_gene_acc,
+                    c->d_Ahat_t, c->d_Uhat_t};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -589,6 +645,28 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         memcpy(c->fp.kcount, kcount, sizeof(kcount));
         memcpy(c->fp.klist, klist, sizeof(klist));
     }
+    // adjoint buffers (global genes only; gene maps make alpha decisions)
+    if (cfg->max_rollout_steps > 0 && c->n_p == 0 && !cfg->maintain_genes) {
+        c->adj = true;
+        c->max_steps = cfg->max_rollout_steps;
+        c->ckpt = cfg->ckpt_every > 0 ? cfg->ckpt_every : 8;
+        const int n_ckpt = (c->max_steps + c->ckpt - 1) / c->ckpt;
+        const size_t nA1 = c->N * C;
+        ALLOC(c->d_ckpt, (size_t)n_ckpt * nA1);
+        ALLOC(c->d_seg, (size_t)std::max(c->ckpt, 2) * nA1);
+        ALLOC(c->d_gA[0], nA1);
+        ALLOC(c->d_gA[1], nA1);
+        ALLOC(c->d_gpre, nA1);
+        ALLOC(c->d_gU, c->N * K);
+        ALLOC(c->d_V, c->N * K);
+        ALLOC(c->d_gene_part, (size_t)adjoint_blocks(H, W) * K * 3);
+        ALLOC(c->d_gene_acc, (size_t)K * 3);
+        if (path == LENIA_CONV_FFT) {
+            const int g = std::min(K, kMaxChannels);
+            ALLOC(c->d_Ahat_t, (size_t)g * (W / 2) * H);
+            ALLOC(c->d_Uhat_t, (size_t)g * (W / 2) * H);
+        }
+    }
     CK_INIT(cudaStreamSynchronize(s));
     CK_INIT(cudaGetLastError());
 #undef ALLOC
@@ -632,10 +710,91 @@ lenia_status lenia_rollout(lenia_ctx* c, float* A, float* P, int32_t n_steps, fl
     return LENIA_OK;
 }
 
-lenia_status lenia_backward(lenia_ctx* c, const float*, const float*, int32_t, const float*, float*, float*,
-                            void*)
+lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int32_t n_steps, const float* gA_T,
+                            float* gA0, float* g_genes, void* stream)
 {
-    return fail(c, LENIA_ENOTSUP, "lenia_backward is not implemented in this build");
+    if (!c) return LENIA_EINVAL;
+    if (!c->adj)
+        return fail(c, LENIA_ENOTSUP,
+                    "lenia_backward needs global genes and a context made with max_rollout_steps > 0");
+    if (!A0 || !gA_T) return fail(c, LENIA_EINVAL, "A0 and gA_T must be non-null");
+    if (P0) return fail(c, LENIA_EINVAL, "P0 must be NULL: the adjoint covers global genes only");
+    if (n_steps < 1 || n_steps > c->max_steps) return fail(c, LENIA_EINVAL, "n_steps must be 1..max_rollout_steps");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int C = c->cfg.n_channels, K = c->cfg.n_kernels, L = c->ckpt;
+    const size_t nA = c->N * C;
+    auto ckpt = [&](int j) { return c->d_ckpt + (size_t)j * nA; };
+    auto seg = [&](int j) { return c->d_seg + (size_t)j * nA; };
+
+    // forward pass, keeping the states at multiples of the checkpoint interval
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(ckpt(0), A0, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    const float* prev = ckpt(0);
+    for (int t = 0; t + 1 < n_steps; t++) {
+        float* dst = ((t + 1) % L == 0) ? ckpt((t + 1) / L) : seg((t + 1) & 1);
+        lenia_status st = step_impl(c, prev, nullptr, dst, nullptr, nullptr, nullptr, nullptr, s);
+        if (st != LENIA_OK) return st;
+        prev = dst;
+    }
+    // backward, segment by segment from the last: recompute the segment's
+    // states from its checkpoint, then apply the step adjoint in reverse
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_gene_acc, 0, (size_t)K * 3 * sizeof(double), s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_gA[0], gA_T, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    int cur = 0;
+    const int n_seg = (n_steps + L - 1) / L;
+    for (int sg = n_seg - 1; sg >= 0; sg--) {
+        const int s0 = sg * L, s1 = std::min(n_steps, s0 + L);
+        for (int j = 1; j < s1 - s0; j++) {
+            lenia_status st = step_impl(c, j == 1 ? ckpt(sg) : seg(j - 1), nullptr, seg(j), nullptr, nullptr,
+                                        nullptr, nullptr, s);
+            if (st != LENIA_OK) return st;
+        }
+        for (int t = s1 - 1; t >= s0; t--) {
+            const float* At = t == s0 ? ckpt(sg) : seg(t - s0);
+            lenia_status st = potentials(c, At, c->d_U, s);
+            if (st != LENIA_OK) return st;
+            AdjParams ap;
+            memset(&ap, 0, sizeof(ap));
+            ap.A = At;
+            ap.U = c->d_U;
+            ap.gA_next = c->d_gA[cur];
+            ap.gpre = c->d_gpre;
+            ap.gU = c->d_gU;
+            ap.V = c->d_V;
+            ap.gA_out = c->d_gA[cur ^ 1];
+            ap.gene_partials = c->d_gene_part;
+            ap.gene_acc = c->d_gene_acc;
+            ap.H = c->cfg.height;
+            ap.W = c->cfg.width;
+            ap.growth_form = c->cfg.growth_form;
+            ap.dt = c->cfg.dt;
+            ap.kt = c->kt;
+            CUDA_OR_FAIL(c, launch_adjoint_epilogue(ap, s));
+            st = transposed_conv(c, c->d_gU, c->d_V, s);
+            if (st != LENIA_OK) return st;
+            CUDA_OR_FAIL(c, launch_adjoint_gather(ap, s));
+            cur ^= 1;
+        }
+    }
+    if (gA0) CUDA_OR_FAIL(c, cudaMemcpyAsync(gA0, c->d_gA[cur], nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    if (g_genes) CUDA_OR_FAIL(c, launch_adjoint_gene_out(c->d_gene_acc, K * 3, g_genes, s));
+    return LENIA_OK;
+}
+
+lenia_status lenia_set_genes(lenia_ctx* c, const float* genes)
+{
+    if (!c || !genes) return LENIA_EINVAL;
+    const int K = c->cfg.n_kernels;
+    for (int k = 0; k < K; k++) {
+        const float mu = genes[3 * k], sg = genes[3 * k + 1], h = genes[3 * k + 2];
+        if (!isfinite(mu) || !isfinite(sg) || !isfinite(h)) return fail(c, LENIA_EINVAL, "genes must be finite");
+        if (!(c->cfg.localized & LENIA_LOC_SIGMA) && !(sg > 0.f)) return fail(c, LENIA_EINVAL, "sigma must be > 0");
+    }
+    for (int k = 0; k < K; k++) {
+        c->kd[k].mu = c->kt.mu[k] = genes[3 * k];
+        c->kd[k].sigma = c->kt.sigma[k] = genes[3 * k + 1];
+        c->kd[k].h = c->kt.h[k] = genes[3 * k + 2];
+    }
+    return LENIA_OK;
 }
 
 lenia_status lenia_stats(lenia_ctx* c, const float* A, float* out, void* stream)

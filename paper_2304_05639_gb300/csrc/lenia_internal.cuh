@@ -64,8 +64,25 @@ struct FftParams {
     const float2* tw_W;        // exp(-2 pi i m / W), m <= M  (real-signal packing)
     const float2* tw_H;        // per-pass twiddle tables of the length-H column transforms
     int H, W, C, K;
+    int k_base;                // the column pass writes Uhat plane k - k_base (0 for the forward step)
     int kcount[kMaxChannels];
     int klist[kMaxChannels][kMaxKernels];
+};
+
+// Adjoint of one step with global genes.
+struct AdjParams {
+    const float* A;            // step input A_t [C][H][W]
+    const float* U;            // potentials of A_t [K][H][W]
+    const float* gA_next;      // dL/dA_{t+1} [C][H][W]
+    float* gpre;               // clip-masked dL/dA_{t+1} [C][H][W]
+    float* gU;                 // dL/dU [K][H][W]
+    const float* V;            // K~_k (x) gU_k [K][H][W]
+    float* gA_out;             // dL/dA_t [C][H][W]
+    double* gene_partials;     // [blocks][K][3]
+    double* gene_acc;          // [K][3]: d/dmu, d/dsigma, d/dh
+    int H, W, growth_form;
+    float dt;
+    KernelTable kt;
 };
 
 // Launchers (return the cudaError_t of the launch).
@@ -81,6 +98,10 @@ cudaError_t launch_stats_final(const double* partials, int n_blocks, int C, int 
                                float* out, cudaStream_t s);
 cudaError_t launch_spectra(const double* Kd, int R, int H, int W, const double* cos_H,
                            const double* cos_W, double* T_scratch, float* S_out, cudaStream_t s);
+int adjoint_blocks(int H, int W);
+cudaError_t launch_adjoint_epilogue(const AdjParams& p, cudaStream_t s);
+cudaError_t launch_adjoint_gather(const AdjParams& p, cudaStream_t s);
+cudaError_t launch_adjoint_gene_out(const double* gene_acc, int nv, float* out, cudaStream_t s);
 bool epilogue_rows_supported(const EpiParams& p);
 cudaError_t launch_epilogue_rows(const EpiParams& p, int num_sms, int* status, cudaStream_t s, int* n_blocks);
 bool fft_size_supported(int H, int W);

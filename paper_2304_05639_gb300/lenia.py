@@ -25,7 +25,7 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_potentials", "lenia_update_from_potentials", "lenia_step_host",
            "lenia_kernel_weights", "lenia_conv_path", "lenia_launches_per_step",
            "lenia_last_error", "lenia_status_string", "lenia_destroy", "lenia_profile_start",
-           "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check")
+           "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes")
 PROFILE_KINDS = 7
 
 
@@ -108,6 +108,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_profile_kind_name.restype = ctypes.c_char_p
     lib.lenia_stats_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp]
     lib.lenia_stats_noalloc.restype = st
+    lib.lenia_set_genes.argtypes = [vp, vp]
+    lib.lenia_set_genes.restype = st
     lib.lenia_check.argtypes = [vp, vp]
     lib.lenia_check.restype = st
     lib.lenia_destroy.argtypes = [vp]
@@ -187,6 +189,12 @@ def lenia_stats_noalloc(A, n_channels, height, width, out, stream=None):
         raise LeniaError(st, f"lenia_stats_noalloc: {load().lenia_status_string(st).decode()}")
 
 
+def lenia_set_genes(ctx, genes):
+    """genes: host array-like [K][3] of (mu, sigma, h)."""
+    g = np.ascontiguousarray(np.asarray(genes, dtype=np.float32))
+    _check(ctx, load().lenia_set_genes(ctx, g.ctypes.data))
+
+
 def lenia_check(ctx, stream=None):
     _check(ctx, load().lenia_check(ctx, _stream(stream)))
 
@@ -246,11 +254,12 @@ def lenia_destroy(ctx):
 
 # ------------------------------------------------------ world helpers
 
-def config_from_world(world: "_inputs.World", conv_path: int = CONV_AUTO):
+def config_from_world(world: "_inputs.World", conv_path: int = CONV_AUTO, max_rollout_steps: int = 0,
+                      ckpt_every: int = 0):
     cfg = LeniaConfig(world.height, world.width, world.n_channels, world.n_kernels,
                       float(world.dt), world.growth_form, world.localized, world.maintain_genes,
                       float(world.eps_u), float(world.eps_p), world.r_diff, world.alpha_on,
-                      conv_path, 0, 0)
+                      conv_path, max_rollout_steps, ckpt_every)
     ks = []
     for k in world.kernels:
         d = LeniaKernelDesc()
@@ -298,6 +307,63 @@ class Simulation:
                         dtype=torch.float32, device=self.device)
         lenia_potentials(self.ctx, A, U)
         return U
+
+    def close(self):
+        if self.ctx:
+            lenia_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def genes_of(world) -> np.ndarray:
+    """[K][3] float32 (mu, sigma, h) of a world's kernels."""
+    return np.array([[k.mu, k.sigma, k.h] for k in world.kernels], np.float32)
+
+
+class LeniaRollout:
+    """Differentiable n-step rollout of a world with global genes.
+
+    ``rollout(A0, genes)`` returns A_T; gradients flow to A0 and to the
+    per-kernel genes [K][3] (mu, sigma, h) through lenia_backward (the
+    hand-written adjoint with checkpointed recompute)."""
+
+    def __init__(self, world, n_steps: int, ckpt_every: int = 8, conv_path: int = CONV_AUTO):
+        import torch
+
+        cfg, ks = config_from_world(world, conv_path, max_rollout_steps=n_steps, ckpt_every=ckpt_every)
+        self.ctx = lenia_init(cfg, ks)
+        self.n_steps = n_steps
+        self.K = world.n_kernels
+        outer = self
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, A0, genes):
+                lenia_set_genes(outer.ctx, genes.detach().float().cpu().numpy())
+                A = A0.detach().contiguous().clone()
+                lenia_rollout(outer.ctx, A, None, outer.n_steps)
+                fctx.save_for_backward(A0, genes)
+                return A
+
+            @staticmethod
+            def backward(fctx, gA_T):
+                A0, genes = fctx.saved_tensors
+                lenia_set_genes(outer.ctx, genes.detach().float().cpu().numpy())
+                gA0 = torch.empty_like(A0)
+                gg = torch.empty((outer.K, 3), dtype=torch.float32, device=A0.device)
+                lenia_backward(outer.ctx, A0.detach().contiguous(), None, outer.n_steps,
+                               gA_T.detach().float().contiguous(), gA0, gg)
+                return gA0, gg.to(genes.dtype)
+
+        self._fn = _Fn
+
+    def __call__(self, A0, genes):
+        return self._fn.apply(A0, genes)
 
     def close(self):
         if self.ctx:
