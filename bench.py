@@ -106,6 +106,92 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def adjoint_leg(torch, lenia, inputs, stream):
+    """Forward rollout vs rollout adjoint: 256^2, 3 channels, 15 kernels R=13,
+    global genes, 64 steps, checkpoints every 8."""
+    w = inputs.global_multi_channel()
+    n, ck = 64, 8
+    cfg, ks = lenia.config_from_world(w, lenia.CONV_AUTO, max_rollout_steps=n, ckpt_every=ck)
+    ctx = lenia.lenia_init(cfg, ks, stream)
+    try:
+        A0 = torch.from_numpy(w.A).cuda()
+        A = A0.clone()
+        gA_T = torch.ones_like(A0)
+        gA0 = torch.empty_like(A0)
+        gg = torch.empty((w.n_kernels, 3), dtype=torch.float32, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for _ in range(2):                                   # warm-up
+            A.copy_(A0)
+            lenia.lenia_rollout(ctx, A, None, n, None, stream)
+            lenia.lenia_backward(ctx, A0, None, n, gA_T, gA0, gg, stream)
+        reps = 5
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            A.copy_(A0)
+            lenia.lenia_rollout(ctx, A, None, n, None, stream)
+        ev[1].record(stream)
+        for _ in range(reps):
+            lenia.lenia_backward(ctx, A0, None, n, gA_T, gA0, gg, stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        lenia.lenia_check(ctx)
+        fwd = ev[0].elapsed_time(ev[1]) / reps
+        bwd = ev[1].elapsed_time(ev[2]) / reps
+        return {"workload": "256x256, 3 channels, 15 kernels R=13, global genes, 64 steps, checkpoint every 8",
+                "fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_over_fwd": (fwd + bwd) / fwd,
+                "conv_path": "fft" if lenia.lenia_conv_path(ctx) == lenia.CONV_FFT else "direct",
+                "note": "bwd recomputes the forward from checkpoints inside lenia_backward"}
+    finally:
+        lenia.lenia_destroy(ctx)
+
+
+def batched_leg(torch, lenia, inputs, stream, steps=200):
+    """256 single-channel localized-gene worlds of sides {64,128,256,512},
+    R in 8..16, in one batch (CUDA graph per two steps) vs one plain
+    1024^2 world of the same recipe, per site-step."""
+    worlds = inputs.batched_worlds()
+    sites = sum(w.sites for w in worlds)
+    batch = lenia.lenia_batch_init(worlds, autotune=True, stream=stream)
+    try:
+        A = [torch.from_numpy(w.A).cuda() for w in worlds]
+        P = [torch.from_numpy(w.P).cuda() for w in worlds]
+        lenia.lenia_batch_rollout(batch, A, P, 4, stream)    # capture + warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lenia.lenia_batch_rollout(batch, A, P, steps, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lenia.lenia_batch_check(batch)
+        ms = e0.elapsed_time(e1)
+        paths = [lenia.lenia_batch_conv_path(batch, i) for i in range(len(worlds))]
+    finally:
+        lenia.lenia_batch_destroy(batch)
+    plain = inputs.localized_single_channel()
+    cfg, ks = lenia.config_from_world(plain)
+    ctx = lenia.lenia_init(cfg, ks, stream)
+    try:
+        a, p = torch.from_numpy(plain.A).cuda(), torch.from_numpy(plain.P).cuda()
+        lenia.lenia_rollout(ctx, a, p, 4, None, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lenia.lenia_rollout(ctx, a, p, steps, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+    finally:
+        lenia.lenia_destroy(ctx)
+    v = sites * steps / (ms / 1e3)
+    pv = plain.sites * steps / (plain_ms / 1e3)
+    return {"workload": f"{len(worlds)} worlds, sides 64-512, R 8..16, localized mu/sigma, {sites} sites",
+            "steps": steps, "ms_per_step": ms / steps, "value": v, "unit": UNIT,
+            "alg_bytes_per_site": 24, "frac_of_hbm": v * 24 / 1e9 / _peaks()[0],
+            "fft_worlds": paths.count(lenia.CONV_FFT), "direct_worlds": paths.count(lenia.CONV_DIRECT),
+            "plain_1024_single_world": {"ms_per_step": plain_ms / steps, "value": pv},
+            "batched_over_plain": v / pv}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -305,6 +391,9 @@ def run_ours(args):
         "clocks": clk,
         "stats_finite": ok_stats,
     }
+    if not args.no_extras and ws == 1 and args.size == 2048:
+        line["adjoint"] = adjoint_leg(torch, lenia, inputs, stream)
+        line["batched"] = batched_leg(torch, lenia, inputs, stream)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -321,6 +410,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and batched-world legs")
     ap.add_argument("--size", type=int, default=2048, help="torus side (2048 = the benchmark workload)")
     ap.add_argument("--conv-path", type=int, default=0, help="0 auto, 1 fft, 2 direct")
     args = ap.parse_args()

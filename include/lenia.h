@@ -232,6 +232,33 @@ LENIA_API int32_t lenia_conv_path(const lenia_ctx* ctx);
 /* Number of CUDA kernel launches one lenia_step enqueues (with stats). */
 LENIA_API int32_t lenia_launches_per_step(const lenia_ctx* ctx);
 
+/* ---- Batched worlds (many independent worlds of uneven sizes and genotypes;
+ * the scale-out of the paper's Section 1.4 on one GPU; not a construct of the
+ * paper itself).
+ * lenia_batch_init makes one context per world from cfgs[0..n_worlds) and
+ * kernels (world w's n_kernels descriptors follow world w-1's).  With
+ * autotune != 0, worlds whose conv_path is AUTO get the faster of the FFT and
+ * direct paths, timed once per distinct (size, channels, kernels, genes,
+ * largest radius).  All scratch is allocated here.
+ * lenia_batch_rollout advances every world n_steps in place: A and P are HOST
+ * arrays of n_worlds DEVICE pointers (P[w] may be NULL for worlds without gene
+ * maps; P itself may be NULL if no world has them).  The steps of all worlds
+ * are captured once per pointer set into a CUDA graph whose branches run the
+ * worlds concurrently; one graph launch advances every world two steps.  The
+ * work is ordered after earlier work on `stream` and before later work.
+ * Worlds must not share buffers.  No statistics are computed. */
+typedef struct lenia_batch lenia_batch;
+LENIA_API lenia_status lenia_batch_init(int32_t n_worlds, const lenia_config* cfgs,
+                                        const lenia_kernel_desc* kernels, int32_t autotune,
+                                        void* stream, lenia_batch** out);
+LENIA_API lenia_status lenia_batch_rollout(lenia_batch* batch, float* const* A, float* const* P,
+                                           int32_t n_steps, void* stream);
+/* Convolution path chosen for world w (LENIA_CONV_FFT or LENIA_CONV_DIRECT), or -1. */
+LENIA_API int32_t lenia_batch_conv_path(const lenia_batch* batch, int32_t world);
+/* lenia_check over every world's context after synchronising `stream`. */
+LENIA_API lenia_status lenia_batch_check(lenia_batch* batch, void* stream);
+LENIA_API void lenia_batch_destroy(lenia_batch* batch);
+
 LENIA_API const char* lenia_last_error(const lenia_ctx* ctx);
 LENIA_API const char* lenia_status_string(lenia_status s);
 LENIA_API void lenia_destroy(lenia_ctx* ctx);

@@ -252,6 +252,25 @@ def global_multi_channel(H=256, W=256, R=13, patch=48, seed_index=4, dt=0.2,
     return World(H, W, n_channels, kernels, dt, A=A, name=name)
 
 
+def batched_worlds(n_worlds=256, sizes=(64, 128, 256, 512), r_range=(8, 16), n_geno=4,
+                   seed_index=3, dt=0.1, live=False):
+    """n_worlds independent single-channel localized-gene worlds: side drawn
+    uniformly from `sizes`, radius uniformly from r_range, n_geno genotypes
+    (mu ~ U[0.10, 0.40), sigma ~ U[0.01, 0.06)) on squares of side/8 (at
+    least 8) as in the single-world recipe; maintenance on."""
+    rng = Rng(BASE_SEED + seed_index)
+    side = rng.integers(n_worlds, 0, len(sizes) - 1)
+    rad = rng.integers(n_worlds, r_range[0], r_range[1])
+    worlds = []
+    for w in range(n_worlds):
+        S = int(sizes[side[w]])
+        R = int(min(rad[w], (S - 1) // 2))
+        worlds.append(localized_single_channel(H=S, W=S, R=R, patch=max(8, S // 8), n_geno=n_geno,
+                                               seed_index=seed_index * 100000 + w, dt=dt,
+                                               name=f"batch{w}", live=live))
+    return worlds
+
+
 # The five workloads, full size.  Parity tests use reduced shapes of the
 # same recipes; the benchmark times the 2048^2 multi-channel one.
 def workload(name: str) -> World:

@@ -25,7 +25,8 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_potentials", "lenia_update_from_potentials", "lenia_step_host",
            "lenia_kernel_weights", "lenia_conv_path", "lenia_launches_per_step",
            "lenia_last_error", "lenia_status_string", "lenia_destroy", "lenia_profile_start",
-           "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes")
+           "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes", "lenia_batch_init",
+           "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy")
 PROFILE_KINDS = 7
 
 
@@ -108,6 +109,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_profile_kind_name.restype = ctypes.c_char_p
     lib.lenia_stats_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp]
     lib.lenia_stats_noalloc.restype = st
+    lib.lenia_batch_init.argtypes = [ctypes.c_int32, ctypes.POINTER(LeniaConfig), ctypes.POINTER(LeniaKernelDesc),
+                                     ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.lenia_batch_init.restype = st
+    lib.lenia_batch_rollout.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, vp]
+    lib.lenia_batch_rollout.restype = st
+    lib.lenia_batch_conv_path.argtypes = [vp, ctypes.c_int32]
+    lib.lenia_batch_conv_path.restype = ctypes.c_int32
+    lib.lenia_batch_check.argtypes = [vp, vp]
+    lib.lenia_batch_check.restype = st
+    lib.lenia_batch_destroy.argtypes = [vp]
+    lib.lenia_batch_destroy.restype = None
     lib.lenia_set_genes.argtypes = [vp, vp]
     lib.lenia_set_genes.restype = st
     lib.lenia_check.argtypes = [vp, vp]
@@ -187,6 +199,54 @@ def lenia_stats_noalloc(A, n_channels, height, width, out, stream=None):
                                     _stream(stream))
     if st != LENIA_OK:
         raise LeniaError(st, f"lenia_stats_noalloc: {load().lenia_status_string(st).decode()}")
+
+
+def lenia_batch_init(worlds, autotune: bool = True, conv_path: int = CONV_AUTO, stream=None):
+    """One batch over inputs.World objects; returns the batch handle."""
+    lib = load()
+    cfgs, kds = [], []
+    for w in worlds:
+        cfg, ks = config_from_world(w, conv_path)
+        cfgs.append(cfg)
+        kds.extend(ks)
+    ca = (LeniaConfig * len(cfgs))(*cfgs)
+    ka = (LeniaKernelDesc * len(kds))(*kds)
+    out = ctypes.c_void_p()
+    st = lib.lenia_batch_init(len(cfgs), ca, ka, int(bool(autotune)), _stream(stream), ctypes.byref(out))
+    if st != LENIA_OK:
+        raise LeniaError(st, f"lenia_batch_init: {lib.lenia_status_string(st).decode()}")
+    return out.value
+
+
+def _ptr_array(xs):
+    arr = (ctypes.c_void_p * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = _ptr(x)
+    return arr
+
+
+def lenia_batch_rollout(batch, A_list, P_list, n_steps, stream=None):
+    lib = load()
+    pa = _ptr_array(A_list)
+    pp = _ptr_array(P_list) if P_list is not None else None
+    st = lib.lenia_batch_rollout(batch, pa, pp, int(n_steps), _stream(stream))
+    if st != LENIA_OK:
+        raise LeniaError(st, f"lenia_batch_rollout: {lib.lenia_status_string(st).decode()}")
+
+
+def lenia_batch_conv_path(batch, world: int) -> int:
+    return load().lenia_batch_conv_path(batch, int(world))
+
+
+def lenia_batch_check(batch, stream=None):
+    st = load().lenia_batch_check(batch, _stream(stream))
+    if st != LENIA_OK:
+        raise LeniaError(st, "lenia_batch_check")
+
+
+def lenia_batch_destroy(batch):
+    if batch:
+        load().lenia_batch_destroy(batch)
 
 
 def lenia_set_genes(ctx, genes):

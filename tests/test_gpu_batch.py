@@ -1,0 +1,76 @@
+"""Batched worlds (lenia_batch_*): a batch rollout equals per-world rollouts
+on the same convolution paths bit for bit, and one batch step matches the
+FP64 oracle per world.  GPU only."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_05639_gb300 import build, inputs, lenia
+from gpu_util import compare_step, alpha_margin, to_dev, torch_mod
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    oracle.build()
+    torch_mod()
+
+
+def _worlds():
+    ws = inputs.batched_worlds(n_worlds=9, sizes=(64, 128, 256), r_range=(6, 12), live=True)
+    # one non-power-of-two world (direct path only) and one multi-channel world
+    ws.append(inputs.localized_single_channel(H=96, W=80, R=7, patch=16, n_geno=2, live=True, name="odd"))
+    ws.append(inputs.multi_channel(H=64, W=128, R=9, patch=20, n_geno=3, live=True, name="mc"))
+    return ws
+
+
+@pytest.mark.parametrize("n_steps", [3, 4])
+def test_batch_rollout_equals_single_world_rollouts(n_steps):
+    torch = torch_mod()
+    ws = _worlds()
+    batch = lenia.lenia_batch_init(ws, autotune=True)
+    try:
+        A = [to_dev(w.A) for w in ws]
+        P = [to_dev(w.P) if w.P is not None else None for w in ws]
+        lenia.lenia_batch_rollout(batch, A, P, n_steps)
+        lenia.lenia_batch_check(batch)
+        paths = [lenia.lenia_batch_conv_path(batch, i) for i in range(len(ws))]
+        assert set(paths) <= {lenia.CONV_FFT, lenia.CONV_DIRECT}
+        assert paths[-2] == lenia.CONV_DIRECT        # 96 x 80 has no FFT path
+        for i, w in enumerate(ws):
+            cfg, ks = lenia.config_from_world(w, paths[i])
+            ctx = lenia.lenia_init(cfg, ks)
+            try:
+                a, p = to_dev(w.A), (to_dev(w.P) if w.P is not None else None)
+                lenia.lenia_rollout(ctx, a, p, n_steps)
+                torch.cuda.synchronize()
+                assert torch.equal(a, A[i]), w.name
+                if p is not None:
+                    assert torch.equal(p, P[i]), w.name
+            finally:
+                lenia.lenia_destroy(ctx)
+        # the captured graphs are reused for the same buffers
+        lenia.lenia_batch_rollout(batch, A, P, 2)
+        lenia.lenia_batch_check(batch)
+    finally:
+        lenia.lenia_batch_destroy(batch)
+
+
+def test_batch_step_matches_oracle():
+    torch = torch_mod()
+    ws = _worlds()[:4] + _worlds()[-2:]
+    batch = lenia.lenia_batch_init(ws, autotune=True)
+    try:
+        A = [to_dev(w.A) for w in ws]
+        P = [to_dev(w.P) if w.P is not None else None for w in ws]
+        lenia.lenia_batch_rollout(batch, A, P, 1)
+        lenia.lenia_batch_check(batch)
+        for i, w in enumerate(ws):
+            A1, P1, U, al = oracle.step(w, return_u=True, return_alpha=True)
+            Ph = np.stack([[oracle.diffuse(w.P[p, k]) for k in range(w.n_kernels)] for p in range(w.n_planes)])
+            g = {"A": A[i].cpu().numpy(), "P": P[i].cpu().numpy()}
+            compare_step(w, g, A1, P1, al, alpha_margin(w, U, Ph))
+    finally:
+        lenia.lenia_batch_destroy(batch)
