@@ -192,6 +192,22 @@ def batched_leg(torch, lenia, inputs, stream, steps=200):
             "batched_over_plain": v / pv}
 
 
+def max_over_ranks(values, torch, device=None):
+    """Element-wise max of a list of floats over all ranks (identity at N = 1)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_value(world_size, sites_per_rank, steps, slowest_ms):
+    """Whole-job throughput of independent replicas: every rank's site-steps
+    over the slowest rank's time."""
+    return world_size * sites_per_rank * steps / (slowest_ms / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -340,12 +356,9 @@ def run_ours(args):
                                   oA if i % 2 == 0 else hA, oP if i % 2 == 0 else hP, hst, stream)
         e2e_s = time.perf_counter() - t0
 
-    t_max = ms
-    e2e_max = e2e_s
-    if ws > 1:
-        t = torch.tensor([ms, e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max, e2e_max = float(t[0]), float(t[1])
+    t_max, e2e_max = max_over_ranks([ms, e2e_s if e2e_s == e2e_s else 0.0], torch, dev)
+    if e2e_s != e2e_s:
+        e2e_max = float("nan")
 
     ok_stats = bool(torch.isfinite(stats).all())
     path = lenia.lenia_conv_path(ctx)
@@ -355,7 +368,7 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return 0
 
-    value = ws * sites * args.steps / (t_max / 1e3)
+    value = job_value(ws, sites, args.steps, t_max)
     hbm, peak_kind = _peaks()
     # dominant kernel: the largest share of the timed region
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
@@ -384,7 +397,8 @@ def run_ours(args):
         "kernels_ms": {k: {"avg_ms": v[0] / max(1, v[1]), "launches": v[1],
                            "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
                        for k, v in prof.items()},
-        "e2e": {"value": (ws * sites * e2e_steps / e2e_max) if e2e_max == e2e_max else None, "unit": UNIT,
+        "e2e": {"value": job_value(ws, sites, e2e_steps, e2e_max * 1e3) if e2e_max == e2e_max else None,
+                "unit": UNIT,
                 "h2d_bytes_per_step": int(world.A.nbytes + world.P.nbytes),
                 "d2h_bytes_per_step": int(world.A.nbytes + world.P.nbytes + hst.numel() * 4)},
         "gpu_launches": launches_per_step * args.steps,

@@ -177,6 +177,13 @@ LENIA_API lenia_status lenia_update_from_potentials(lenia_ctx* ctx, const float*
  * calls it before returning. */
 LENIA_API lenia_status lenia_check(lenia_ctx* ctx, void* stream);
 
+/* Failure-path self-test (no counterpart in the paper): enqueue one block whose
+ * mbarrier wait nothing completes, bounded by limit_mcycles million SM clock
+ * cycles (1..4000); when the bound runs out it sets the device status word as
+ * a streaming kernel would, so the next lenia_check returns LENIA_ETIMEOUT.
+ * Nothing faults or traps; the context stays usable. */
+LENIA_API lenia_status lenia_selftest_wait_timeout(lenia_ctx* ctx, int32_t limit_mcycles, void* stream);
+
 /* lenia_step with HOST buffers: copies A_in/P_in host->device into library
  * buffers, steps, and copies A_out/P_out (and stats_out, C*3 floats, nullable)
  * back; returns after the stream has finished.  Page-locked host memory

@@ -843,6 +843,13 @@ lenia_status lenia_check(lenia_ctx* c, void* stream)
     return LENIA_OK;
 }
 
+lenia_status lenia_selftest_wait_timeout(lenia_ctx* c, int32_t limit_mcycles, void* stream)
+{
+    if (!c || limit_mcycles < 1 || limit_mcycles > 4000) return LENIA_EINVAL;
+    CUDA_OR_FAIL(c, launch_selftest_wait((long long)limit_mcycles * 1000000LL, c->d_status, (cudaStream_t)stream));
+    return LENIA_OK;
+}
+
 lenia_status lenia_step_host(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
                              float* stats_out, void* stream)
 {

@@ -98,6 +98,7 @@ cudaError_t launch_stats_final(const double* partials, int n_blocks, int C, int 
                                float* out, cudaStream_t s);
 cudaError_t launch_spectra(const double* Kd, int R, int H, int W, const double* cos_H,
                            const double* cos_W, double* T_scratch, float* S_out, cudaStream_t s);
+cudaError_t launch_selftest_wait(long long limit_cycles, int* status, cudaStream_t s);
 int adjoint_blocks(int H, int W);
 cudaError_t launch_adjoint_epilogue(const AdjParams& p, cudaStream_t s);
 cudaError_t launch_adjoint_gather(const AdjParams& p, cudaStream_t s);

@@ -26,7 +26,8 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_kernel_weights", "lenia_conv_path", "lenia_launches_per_step",
            "lenia_last_error", "lenia_status_string", "lenia_destroy", "lenia_profile_start",
            "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes", "lenia_batch_init",
-           "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy")
+           "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy",
+           "lenia_selftest_wait_timeout")
 PROFILE_KINDS = 7
 
 
@@ -120,6 +121,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_batch_check.restype = st
     lib.lenia_batch_destroy.argtypes = [vp]
     lib.lenia_batch_destroy.restype = None
+    lib.lenia_selftest_wait_timeout.argtypes = [vp, ctypes.c_int32, vp]
+    lib.lenia_selftest_wait_timeout.restype = st
     lib.lenia_set_genes.argtypes = [vp, vp]
     lib.lenia_set_genes.restype = st
     lib.lenia_check.argtypes = [vp, vp]
@@ -253,6 +256,10 @@ def lenia_set_genes(ctx, genes):
     """genes: host array-like [K][3] of (mu, sigma, h)."""
     g = np.ascontiguousarray(np.asarray(genes, dtype=np.float32))
     _check(ctx, load().lenia_set_genes(ctx, g.ctypes.data))
+
+
+def lenia_selftest_wait_timeout(ctx, limit_mcycles: int = 200, stream=None):
+    _check(ctx, load().lenia_selftest_wait_timeout(ctx, int(limit_mcycles), _stream(stream)))
 
 
 def lenia_check(ctx, stream=None):

@@ -292,6 +292,28 @@ def test_check_reports_ok_after_steps():
         lenia.lenia_destroy(ctx)
 
 
+def test_bounded_wait_timeout_is_reported_and_context_survives():
+    """A device wait that nothing completes gives up after its clock bound and
+    surfaces as LENIA_ETIMEOUT on the host; the status clears and the context
+    keeps working (no fault, no trap)."""
+    torch = torch_mod()
+    w = w_c3_wide()
+    cfg, ks = lenia.config_from_world(w, 1)
+    ctx = lenia.lenia_init(cfg, ks)
+    try:
+        lenia.lenia_selftest_wait_timeout(ctx, 200)       # about 0.1 s of SM clock
+        with pytest.raises(lenia.LeniaError) as e:
+            lenia.lenia_check(ctx)
+        assert e.value.status == lenia.LENIA_ETIMEOUT
+        lenia.lenia_check(ctx)                            # cleared
+        A, P = to_dev(w.A), to_dev(w.P)
+        A2, P2 = torch.empty_like(A), torch.empty_like(P)
+        lenia.lenia_step(ctx, A, P, A2, P2)
+        lenia.lenia_check(ctx)
+    finally:
+        lenia.lenia_destroy(ctx)
+
+
 def test_step_host_matches_step():
     torch = torch_mod()
     w = w_c2_small()
