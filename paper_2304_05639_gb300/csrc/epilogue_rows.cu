@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
     constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
     constexpr int PH = (LOC & 4) ? NP - 1 : -1;
     static_assert(TOPO == 0 || (KT == 15 && CT == 3), "paper topology has 15 kernels, 3 channels");
+    static_assert(CT * 5 <= ER_THREADS / 32, "one warp per statistics sum");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
     float* Pring = reinterpret_cast<float*>(smem);
@@ -312,6 +313,42 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
             double s = 0.0;
             for (int w = 0; w < ER_CONSUMERS; w++) s += (double)red[w][tid];
             p.partials[(size_t)blockIdx.x * CT * 5 + tid] = s;
+        }
+        if (p.stats_out) {
+            // The last block to finish reduces every block's record in block
+            // order (deterministic) and re-arms the ticket for the next launch.
+            __shared__ unsigned int ticket;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) ticket = atomicAdd(p.ticket, 1u);
+            __syncthreads();
+            if (ticket == gridDim.x - 1) {
+                __threadfence();
+                __shared__ double tot[CT * 5];
+                // one warp per sum: lanes stride over the block records, then a
+                // fixed shuffle tree (deterministic)
+                if (warp < CT * 5) {
+                    double s = 0.0;
+                    for (unsigned b = lane; b < gridDim.x; b += 32)
+                        s += __ldcg(&p.partials[(size_t)b * CT * 5 + warp]);
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+                    if (lane == 0) tot[warp] = s;
+                }
+                __syncthreads();
+                if (tid < CT) {
+                    const int c = tid;
+                    const double two_pi = 6.283185307179586476925286766559;
+                    double ty = atan2(tot[c * 5 + 1], tot[c * 5 + 2]) * H / two_pi;
+                    double tx = atan2(tot[c * 5 + 3], tot[c * 5 + 4]) * W / two_pi;
+                    if (ty < 0.0) ty += H;
+                    if (tx < 0.0) tx += W;
+                    p.stats_out[c * 3 + 0] = (float)tot[c * 5 + 0];
+                    p.stats_out[c * 3 + 1] = (float)ty;
+                    p.stats_out[c * 3 + 2] = (float)tx;
+                }
+                if (tid == 0) *p.ticket = 0u;
+            }
         }
     }
 }

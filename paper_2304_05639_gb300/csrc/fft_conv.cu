@@ -33,9 +33,9 @@ __global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
     const int W = 2 * M;
     const float2* src = reinterpret_cast<const float2*>(p.A + ((size_t)c * p.H + y0) * W);
     auto ld_g = [&](int b, int i) { return __ldg(&src[(size_t)b * M + i]); };
-    auto sld = [&](int b, int i) { return sm[b * SZ + swz(i)]; };
-    auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz(i)] = v; };
-    fft_run<M, NB, T, false, false>(p.tw_M, ld_g, sld, sst, sst);
+    auto sld = [&](int b, int i) { return sm[b * SZ + swz32(i)]; };
+    auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz32(i)] = v; };
+    fft_run<M, NB, T, false, false, ROW_RMAX>(p.tw_M, ld_g, sld, sst, sst);
 
     // X[k] = E[k] + w_W^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i
     // Output column kx holds rows y0 .. y0 + NB - 1 contiguously (b fastest).
@@ -44,12 +44,12 @@ __global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
         const int b = u % NB;
         const int k = u / NB;
         if (k == 0) {
-            float2 z = sm[b * SZ + swz(0)];
+            float2 z = sm[b * SZ + swz32(0)];
             outc[b] = make_float2(z.x + z.y, z.x - z.y);
             continue;
         }
-        const float2 zk = sm[b * SZ + swz(k)];
-        const float2 zm = sm[b * SZ + swz(M - k)];
+        const float2 zk = sm[b * SZ + swz32(k)];
+        const float2 zm = sm[b * SZ + swz32(M - k)];
         {
             float2 e = cscale(cadd(zk, cconj(zm)), 0.5f);
             float2 d = cscale(csub(zk, cconj(zm)), 0.5f);
@@ -97,26 +97,26 @@ __global__ void __launch_bounds__(T) k_rows_c2r(FftParams p)
         const int b = u % NB, q = u / NB;
         if (q == 0) {
             const float2 x = xk[it];                          // (DC, Nyquist)
-            sm[b * SZ + swz(0)] = make_float2(x.x + x.y, x.x - x.y);
+            sm[b * SZ + swz32(0)] = make_float2(x.x + x.y, x.x - x.y);
             continue;
         }
         {
             float2 s = cadd(xk[it], cconj(xm[it]));
             float2 d = cmulc(csub(xk[it], cconj(xm[it])), __ldg(&p.tw_W[q]));
-            sm[b * SZ + swz(q)] = make_float2(s.x - d.y, s.y + d.x);   // s + i d
+            sm[b * SZ + swz32(q)] = make_float2(s.x - d.y, s.y + d.x);   // s + i d
         }
         if (q != M - q) {
             float2 s = cadd(xm[it], cconj(xk[it]));
             float2 d = cmulc(csub(xm[it], cconj(xk[it])), __ldg(&p.tw_W[M - q]));
-            sm[b * SZ + swz(M - q)] = make_float2(s.x - d.y, s.y + d.x);
+            sm[b * SZ + swz32(M - q)] = make_float2(s.x - d.y, s.y + d.x);
         }
     }
     __syncthreads();
     float2* out = reinterpret_cast<float2*>(p.U + ((size_t)k * p.H + y0) * W);
-    auto sld = [&](int b, int i) { return sm[b * SZ + swz(i)]; };
-    auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz(i)] = v; };
+    auto sld = [&](int b, int i) { return sm[b * SZ + swz32(i)]; };
+    auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz32(i)] = v; };
     auto st_g = [&](int b, int i, float2 v) { out[(size_t)b * M + i] = v; };
-    fft_run<M, NB, T, true, false>(p.tw_M, sld, sld, sst, st_g);
+    fft_run<M, NB, T, true, false, ROW_RMAX>(p.tw_M, sld, sld, sst, st_g);
 }
 
 // ------------------------------------------------------- columns: fwd, x K^, inv
@@ -170,10 +170,10 @@ template <int M>
 static cudaError_t rows_launch(const FftParams& p, cudaStream_t s, bool inverse)
 {
     // at least 8 rows per block (64-byte runs of the column-major spectra) and
-    // at least 4096 complex values; one radix-16 butterfly per thread
+    // at least 4096 complex values; one radix-ROW_RMAX butterfly per thread
     constexpr int NB0 = (4096 / M) > 8 ? (4096 / M) : 8;
     constexpr int NB = NB0 < 64 ? NB0 : 64;
-    constexpr int T = (NB * M / 16) < 512 ? (NB * M / 16) : 512;
+    constexpr int T = (NB * M / ROW_RMAX) < 512 ? (NB * M / ROW_RMAX) : 512;
     const size_t smem = (size_t)NB * row_pitch(M) * sizeof(float2);
     if (p.H % NB) return cudaErrorInvalidValue;
     if (!inverse) {

@@ -45,27 +45,35 @@ __device__ __forceinline__ float2 mul_mi(float2 a)
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// cos(2 pi q / 16), q = 0..4: exact decimal expansions of 1, cos(pi/8),
-// sqrt(2)/2, sin(pi/8), 0.
-struct C16 {
-    static constexpr float c1 = 0.923879532511286756128f;
-    static constexpr float c2 = 0.707106781186547524401f;
-    static constexpr float c3 = 0.382683432365089771728f;
+// cos(pi q / 16) and sin(pi q / 16) for q = 0..15 (decimal expansions of
+// cos(pi/16), cos(pi/8), cos(3 pi/16), sqrt(2)/2 and their complements).
+struct C32 {
+    static constexpr float k1 = 0.980785280403230449126f;   // cos(pi/16)
+    static constexpr float k2 = 0.923879532511286756128f;   // cos(pi/8)
+    static constexpr float k3 = 0.831469612302545237079f;   // cos(3 pi/16)
+    static constexpr float k4 = 0.707106781186547524401f;   // cos(pi/4)
+    static constexpr float k5 = 0.555570233019602224743f;   // cos(5 pi/16) = sin(3 pi/16)
+    static constexpr float k6 = 0.382683432365089771728f;   // cos(3 pi/8)  = sin(pi/8)
+    static constexpr float k7 = 0.195090322016128267848f;   // cos(7 pi/16) = sin(pi/16)
+    __host__ __device__ static constexpr float cosq(int q)
+    {
+        return q == 0 ? 1.f : q == 1 ? k1 : q == 2 ? k2 : q == 3 ? k3 : q == 4 ? k4 : q == 5 ? k5 : q == 6 ? k6
+             : q == 7 ? k7 : q == 8 ? 0.f : -cosq(16 - q);
+    }
+    __host__ __device__ static constexpr float sinq(int q) { return q <= 8 ? cosq(8 - q) : cosq(q - 8); }
 };
 
 // w_R^q = exp(-+2 pi i q / R) applied to a, for q < R/2 (compile-time).
 template <int R, int Q, bool INV>
 __device__ __forceinline__ float2 rot(float2 a)
 {
-    static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
-    constexpr int q16 = Q * (16 / R);   // angle in units of 2 pi / 16
-    if constexpr (q16 == 0) return a;
-    else if constexpr (q16 == 4) return mul_mi<INV>(a);
+    static_assert(R == 2 || R == 4 || R == 8 || R == 16 || R == 32, "radix");
+    constexpr int q32 = Q * (32 / R);   // angle in units of 2 pi / 32 = pi / 16
+    if constexpr (q32 == 0) return a;
+    else if constexpr (q32 == 8) return mul_mi<INV>(a);
     else {
-        constexpr float c = (q16 == 1) ? C16::c1 : (q16 == 2) ? C16::c2 : (q16 == 3) ? C16::c3
-                          : (q16 == 5) ? -C16::c3 : (q16 == 6) ? -C16::c2 : -C16::c1;
-        constexpr float s = (q16 == 1) ? C16::c3 : (q16 == 2) ? C16::c2 : (q16 == 3) ? C16::c1
-                          : (q16 == 5) ? C16::c1 : (q16 == 6) ? C16::c2 : C16::c3;
+        constexpr float c = C32::cosq(q32);
+        constexpr float s = C32::sinq(q32);
         // forward: multiply by (c - i s); inverse by (c + i s)
         return INV ? make_float2(a.x * c - a.y * s, a.x * s + a.y * c)
                    : make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
@@ -112,16 +120,20 @@ struct DFT<1, INV> {
     __device__ __forceinline__ static void run(float2*) {}
 };
 
-__host__ __device__ constexpr int fft_radix(int remaining) { return remaining >= 16 ? 16 : remaining; }
+// Radix plan: passes of radix RMAX while at least RMAX remains, then the rest.
+__host__ __device__ constexpr int fft_radix(int remaining, int rmax = 16)
+{
+    return remaining >= rmax ? rmax : remaining;
+}
 
 // Offset of the twiddle table of the pass with sub-transform size NS in the
 // concatenated per-pass tables of a length-N transform; fft_tw_offset(N, N)
 // is the total length.
-__host__ __device__ constexpr int fft_tw_offset(int N, int NS)
+__host__ __device__ constexpr int fft_tw_offset(int N, int NS, int rmax = 16)
 {
     int off = 0;
-    for (int ns = 1; ns < NS && ns < N; ns *= fft_radix(N / ns))
-        if (ns > 1) off += (fft_radix(N / ns) - 1) * ns;
+    for (int ns = 1; ns < NS && ns < N; ns *= fft_radix(N / ns, rmax))
+        if (ns > 1) off += (fft_radix(N / ns, rmax) - 1) * ns;
     return off;
 }
 
@@ -174,33 +186,37 @@ __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp,
 // Full transform: pass 1 reads with ld_first, middle passes use the shared
 // accessors sld/sst, the last pass writes with st_last.  With a single pass
 // the first reader and the last writer are used together.
-template <int N, int NB, int T, bool INV, bool BFAST, int NS = 1, class LF, class SL, class SS, class STL>
+template <int N, int NB, int T, bool INV, bool BFAST, int RMAX = 16, int NS = 1, class LF, class SL, class SS,
+          class STL>
 __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_first, SL sld, SS sst, STL st_last)
 {
-    constexpr int R = fft_radix(N / NS);
+    constexpr int R = fft_radix(N / NS, RMAX);
     constexpr bool first = (NS == 1);
     constexpr bool last = (NS * R == N);
-    const float2* twp = tw + fft_tw_offset(N, NS);
+    const float2* twp = tw + fft_tw_offset(N, NS, RMAX);
     if constexpr (first && last) {
         fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, ld_first, st_last);
     } else if constexpr (first) {
         fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, ld_first, sst);
-        fft_run<N, NB, T, INV, BFAST, NS * R>(tw, ld_first, sld, sst, st_last);
+        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R>(tw, ld_first, sld, sst, st_last);
     } else if constexpr (last) {
         fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, sld, st_last);
     } else {
         fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, sld, sst);
-        fft_run<N, NB, T, INV, BFAST, NS * R>(tw, ld_first, sld, sst, st_last);
+        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R>(tw, ld_first, sld, sst, st_last);
     }
 }
 
-// Shared-memory index swizzle: one float2 of padding per 16 keeps the
+// Shared-memory index swizzle: one float2 of padding per 16 (per 32 for the
+// radix-32 row transforms, whose first pass writes with stride 32) keeps the
 // power-of-two strides of the first passes off a single bank.
 __device__ __forceinline__ int swz(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int swz_size(int n) { return n + (n >> 4) + 1; }
-// Pitch of one transform's row when several rows are walked row-fastest
-// (8 rows x 4 columns per warp): a pitch of 4 (mod 16) float2 puts the rows
-// on distinct bank groups.
-__host__ __device__ constexpr int row_pitch(int n) { return (swz_size(n) + 15) / 16 * 16 + 4; }
+__device__ __forceinline__ int swz32(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr int swz32_size(int n) { return n + (n >> 5) + 1; }
+// Pitch of one row transform when several rows are walked row-fastest
+// (8 rows x 2 columns per half-warp): a pitch of 2 (mod 16) float2 puts those
+// 16 accesses on 16 distinct bank pairs.
+__host__ __device__ constexpr int row_pitch(int n) { return (swz32_size(n) + 15) / 16 * 16 + 2; }
 
 }  // namespace lenia

@@ -42,6 +42,7 @@ struct lenia_ctx {
     float* d_P3 = nullptr;
     float* d_stats = nullptr;
     int* d_status = nullptr;               // device status word (bounded-wait failures)
+    unsigned int* d_ticket = nullptr;      // last-block ticket of the fused stats reduction
     int num_sms = 0;
     int n_part_blocks = 0;
     ConvParams cp;
@@ -194,14 +195,14 @@ lenia_status dalloc(lenia_ctx* c, T** p, size_t n)
     return LENIA_OK;
 }
 
-// Per-pass Stockham twiddle tables of a length-n transform (radix-16 passes
-// and a final smaller radix), each laid out [r - 1][k]:
+// Per-pass Stockham twiddle tables of a length-n transform (passes of radix
+// rmax while at least rmax remains, then the rest), each laid out [r - 1][k]:
 // exp(-2 pi i r k / (Ns R)), computed in FP64 and rounded once.
-std::vector<float2> pass_twiddles(int n)
+std::vector<float2> pass_twiddles(int n, int rmax)
 {
     std::vector<float2> t;
     for (int ns = 1; ns < n;) {
-        const int R = n / ns >= 16 ? 16 : n / ns;
+        const int R = n / ns >= rmax ? rmax : n / ns;
         if (ns > 1)
             for (int r = 1; r < R; r++)
                 for (int k = 0; k < ns; k++) {
@@ -340,16 +341,21 @@ lenia_status step_impl(lenia_ctx* c, const float* A_in, const float* P_in, float
     ep.alpha_out = alpha_out;
     ep.partials = stats_out ? c->d_partials : nullptr;
     int nb = 0;
+    bool fused_stats = false;
     {
         ProfScope ps(c, KIND_EPI, s);
         const bool aligned = ((uintptr_t)ep.A % 16 == 0) && ((uintptr_t)ep.U % 16 == 0) &&
                              (!ep.P || (uintptr_t)ep.P % 16 == 0);
-        if (aligned && epilogue_rows_supported(ep))
+        if (aligned && epilogue_rows_supported(ep)) {
+            ep.stats_out = stats_out;        // reduced by the kernel's last block
+            ep.ticket = c->d_ticket;
+            fused_stats = stats_out != nullptr;
             CUDA_OR_FAIL(c, launch_epilogue_rows(ep, c->num_sms, c->d_status, s, &nb));
-        else
+        } else {
             CUDA_OR_FAIL(c, launch_epilogue(ep, s, &nb));
+        }
     }
-    if (stats_out) {
+    if (stats_out && !fused_stats) {
         ProfScope ps(c, KIND_STATS_F, s);
         CUDA_OR_FAIL(c, launch_stats_final(c->d_partials, nb, c->cfg.n_channels, c->cfg.height,
                                            c->cfg.width, stats_out, s));
@@ -422,7 +428,9 @@ int32_t lenia_conv_path(const lenia_ctx* ctx) { return ctx ? ctx->path : -1; }
 int32_t lenia_launches_per_step(const lenia_ctx* ctx)
 {
     if (!ctx) return -1;
-    return (ctx->path == LENIA_CONV_FFT ? 3 : 1) + 2;
+    EpiParams ep = epi_params(const_cast<lenia_ctx*>(ctx));
+    const bool fused = epilogue_rows_supported(ep);   // stats reduced inside the epilogue
+    return (ctx->path == LENIA_CONV_FFT ? 3 : 1) + (fused ? 1 : 2);
 }
 
 void lenia_destroy(lenia_ctx* c)
@@ -432,7 +440,7 @@ void lenia_destroy(lenia_ctx* c)
                     c->d_Ahat, c->d_Uhat, c->d_U, c->d_partials, c->d_trig, c->d_A2, c->d_P2,
                     c->d_A3, c->d_P3, c->d_stats, c->d_status, c->d_ckpt, c->d_seg, c->d_gA[0],
                     c->d_gA[1], c->d_gpre, c->d_gU, c->d_V, c->d_gene_part, c->d_gene_acc,
-                    c->d_Ahat_t, c->d_Uhat_t};
+                    c->d_Ahat_t, c->d_Uhat_t, c->d_ticket};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -524,6 +532,8 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
     ALLOC(c->d_stats, (size_t)C * 3);
     ALLOC(c->d_status, 1);
     CK_INIT(cudaMemset(c->d_status, 0, sizeof(int)));
+    ALLOC(c->d_ticket, 1);
+    CK_INIT(cudaMemset(c->d_ticket, 0, sizeof(unsigned int)));
     {
         int dev = 0;
         CK_INIT(cudaGetDevice(&dev));
@@ -598,7 +608,7 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         ALLOC(c->d_Ahat, (size_t)C * H * M);
         ALLOC(c->d_Uhat, (size_t)K * H * M);
         ALLOC(c->d_S, (size_t)K * (M + 1) * HS);
-        std::vector<float2> twM = pass_twiddles(M), twW = twiddles(W, M + 1), twH = pass_twiddles(H);
+        std::vector<float2> twM = pass_twiddles(M, ROW_RMAX), twW = twiddles(W, M + 1), twH = pass_twiddles(H, 16);
         ALLOC(c->d_twM, twM.size());
         ALLOC(c->d_twW, twW.size());
         ALLOC(c->d_twH, twH.size());
@@ -838,6 +848,8 @@ lenia_status lenia_check(lenia_ctx* c, void* stream)
     CUDA_OR_FAIL(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {
         CUDA_OR_FAIL(c, cudaMemset(c->d_status, 0, sizeof(int)));
+        // a block that gave up never took its stats ticket: re-arm the counter
+        CUDA_OR_FAIL(c, cudaMemset(c->d_ticket, 0, sizeof(unsigned int)));
         return fail(c, LENIA_ETIMEOUT, "a device-side wait gave up (status " + std::to_string(st) + ")");
     }
     return LENIA_OK;

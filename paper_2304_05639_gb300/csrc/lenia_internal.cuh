@@ -8,6 +8,7 @@ namespace lenia {
 constexpr int kMaxKernels = 64;
 constexpr int kMaxChannels = 8;
 constexpr int kMaxPlanes = 3;   // mu, sigma, h
+constexpr int ROW_RMAX = 32;     // largest radix of the row transforms (column transforms: 16)
 
 // Per-kernel scalars, passed by value to the kernels that need them.
 struct KernelTable {
@@ -25,6 +26,8 @@ struct EpiParams {
     float* P_out;
     uint8_t* alpha_out;
     double* partials;          // [n_blocks][C][5] or null
+    float* stats_out;          // [C][3]; when set, the last block reduces the partials (streaming kernel)
+    unsigned int* ticket;      // completion counter for that reduction (0 between launches)
     const float* sin_y;
     const float* cos_y;
     const float* sin_x;
