@@ -42,6 +42,14 @@ class OracleCfg(ctypes.Structure):
                 ("eps_p", ctypes.c_double)]
 
 
+class OracleEvo(ctypes.Structure):
+    _fields_ = [("mut_p", ctypes.c_int), ("mut_k", ctypes.c_int), ("mut_x0", ctypes.c_int),
+                ("mut_y0", ctypes.c_int), ("mut_half", ctypes.c_int), ("mut_delta", ctypes.c_double),
+                ("pen_p", ctypes.c_int), ("pen_k", ctypes.c_int), ("pen_delta", ctypes.c_double),
+                ("gamma_mut", ctypes.c_double), ("gamma_pen", ctypes.c_double), ("eps_pen", ctypes.c_double),
+                ("r_oxy", ctypes.c_int)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP across output rows)."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -71,7 +79,13 @@ def _load():
                                         ctypes.POINTER(ctypes.c_ubyte)]
             lib.oracle_step.restype = ctypes.c_int
             lib.oracle_update.argtypes = [ctypes.POINTER(OracleCfg), ip, dp, dp, dp, dp, dp, dp, dp, dp,
-                                          ctypes.POINTER(ctypes.c_ubyte)]
+                                          ctypes.POINTER(ctypes.c_ubyte), dp]
+            lib.oracle_disk_mean.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp]
+            lib.oracle_evolve_step.argtypes = [ctypes.POINTER(OracleCfg), ip, ip, ip, dp, dp, dp, dp,
+                                               ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_ubyte),
+                                               ctypes.POINTER(OracleEvo), dp, dp, dp, dp,
+                                               ctypes.POINTER(ctypes.c_ubyte), dp, dp]
+            lib.oracle_evolve_step.restype = ctypes.c_int
             lib.oracle_update.restype = ctypes.c_int
             fp = ctypes.POINTER(ctypes.c_float)
             lib.oracle_step_sites.argtypes = [ctypes.POINTER(OracleCfg), ip, ip, ip, dp, dp, dp, dp,
@@ -228,10 +242,50 @@ def update(world, A, P, U, return_alpha=False):
     P_out = np.zeros_like(Pp) if Pp is not None else None
     alpha = np.zeros(A.shape[1:], np.uint8)
     rc = lib.oracle_update(ctypes.byref(args.cfg), args.ip(args.dst), _dp(args.h), _dp(args.mu),
-                           _dp(args.sg), _dp(A), _opt(Pp), _dp(U), _dp(A_out), _opt(P_out), _bp(alpha))
+                           _dp(args.sg), _dp(A), _opt(Pp), _dp(U), _dp(A_out), _opt(P_out), _bp(alpha),
+                           _NULL_D)
     if rc != 0:
         raise RuntimeError("oracle_update failed")
     return (A_out, P_out, alpha) if return_alpha else (A_out, P_out)
+
+
+def disk_mean(X, r):
+    """Periodic average over the disk |d| <= r."""
+    lib = _load()
+    X = _f64(X)
+    H, W = X.shape
+    out = np.zeros((H, W))
+    lib.oracle_disk_mean(H, W, _dp(X), int(r), _dp(out))
+    return out
+
+
+def evolve_step(world, events, walls=None, A=None, P=None, return_tsum=False):
+    """One step with walls, explosion penalisation and mutation (Algorithm 2,
+    Sections 2.5-2.7).  `events` holds the step's random choices (see
+    inputs.evolution_events); walls is a [H, W] 0/1 array or None.
+    Returns (A', P', alpha, E_pen) and, on request, sum_k t_k (the quantity
+    Delta_sum(U) thresholds)."""
+    lib = _load()
+    args = _Args(world)
+    A = _f64(world.A if A is None else A)
+    P = world.P if P is None else P
+    Pp = _f64(P) if (world.n_planes and P is not None) else None
+    A_out = np.zeros_like(A)
+    P_out = np.zeros_like(Pp) if Pp is not None else None
+    H, W = A.shape[1:]
+    alpha = np.zeros((H, W), np.uint8)
+    epen = np.zeros((H, W))
+    tsum = np.zeros((H, W))
+    wl = np.ascontiguousarray(walls, np.uint8) if walls is not None else None
+    ev = OracleEvo(events["mut_p"], events["mut_k"], events["mut_x0"], events["mut_y0"], events["mut_half"],
+                   events["mut_delta"], events["pen_p"], events["pen_k"], events["pen_delta"],
+                   events["gamma_mut"], events["gamma_pen"], events["eps_pen"], events["r_oxy"])
+    rc = lib.oracle_evolve_step(*args.kernel_args(), _bp(wl), ctypes.byref(ev), _dp(A), _opt(Pp),
+                                _dp(A_out), _opt(P_out), _bp(alpha), _dp(epen), _dp(tsum))
+    if rc != 0:
+        raise RuntimeError("oracle_evolve_step failed")
+    out = (A_out, P_out, alpha, epen)
+    return out + (tsum,) if return_tsum else out
 
 
 def step_sites(world, ys, xs, A=None, P=None):

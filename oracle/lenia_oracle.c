@@ -15,8 +15,8 @@
  *
  * Step order follows Algorithm 2 (intrinsic evolution loop): diffuse the
  * genospace, convolve the phenospace, compute alpha, mask the genospace,
- * growth mapping and clipped update.  Environment, E_pen, mutation and
- * penalization (the other lines of Algorithm 2) are not part of this step.
+ * growth mapping and clipped update.  oracle_evolve_step adds the other lines
+ * of Algorithm 2: environment (walls), E_pen, mutation and penalisation.
  *
  * Readings where the paper is silent or ambiguous (each one is also listed in
  * the design notes):
@@ -33,6 +33,17 @@
  *  R8 diffusion with no neighbour above eps_p gives 0.
  *  R9 g = 0 where the gene sigma is 0; the update uses the masked genes, so
  *     where alpha = 0 the growth is h*(2*0 - 1) = -h (form 0) or 0 (form 1).
+ *  R14 walls zero A and P at the wall sites before the step (the environment
+ *     line comes first in Algorithm 2); the step's own output is not masked.
+ *  R15 K_oxy is the disk |d|_2 <= r_oxy divided by its point count (like
+ *     K_diff, Section 2.3); Delta_sum(U) sums the per-kernel alpha tests of R5.
+ *  R16 "(x,y) in E_pen" reads E_pen > eps_pen, a parameter (default 0.5: at
+ *     the straight edge of a large body E_pen is 1/2).
+ *  R17 the mutation square is x in [x0 - s, x0 + s), y in [y0 - s, y0 + s),
+ *     periodic; delta and the centre are inputs (drawn by the caller).
+ *  R18 penalisation: p is the mu or the sigma plane, delta > 0 for mu and
+ *     delta < 0 for sigma (Figure 3's arrows); no clip after either operator
+ *     (the next step's diffusion clips to [0, 1]).
  */
 #include <math.h>
 #include <stdint.h>
@@ -192,23 +203,27 @@ static plane_map planes_of(int loc)
  *  a_in[c]: the site's state.  Writes a_out[c], p_out[pk] and returns alpha. */
 static int site_update(const oracle_cfg* cfg, plane_map pm, const int* dst, const double* h,
                        const double* mu, const double* sigma, const double* u, const double* ph,
-                       const double* a_in, double* a_out, double* p_out)
+                       const double* a_in, double* a_out, double* p_out, double* tsum_out)
 {
     const int K = cfg->K;
     double g[64];
     double hk[64];
     int alpha = 1;
+    double tsum = 0.0;
     for (int k = 0; k < K; k++) {
         double m = pm.p_mu >= 0 ? ph[pm.p_mu * K + k] : mu[k];
         double s = pm.p_sigma >= 0 ? ph[pm.p_sigma * K + k] : sigma[k];
         hk[k] = pm.p_h >= 0 ? ph[pm.p_h * K + k] : h[k];
         g[k] = growth_bump(u[k], m, s);
+        /* the per-kernel test of alpha (R5): growth h g, or the potential */
+        double t = cfg->alpha_on ? u[k] : hk[k] * g[k];
+        tsum += t;
         if (cfg->maintain) {
             /* Section 2.2: alpha = Delta_all(U) AND Delta_all(P) (R5). */
-            double t = cfg->alpha_on ? u[k] : hk[k] * g[k];
             if (!(t > cfg->eps_u)) alpha = 0;
         }
     }
+    if (tsum_out) *tsum_out = tsum;
     if (cfg->maintain)
         for (int pk = 0; pk < pm.n_p * K; pk++)
             if (!(ph[pk] > cfg->eps_p)) alpha = 0;
@@ -241,7 +256,7 @@ static int site_update(const oracle_cfg* cfg, plane_map pm, const int* dst, cons
  * U[K][H][W]: diffusion (or plain genes), then site_update everywhere. */
 int oracle_update(const oracle_cfg* cfg, const int* dst, const double* h, const double* mu,
                   const double* sigma, const double* A, const double* P, const double* U,
-                  double* A_out, double* P_out, unsigned char* alpha_out)
+                  double* A_out, double* P_out, unsigned char* alpha_out, double* tsum_out)
 {
     const int H = cfg->H, W = cfg->W, C = cfg->C, K = cfg->K;
     const size_t N = (size_t)H * W;
@@ -265,11 +280,13 @@ int oracle_update(const oracle_cfg* cfg, const int* dst, const double* h, const 
         for (int k = 0; k < K; k++) u[k] = U[(size_t)k * N + i];
         for (int pk = 0; pk < pm.n_p * K; pk++) ph[pk] = Ph[(size_t)pk * N + i];
         for (int c = 0; c < C; c++) a_in[c] = A[(size_t)c * N + i];
-        int alpha = site_update(cfg, pm, dst, h, mu, sigma, u, ph, a_in, a_out, p_out);
+        double ts = 0.0;
+        int alpha = site_update(cfg, pm, dst, h, mu, sigma, u, ph, a_in, a_out, p_out, &ts);
         for (int c = 0; c < C; c++) A_out[(size_t)c * N + i] = a_out[c];
         if (P_out)
             for (int pk = 0; pk < pm.n_p * K; pk++) P_out[(size_t)pk * N + i] = p_out[pk];
         if (alpha_out) alpha_out[i] = (unsigned char)alpha;
+        if (tsum_out) tsum_out[i] = ts;
     }
     free(Ph);
     return 0;
@@ -294,7 +311,7 @@ int oracle_step(const oracle_cfg* cfg, const int* src, const int* dst, const int
     double* U = (double*)malloc(sizeof(double) * (size_t)K * N);
     for (int k = 0; k < K; k++)
         oracle_potential(H, W, A + (size_t)src[k] * N, R[k], Kw + kw_off[k], U + (size_t)k * N, 0);
-    int rc = oracle_update(cfg, dst, h, mu, sigma, A, P, U, A_out, P_out, alpha_out);
+    int rc = oracle_update(cfg, dst, h, mu, sigma, A, P, U, A_out, P_out, alpha_out, NULL);
     if (U_out) memcpy(U_out, U, sizeof(double) * (size_t)K * N);
     free(U);
     return rc;
@@ -356,7 +373,7 @@ int oracle_step_sites(const oracle_cfg* cfg, const int* src, const int* dst, con
             ph[pk] = r;
         }
         for (int c = 0; c < C; c++) a_in[c] = (double)A[(size_t)c * N + (size_t)y * W + x];
-        int alpha = site_update(cfg, pm, dst, h, mu, sigma, u, ph, a_in, a_out, p_out);
+        int alpha = site_update(cfg, pm, dst, h, mu, sigma, u, ph, a_in, a_out, p_out, NULL);
         for (int c = 0; c < C; c++) A_out[(size_t)c * n + i] = a_out[c];
         if (P_out)
             for (int pk = 0; pk < pm.n_p * K; pk++) P_out[(size_t)pk * n + i] = p_out[pk];
@@ -367,6 +384,100 @@ int oracle_step_sites(const oracle_cfg* cfg, const int* src, const int* dst, con
         if (alpha_out) alpha_out[i] = (unsigned char)alpha;
     }
     return 0;
+}
+
+/* Normalised disk average over |d|_2 <= r (periodic):
+ * out(x) = sum_{|d| <= r} in(x + d) / #{|d| <= r}. */
+void oracle_disk_mean(int H, int W, const double* in, int r, double* out)
+{
+    int n = 0;
+    for (int dy = -r; dy <= r; dy++)
+        for (int dx = -r; dx <= r; dx++)
+            if (dy * dy + dx * dx <= r * r) n++;
+    #pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            double s = 0.0;
+            for (int dy = -r; dy <= r; dy++)
+                for (int dx = -r; dx <= r; dx++) {
+                    if (dy * dy + dx * dx > r * r) continue;
+                    s += in[(size_t)wrap(y + dy, H) * W + wrap(x + dx, W)];
+                }
+            out[(size_t)y * W + x] = s / (double)n;
+        }
+}
+
+/* Random choices of one step of Algorithm 2's evolutionary operators (drawn
+ * by the caller, so both implementations see the same ones):
+ *   mutation (Section 2.5): plane mut_p, kernel mut_k, delta mut_delta, square
+ *     of side 2 mut_half with corner (x0 - s, y0 - s), i.e. x in [x0 - s, x0 + s);
+ *   penalisation (Section 2.6): plane pen_p, kernel pen_k, delta pen_delta
+ *     (its sign chosen by the caller from the plane).
+ * A plane index < 0 switches that operator off. */
+typedef struct {
+    int mut_p, mut_k, mut_x0, mut_y0, mut_half;
+    double mut_delta;
+    int pen_p, pen_k;
+    double pen_delta;
+    double gamma_mut, gamma_pen, eps_pen;
+    int r_oxy;
+} oracle_evo;
+
+/* One step with Algorithm 2's remaining lines:
+ *   line 158: walls (walls[i] != 0) remove A and P before the step (Section 2.7);
+ *   lines 159-165: diffuse, convolve, alpha, mask, update (oracle_step);
+ *   line 164: E_oxy = (1 - Delta_sum(U)) * K_oxy, E_pen = (1 - E_oxy) * K_oxy,
+ *     Delta_sum(U) = [sum_k t_k > eps_u] with t_k the per-kernel alpha test,
+ *     K_oxy the normalised disk of radius r_oxy (Section 2.6);
+ *   line 166: P[mut_p, mut_k] += gamma_mut delta on the square AND alpha;
+ *   line 167: P[pen_p, pen_k] += gamma_pen delta on [E_pen > eps_pen] AND alpha.
+ * epen_out and tsum_out (nullable) receive E_pen and sum_k t_k. */
+int oracle_evolve_step(const oracle_cfg* cfg, const int* src, const int* dst, const int* R,
+                       const double* h, const double* mu, const double* sigma,
+                       const double* Kw, const long* kw_off, const unsigned char* walls,
+                       const oracle_evo* ev, const double* A, const double* P,
+                       double* A_out, double* P_out, unsigned char* alpha_out, double* epen_out,
+                       double* tsum_out)
+{
+    const int H = cfg->H, W = cfg->W, C = cfg->C, K = cfg->K;
+    const size_t N = (size_t)H * W;
+    const plane_map pm = planes_of(cfg->localized);
+    const size_t nP = (size_t)pm.n_p * K * N;
+    double* Aw = (double*)malloc(sizeof(double) * C * N);
+    double* Pw = nP ? (double*)malloc(sizeof(double) * nP) : NULL;
+    for (size_t i = 0; i < C * N; i++) Aw[i] = (walls && walls[i % N]) ? 0.0 : A[i];
+    for (size_t i = 0; i < nP; i++) Pw[i] = (walls && walls[i % N]) ? 0.0 : P[i];
+    double* U = (double*)malloc(sizeof(double) * (size_t)K * N);
+    for (int k = 0; k < K; k++)
+        oracle_potential(H, W, Aw + (size_t)src[k] * N, R[k], Kw + kw_off[k], U + (size_t)k * N, 0);
+    unsigned char* al = (unsigned char*)malloc(N);
+    double* tsum = (double*)malloc(sizeof(double) * N);
+    int rc = oracle_update(cfg, dst, h, mu, sigma, Aw, Pw, U, A_out, P_out, al, tsum);
+    double* empty = (double*)malloc(sizeof(double) * N);
+    double* eoxy = (double*)malloc(sizeof(double) * N);
+    double* epen = (double*)malloc(sizeof(double) * N);
+    for (size_t i = 0; i < N; i++) empty[i] = (tsum[i] > cfg->eps_u) ? 0.0 : 1.0;
+    oracle_disk_mean(H, W, empty, ev->r_oxy, eoxy);
+    for (size_t i = 0; i < N; i++) empty[i] = 1.0 - eoxy[i];
+    oracle_disk_mean(H, W, empty, ev->r_oxy, epen);
+    if (P_out && pm.n_p && ev->mut_p >= 0) {
+        double* mp = P_out + ((size_t)ev->mut_p * K + ev->mut_k) * N;
+        for (int dy = -ev->mut_half; dy < ev->mut_half; dy++)
+            for (int dx = -ev->mut_half; dx < ev->mut_half; dx++) {
+                size_t i = (size_t)wrap(ev->mut_y0 + dy, H) * W + wrap(ev->mut_x0 + dx, W);
+                if (al[i]) mp[i] += ev->gamma_mut * ev->mut_delta;
+            }
+    }
+    if (P_out && pm.n_p && ev->pen_p >= 0) {
+        double* pp = P_out + ((size_t)ev->pen_p * K + ev->pen_k) * N;
+        for (size_t i = 0; i < N; i++)
+            if (al[i] && epen[i] > ev->eps_pen) pp[i] += ev->gamma_pen * ev->pen_delta;
+    }
+    if (alpha_out) memcpy(alpha_out, al, N);
+    if (epen_out) memcpy(epen_out, epen, sizeof(double) * N);
+    if (tsum_out) memcpy(tsum_out, tsum, sizeof(double) * N);
+    free(Aw); free(Pw); free(U); free(al); free(tsum); free(empty); free(eoxy); free(epen);
+    return rc;
 }
 
 /* Per-channel mass and circular-mean centroid:

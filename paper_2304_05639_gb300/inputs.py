@@ -285,6 +285,42 @@ def workload(name: str) -> World:
     raise KeyError(name)
 
 
+def evolution_events(world: World, step: int, seed_index: int = 5, gamma_mut=1.0, gamma_pen=0.2,
+                     mut_half=4, r_oxy=3, eps_pen=0.01, delta_scale=0.01) -> dict:
+    """The random choices of one step of the evolutionary operators
+    (Sections 2.5-2.6), drawn from the counter-based stream (seed, step):
+    mutation plane, kernel, delta ~ U[-1, 1) * delta_scale and square centre;
+    penalisation plane (mu or sigma), kernel and |delta| ~ U[0, 1) * delta_scale
+    with sign +1 for mu (raise mu) and -1 for sigma (lower sigma).  The gamma,
+    square half-size, r_oxy and E_pen threshold are carried along."""
+    rng = Rng(BASE_SEED * 1000003 + seed_index * 7919 + step)
+    n_p = max(1, world.n_planes)
+    mut_p = int(rng.integers(1, 0, n_p - 1)[0])
+    mut_k = int(rng.integers(1, 0, world.n_kernels - 1)[0])
+    mut_delta = float(rng.uniform(1, -1.0, 1.0)[0]) * delta_scale
+    y0 = int(rng.integers(1, 0, world.height - 1)[0])
+    x0 = int(rng.integers(1, 0, world.width - 1)[0])
+    # penalisation acts on a localized mu or sigma plane
+    loc_bits = [b for b in (LOC_MU, LOC_SIGMA, LOC_H) if world.localized & b]
+    pen_choices = [p for p, bit in enumerate(loc_bits) if bit in (LOC_MU, LOC_SIGMA)]
+    pen_p = pen_choices[int(rng.integers(1, 0, len(pen_choices) - 1)[0])] if pen_choices else -1
+    pen_k = int(rng.integers(1, 0, world.n_kernels - 1)[0])
+    mag = float(rng.uniform(1)[0]) * delta_scale
+    sign = 1.0 if (pen_p >= 0 and loc_bits[pen_p] == LOC_MU) else -1.0
+    if world.n_planes == 0:
+        mut_p = pen_p = -1
+    return dict(mut_p=mut_p, mut_k=mut_k, mut_x0=x0, mut_y0=y0, mut_half=mut_half, mut_delta=mut_delta,
+                pen_p=pen_p, pen_k=pen_k, pen_delta=sign * mag, gamma_mut=gamma_mut, gamma_pen=gamma_pen,
+                eps_pen=eps_pen, r_oxy=r_oxy)
+
+
+def wall_strip(H: int, W: int, x0: int, width: int) -> np.ndarray:
+    """A vertical wall (Section 2.7): columns x0 .. x0 + width - 1, all rows."""
+    w = np.zeros((H, W), np.uint8)
+    w[:, x0:x0 + width] = 1
+    return w
+
+
 def random_field(seed: int, shape, lo=0.0, hi=1.0) -> np.ndarray:
     """Plain U[lo,hi) float32 array (for unit tests of single stages)."""
     n = int(math.prod(shape))
