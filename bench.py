@@ -192,6 +192,55 @@ def batched_leg(torch, lenia, inputs, stream, steps=200):
             "batched_over_plain": v / pv}
 
 
+def evolve_leg(torch, lenia, inputs, stream, plain_ms, steps=100):
+    """The headline world with Algorithm 2's evolutionary lines switched on:
+    an 8-column wall, one mutation and one penalisation per step (seeded
+    events, r_oxy = 4, square half-size 16), against the plain step."""
+    w = inputs.multi_channel()
+    H, W = w.height, w.width
+    cfg, ks = lenia.config_from_world(w)
+    ctx = lenia.lenia_init(cfg, ks, stream)
+    try:
+        lenia.lenia_set_walls(ctx, inputs.wall_strip(H, W, W // 2, 8))
+        evs = [lenia.events_struct(inputs.evolution_events(w, s, gamma_mut=1.0, gamma_pen=0.2, mut_half=16,
+                                                            r_oxy=4))
+               for s in range(steps + 3)]
+        bufs = [(torch.from_numpy(w.A).cuda(), torch.from_numpy(w.P).cuda())]
+        bufs.append((torch.empty_like(bufs[0][0]), torch.empty_like(bufs[0][1])))
+        st = torch.zeros((steps + 3, w.n_channels, 3), dtype=torch.float32, device="cuda")
+
+        def step(i):
+            (a, p), (a2, p2) = bufs[i % 2], bufs[(i + 1) % 2]
+            lenia.lenia_step_evolve(ctx, a, p, a2, p2, evs[i], st[i], None, None, stream)
+
+        for i in range(3):
+            step(i)
+        torch.cuda.synchronize()
+        lenia.lenia_profile_start(ctx, 16 * steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            step(3 + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = lenia.lenia_profile_stop(ctx)
+        lenia.lenia_check(ctx)
+        ms = e0.elapsed_time(e1) / steps
+    finally:
+        lenia.lenia_destroy(ctx)
+    sites = H * W
+    disk_ms = sum(prof[k][0] for k in ("oxy_disk", "pen_disk") if k in prof) / steps
+    # each disk pass reads its input (1 or 2 bytes per site) and the second the
+    # alpha byte, and writes 2 bytes (counts) or the touched gene values
+    disk_bytes = sites * (1 + 2) + sites * (2 + 1)
+    return {"workload": "2048x2048, 3 channels, 15 kernels R=18, walls + mutation + penalisation each step",
+            "steps": steps, "ms_per_step": ms, "value": sites / (ms / 1e3), "unit": UNIT,
+            "over_plain_step": ms / plain_ms,
+            "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
+            "disk_passes_gbs": disk_bytes / (disk_ms / 1e3) / 1e9 if disk_ms > 0 else None,
+            "stats_finite": bool(torch.isfinite(st).all())}
+
+
 def max_over_ranks(values, torch, device=None):
     """Element-wise max of a list of floats over all ranks (identity at N = 1)."""
     import torch.distributed as dist
@@ -408,6 +457,7 @@ def run_ours(args):
     if not args.no_extras and ws == 1 and args.size == 2048:
         line["adjoint"] = adjoint_leg(torch, lenia, inputs, stream)
         line["batched"] = batched_leg(torch, lenia, inputs, stream)
+        line["evolve"] = evolve_leg(torch, lenia, inputs, stream, t_max / args.steps)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -424,7 +474,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and batched-world legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched-world and evolution legs")
     ap.add_argument("--size", type=int, default=2048, help="torus side (2048 = the benchmark workload)")
     ap.add_argument("--conv-path", type=int, default=0, help="0 auto, 1 fft, 2 direct")
     args = ap.parse_args()

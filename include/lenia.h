@@ -171,6 +171,45 @@ LENIA_API lenia_status lenia_update_from_potentials(lenia_ctx* ctx, const float*
                                           const float* U_in, float* A_out, float* P_out,
                                           uint8_t* alpha_out, void* stream);
 
+/* ---- Evolutionary lines of Algorithm 2 (Sections 2.5-2.7).
+ * The random choices of one step, drawn by the caller (any generator can drive
+ * them, and a step is reproducible from its events):
+ *   mutation (Section 2.5): gene plane mut_plane (index among the localized
+ *     planes mu, sigma, h in that order; -1 = off), kernel mut_kernel, delta
+ *     mut_delta and the periodic square x in [mut_x0 - mut_half, mut_x0 +
+ *     mut_half), y likewise: P += gamma_mut * mut_delta there where alpha = 1.
+ *   penalisation (Section 2.6): plane pen_plane (-1 = off), kernel pen_kernel
+ *     and pen_delta (the caller picks its sign: > 0 on a mu plane, < 0 on a
+ *     sigma plane): P += gamma_pen * pen_delta where E_pen > eps_pen and
+ *     alpha = 1, with E_oxy = (1 - Delta_sum(U)) * K_oxy, E_pen = (1 - E_oxy)
+ *     * K_oxy and K_oxy the disk |d|_2 <= r_oxy (1..32) over its point count.
+ *     Delta_sum(U) thresholds the sum over kernels of the per-kernel alpha
+ *     test (h_k g_k, or U_k with alpha_on) at eps_u. */
+typedef struct {
+    int32_t mut_plane, mut_kernel, mut_x0, mut_y0, mut_half;
+    double mut_delta, gamma_mut;
+    int32_t pen_plane, pen_kernel;
+    double pen_delta, gamma_pen, eps_pen;
+    int32_t r_oxy;
+} lenia_events;
+
+/* Walls (Section 2.7): mask is a HOST array [H][W] of bytes, non-zero at wall
+ * sites, or NULL to remove every wall.  Synchronous; the context keeps a
+ * device list of the wall sites. */
+LENIA_API lenia_status lenia_set_walls(lenia_ctx* ctx, const uint8_t* mask);
+
+/* One step of Algorithm 2 with its evolutionary lines, in its order:
+ * (1) the walls zero A and P at their sites IN PLACE (A, P: the current
+ * state, device); (2) the step of lenia_step from (A, P) into (A_out, P_out);
+ * (3) E_pen from that step's Delta_sum(U); (4) mutation and (5) penalisation
+ * of P_out as `ev` (host) describes.  stats_out (C*3 floats), alpha_out
+ * ([H][W] bytes) and epen_out ([H][W] floats, E_pen) are nullable device
+ * outputs.  Without gene maps both operators must be off.  The first call
+ * allocates 4 bytes of scratch per site (synchronously). */
+LENIA_API lenia_status lenia_step_evolve(lenia_ctx* ctx, float* A, float* P, float* A_out, float* P_out,
+                                         const lenia_events* ev, float* stats_out, uint8_t* alpha_out,
+                                         float* epen_out, void* stream);
+
 /* Waits for `stream` and reads the context's device status word: returns
  * LENIA_ETIMEOUT (and clears the word) if a kernel gave up a bounded
  * device-side wait since the last check, else LENIA_OK.  lenia_step_host
@@ -197,7 +236,7 @@ LENIA_API lenia_status lenia_step_host(lenia_ctx* ctx, const float* A_in, const 
  * lenia_profile_stop waits for those events and fills total_ms[kind] (summed
  * milliseconds) and counts[kind] for the launch kinds 0..LENIA_PROFILE_KINDS-1
  * (names from lenia_profile_kind_name), then turns recording off. */
-#define LENIA_PROFILE_KINDS 7
+#define LENIA_PROFILE_KINDS 10
 LENIA_API lenia_status lenia_profile_start(lenia_ctx* ctx, int32_t max_launches);
 LENIA_API lenia_status lenia_profile_stop(lenia_ctx* ctx, float* total_ms, int32_t* counts);
 LENIA_API const char* lenia_profile_kind_name(int32_t kind);

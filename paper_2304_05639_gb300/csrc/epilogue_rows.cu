@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
             float ph[NPK > 0 ? NPK : 1];
             float pmin = 1.f;                  // min over the diffused genes
             float tmin = 3.4e38f;              // min over the alpha tests (h g, or U)
+            float tsum = 0.f;                  // their sum (Delta_sum)
             float acc[CT];
 #pragma unroll
             for (int c = 0; c < CT; c++) acc[c] = 0.f;
@@ -247,7 +248,9 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
                 const float hh = PH >= 0 ? ph[(PH >= 0 ? PH : 0) * KT + k] : p.kt.h[k];
                 const float z = (u - m) * rcp_approx(sg);
                 const float gk = sg > 0.f ? ex2_approx(-C_HALF_LOG2E * (z * z)) : 0.f;
-                tmin = fminf(tmin, p.alpha_on ? u : hh * gk);
+                const float tk = p.alpha_on ? u : hh * gk;
+                tmin = fminf(tmin, tk);
+                tsum += tk;
                 const float G = p.growth_form == 0 ? fmaf(2.f * gk, hh, -hh) : hh * gk;
                 const int d = TOPO ? paper_dst(k) : p.kt.dst[k];
 #pragma unroll
@@ -268,6 +271,7 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
                 st[c * 5 + 4] += an * cx;
             }
             if (p.alpha_out) p.alpha_out[gi] = alpha ? 1 : 0;
+            if (p.empty_out) p.empty_out[gi] = tsum > eps_u ? 0 : 1;
             if (p.P_out) {
                 const bool keep = !p.maintain || alpha;
 #pragma unroll

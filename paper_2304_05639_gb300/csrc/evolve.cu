@@ -1,0 +1,122 @@
+// The evolutionary lines of Algorithm 2 around the Lenia step:
+//   environment (Section 2.7): walls remove A and P at their sites before the step;
+//   penalising area (Section 2.6): E_oxy = (1 - Delta_sum(U)) * K_oxy,
+//     E_pen = (1 - E_oxy) * K_oxy, K_oxy the disk |d| <= r_oxy over its point count n;
+//   mutation (Section 2.5): P_{pk} += gamma_mut delta on a periodic square AND alpha;
+//   penalisation (Section 2.6): P_{pk} += gamma_pen delta on [E_pen > eps_pen] AND alpha.
+//
+// Both disk averages are taken on integer counts, so they are exact:
+//   c(x) = #{empty sites in the disk at x}        (E_oxy = c / n)
+//   M(x) = sum over the disk of (n - c)           (E_pen = M / n^2)
+// and the penalising test E_pen > eps_pen is M > floor(eps_pen n^2), decided
+// on the host in FP64 once per step.
+//
+// Each disk pass loads a (32 + 2r)^2 tile with its periodic halo into shared
+// memory, turns every tile row into exclusive prefix sums, and adds, for each
+// of the 2r + 1 rows of the disk, the difference of two prefix sums.
+#include "lenia_internal.cuh"
+
+namespace lenia {
+
+constexpr int DK_T = 32;        // output tile side
+constexpr int DK_THREADS = 256; // 32 x 8 threads, 4 output rows each
+
+__device__ __forceinline__ int wrap_i(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// PASS 1: empty (0/1 bytes) -> c.  PASS 2: c -> M, then mutation, penalisation
+// and the optional E_pen output at each site.
+template <int PASS>
+__global__ void __launch_bounds__(DK_THREADS) k_disk_pass(EvoParams p)
+{
+    extern __shared__ int pre[];                // [S][S + 1] exclusive row prefix sums
+    const int r = p.r_oxy;
+    const int S = DK_T + 2 * r;
+    const int SP = S + 1;                       // odd row pitch: the row scans hit distinct banks
+    const int y0 = blockIdx.y * DK_T - r, x0 = blockIdx.x * DK_T - r;
+    for (int e = threadIdx.x; e < S * S; e += DK_THREADS) {
+        const int ty = e / S, tx = e - ty * S;
+        const size_t gi = (size_t)wrap_i(y0 + ty, p.H) * p.W + wrap_i(x0 + tx, p.W);
+        pre[ty * SP + tx + 1] = PASS == 1 ? (int)p.empty[gi] : p.n_disk - (int)p.cnt_in[gi];
+    }
+    __syncthreads();
+    for (int row = threadIdx.x; row < S; row += DK_THREADS) {
+        int* q = pre + row * SP;
+        int run = 0;
+        q[0] = 0;
+        for (int j = 1; j <= S; j++) {
+            run += q[j];
+            q[j] = run;
+        }
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 31, tyb = threadIdx.x >> 5;
+    const int x = blockIdx.x * DK_T + tx;
+    if (x >= p.W) return;
+    const size_t N = (size_t)p.H * p.W;
+    for (int j = 0; j < DK_T / 8; j++) {
+        const int ty = tyb + 8 * j;
+        const int y = blockIdx.y * DK_T + ty;
+        if (y >= p.H) break;
+        int s = 0;
+        for (int dy = -r; dy <= r; dy++) {
+            const int hw = p.half_width[dy < 0 ? -dy : dy];
+            const int* q = pre + (ty + r + dy) * SP;
+            s += q[tx + r + hw + 1] - q[tx + r - hw];
+        }
+        const size_t i = (size_t)y * p.W + x;
+        if (PASS == 1) {
+            p.cnt_out[i] = (uint16_t)s;
+        } else {
+            if (p.epen_out) p.epen_out[i] = (float)((double)s / p.n_disk2);
+            if (p.alpha[i]) {
+                if (p.mut_plane >= 0 && wrap_i(x - p.mut_x0 + p.mut_half, p.W) < 2 * p.mut_half &&
+                    wrap_i(y - p.mut_y0 + p.mut_half, p.H) < 2 * p.mut_half)
+                    p.P[(size_t)p.mut_plane * N + i] += p.mut_add;
+                if (p.pen_plane >= 0 && (long long)s > p.pen_thresh)
+                    p.P[(size_t)p.pen_plane * N + i] += p.pen_add;
+            }
+        }
+    }
+}
+
+// A and P are zeroed at each listed wall site (in place).
+__global__ void k_walls_zero(const int* idx, int n, float* A, int C, float* P, int npk, size_t N)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const size_t i = (size_t)idx[t];
+    for (int c = 0; c < C; c++) A[(size_t)c * N + i] = 0.f;
+    for (int pk = 0; pk < npk; pk++) P[(size_t)pk * N + i] = 0.f;
+}
+
+size_t disk_pass_smem(int r)
+{
+    const int S = DK_T + 2 * r;
+    return (size_t)S * (S + 1) * sizeof(int);
+}
+
+cudaError_t launch_disk_pass(const EvoParams& p, int pass, cudaStream_t s)
+{
+    // at most (32 + 64) x 97 ints = 37 KB for r_oxy = 32: no opt-in needed
+    const size_t smem = disk_pass_smem(p.r_oxy);
+    const dim3 grid((p.W + DK_T - 1) / DK_T, (p.H + DK_T - 1) / DK_T);
+    if (pass == 1)
+        k_disk_pass<1><<<grid, DK_THREADS, smem, s>>>(p);
+    else
+        k_disk_pass<2><<<grid, DK_THREADS, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walls_zero(const int* idx, int n, float* A, int C, float* P, int npk, size_t N,
+                              cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_walls_zero<<<(n + 255) / 256, 256, 0, s>>>(idx, n, A, C, P, npk, N);
+    return cudaGetLastError();
+}
+
+}  // namespace lenia

@@ -62,6 +62,12 @@ struct lenia_ctx {
     double* d_gene_acc = nullptr;
     float2* d_Ahat_t = nullptr;            // spectra of up to 8 gradient planes (transposed conv)
     float2* d_Uhat_t = nullptr;
+    // evolutionary operators (lenia_set_walls, lenia_step_evolve)
+    int* d_walls = nullptr;                // wall site indices
+    int n_walls = 0;
+    uint8_t* d_alpha_e = nullptr;          // [H][W] alpha of the evolving step
+    uint8_t* d_empty = nullptr;            // [H][W] not Delta_sum(U)
+    uint16_t* d_cnt = nullptr;             // [H][W] empty sites per K_oxy disk
     // optional per-launch timing (lenia_profile_start / lenia_profile_stop)
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -71,8 +77,11 @@ struct lenia_ctx {
 
 // names of the launch kinds the profiler distinguishes
 static const char* kKindNames[] = {"rows_r2c", "cols_conv", "rows_c2r", "direct_conv", "epilogue",
-                                   "stats_partials", "stats_final"};
-enum { KIND_R2C, KIND_COLS, KIND_C2R, KIND_DIRECT, KIND_EPI, KIND_STATS_P, KIND_STATS_F, KIND_COUNT };
+                                   "stats_partials", "stats_final", "walls", "oxy_disk", "pen_disk"};
+enum { KIND_R2C, KIND_COLS, KIND_C2R, KIND_DIRECT, KIND_EPI, KIND_STATS_P, KIND_STATS_F, KIND_WALLS,
+       KIND_OXY, KIND_PEN, KIND_COUNT };
+static_assert(KIND_COUNT == LENIA_PROFILE_KINDS, "profile kinds and the header disagree");
+static_assert(sizeof(kKindNames) / sizeof(kKindNames[0]) == KIND_COUNT, "one name per profile kind");
 
 namespace {
 
@@ -326,7 +335,8 @@ lenia_status check_state_args(lenia_ctx* c, const float* A_in, const float* P_in
 }
 
 lenia_status step_impl(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
-                       float* stats_out, uint8_t* alpha_out, const float* U_given, cudaStream_t s)
+                       float* stats_out, uint8_t* alpha_out, const float* U_given, cudaStream_t s,
+                       uint8_t* empty_out = nullptr)
 {
     if (!U_given) {
         lenia_status st = potentials(c, A_in, c->d_U, s);
@@ -339,6 +349,7 @@ lenia_status step_impl(lenia_ctx* c, const float* A_in, const float* P_in, float
     ep.A_out = A_out;
     ep.P_out = c->n_p ? P_out : nullptr;
     ep.alpha_out = alpha_out;
+    ep.empty_out = empty_out;
     ep.partials = stats_out ? c->d_partials : nullptr;
     int nb = 0;
     bool fused_stats = false;
@@ -440,7 +451,8 @@ void lenia_destroy(lenia_ctx* c)
                     c->d_Ahat, c->d_Uhat, c->d_U, c->d_partials, c->d_trig, c->d_A2, c->d_P2,
                     c->d_A3, c->d_P3, c->d_stats, c->d_status, c->d_ckpt, c->d_seg, c->d_gA[0],
                     c->d_gA[1], c->d_gpre, c->d_gU, c->d_V, c->d_gene_part, c->d_gene_acc,
-                    c->d_Ahat_t, c->d_Uhat_t, c->d_ticket};
+                    c->d_Ahat_t, c->d_Uhat_t, c->d_ticket, c->d_walls, c->d_alpha_e, c->d_empty,
+                    c->d_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -837,6 +849,106 @@ lenia_status lenia_update_from_potentials(lenia_ctx* c, const float* A_in, const
     if (st != LENIA_OK) return st;
     if (!U_in) return fail(c, LENIA_EINVAL, "U_in must be non-null");
     return step_impl(c, A_in, P_in, A_out, P_out, nullptr, alpha_out, U_in, (cudaStream_t)stream);
+}
+
+lenia_status lenia_set_walls(lenia_ctx* c, const uint8_t* mask)
+{
+    if (!c) return LENIA_EINVAL;
+    std::vector<int> idx;
+    if (mask)
+        for (size_t i = 0; i < c->N; i++)
+            if (mask[i]) idx.push_back((int)i);
+    if (c->d_walls) {
+        CUDA_OR_FAIL(c, cudaFree(c->d_walls));
+        c->d_walls = nullptr;
+    }
+    c->n_walls = 0;
+    if (idx.empty()) return LENIA_OK;
+    lenia_status st = dalloc(c, &c->d_walls, idx.size());
+    if (st != LENIA_OK) return st;
+    CUDA_OR_FAIL(c, cudaMemcpy(c->d_walls, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    c->n_walls = (int)idx.size();
+    return LENIA_OK;
+}
+
+lenia_status lenia_step_evolve(lenia_ctx* c, float* A, float* P, float* A_out, float* P_out,
+                               const lenia_events* ev, float* stats_out, uint8_t* alpha_out, float* epen_out,
+                               void* stream)
+{
+    lenia_status st = check_state_args(c, A, P, A_out, P_out);
+    if (st != LENIA_OK) return st;
+    if (!ev) return fail(c, LENIA_EINVAL, "ev must be non-null");
+    const int H = c->cfg.height, W = c->cfg.width, K = c->cfg.n_kernels;
+    if (ev->r_oxy < 1 || ev->r_oxy > kMaxROxy || 2 * ev->r_oxy + 1 > std::min(H, W))
+        return fail(c, LENIA_EINVAL, "r_oxy must be 1..32 and 2 r_oxy + 1 <= min(H, W)");
+    if (!isfinite(ev->mut_delta) || !isfinite(ev->gamma_mut) || !isfinite(ev->pen_delta) ||
+        !isfinite(ev->gamma_pen) || !isfinite(ev->eps_pen))
+        return fail(c, LENIA_EINVAL, "event deltas, rates and eps_pen must be finite");
+    if (ev->mut_plane < -1 || ev->mut_plane >= c->n_p || ev->pen_plane < -1 || ev->pen_plane >= c->n_p)
+        return fail(c, LENIA_EINVAL, "mut_plane and pen_plane must be -1 or a localized gene plane");
+    if (ev->mut_plane >= 0 &&
+        (ev->mut_kernel < 0 || ev->mut_kernel >= K || ev->mut_x0 < 0 || ev->mut_x0 >= W || ev->mut_y0 < 0 ||
+         ev->mut_y0 >= H || ev->mut_half < 0 || 2 * ev->mut_half > std::min(H, W)))
+        return fail(c, LENIA_EINVAL, "mutation kernel, centre or half-size out of range");
+    if (ev->pen_plane >= 0 && (ev->pen_kernel < 0 || ev->pen_kernel >= K))
+        return fail(c, LENIA_EINVAL, "pen_kernel out of range");
+    if (!c->d_empty) {
+        st = dalloc(c, &c->d_alpha_e, c->N);
+        if (st == LENIA_OK) st = dalloc(c, &c->d_empty, c->N);
+        if (st == LENIA_OK) st = dalloc(c, &c->d_cnt, c->N);
+        if (st != LENIA_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // (1) environment: walls remove material from the current state
+    if (c->n_walls > 0) {
+        ProfScope ps(c, KIND_WALLS, s);
+        CUDA_OR_FAIL(c, launch_walls_zero(c->d_walls, c->n_walls, A, c->cfg.n_channels, P, c->n_p * K, c->N, s));
+    }
+    // (2) the step, with its alpha and not-Delta_sum(U) masks
+    uint8_t* alpha = alpha_out ? alpha_out : c->d_alpha_e;
+    st = step_impl(c, A, P, A_out, P_out, stats_out, alpha, nullptr, s, c->d_empty);
+    if (st != LENIA_OK) return st;
+    // (3)-(5) penalising area, mutation, penalisation
+    EvoParams e;
+    memset(&e, 0, sizeof(e));
+    e.empty = c->d_empty;
+    e.cnt_in = c->d_cnt;
+    e.cnt_out = c->d_cnt;
+    e.alpha = alpha;
+    e.P = c->n_p ? P_out : nullptr;
+    e.epen_out = epen_out;
+    e.H = H;
+    e.W = W;
+    e.r_oxy = ev->r_oxy;
+    int n = 0;
+    for (int dy = 0; dy <= ev->r_oxy; dy++) {
+        int w = 0;
+        while ((w + 1) * (w + 1) + dy * dy <= ev->r_oxy * ev->r_oxy) w++;
+        e.half_width[dy] = w;
+        n += (dy == 0 ? 1 : 2) * (2 * w + 1);
+    }
+    e.n_disk = n;
+    e.n_disk2 = (double)n * n;
+    e.mut_plane = ev->mut_plane >= 0 ? ev->mut_plane * K + ev->mut_kernel : -1;
+    e.pen_plane = ev->pen_plane >= 0 ? ev->pen_plane * K + ev->pen_kernel : -1;
+    e.mut_x0 = ev->mut_x0;
+    e.mut_y0 = ev->mut_y0;
+    e.mut_half = ev->mut_half;
+    e.mut_add = (float)(ev->gamma_mut * ev->mut_delta);
+    e.pen_add = (float)(ev->gamma_pen * ev->pen_delta);
+    // E_pen > eps_pen  <=>  M > eps_pen n^2  <=>  M > floor(eps_pen n^2) for integer M
+    const double t = floor(ev->eps_pen * e.n_disk2);
+    e.pen_thresh = t < -1.0 ? -1LL : (t > e.n_disk2 ? (long long)e.n_disk2 : (long long)t);
+    if (!c->n_p) e.mut_plane = e.pen_plane = -1;
+    {
+        ProfScope ps(c, KIND_OXY, s);
+        CUDA_OR_FAIL(c, launch_disk_pass(e, 1, s));
+    }
+    {
+        ProfScope ps(c, KIND_PEN, s);
+        CUDA_OR_FAIL(c, launch_disk_pass(e, 2, s));
+    }
+    return LENIA_OK;
 }
 
 lenia_status lenia_check(lenia_ctx* c, void* stream)

@@ -25,6 +25,7 @@ struct EpiParams {
     float* A_out;
     float* P_out;
     uint8_t* alpha_out;
+    uint8_t* empty_out;        // 1 where sum_k t_k <= eps_u (not Delta_sum(U)), or null
     double* partials;          // [n_blocks][C][5] or null
     float* stats_out;          // [C][3]; when set, the last block reduces the partials (streaming kernel)
     unsigned int* ticket;      // completion counter for that reduction (0 between launches)
@@ -40,6 +41,24 @@ struct EpiParams {
     // -sum_{dst(k)=c} h_k for the signed form with global h, else 0
     float acc0[kMaxChannels];
     KernelTable kt;
+};
+
+// Walls, penalising area, mutation and penalisation (Sections 2.5-2.7).
+constexpr int kMaxROxy = 32;
+struct EvoParams {
+    const uint8_t* empty;      // [H][W] 1 where Delta_sum(U) is false
+    const uint16_t* cnt_in;    // [H][W] empty sites in each disk (pass 2 input)
+    uint16_t* cnt_out;         // same buffer, pass 1 output
+    const uint8_t* alpha;      // [H][W] alpha mask of the step
+    float* P;                  // P' [n_p K][H][W], updated in place
+    float* epen_out;           // [H][W] E_pen or null
+    int H, W, r_oxy, n_disk;
+    double n_disk2;            // n_disk^2
+    int half_width[kMaxROxy + 1];   // largest w with w^2 + dy^2 <= r^2, per |dy|
+    int mut_plane, pen_plane;  // plane p K + k, or -1 (operator off)
+    int mut_x0, mut_y0, mut_half;
+    float mut_add, pen_add;    // gamma delta, rounded once from FP64
+    long long pen_thresh;      // penalise where M > pen_thresh
 };
 
 // Direct periodic convolution of every kernel.
@@ -110,5 +129,9 @@ bool epilogue_rows_supported(const EpiParams& p);
 cudaError_t launch_epilogue_rows(const EpiParams& p, int num_sms, int* status, cudaStream_t s, int* n_blocks);
 bool fft_size_supported(int H, int W);
 int epilogue_blocks(int H, int W);
+// pass 1: Delta_sum complement -> counts; pass 2: E_pen, mutation, penalisation
+cudaError_t launch_disk_pass(const EvoParams& p, int pass, cudaStream_t s);
+cudaError_t launch_walls_zero(const int* idx, int n, float* A, int C, float* P, int npk, size_t N,
+                              cudaStream_t s);
 
 }  // namespace lenia

@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
             }
         }
         float acc[CT];
+        float tsum = 0.f;                  // sum of the alpha tests (Delta_sum)
 #pragma unroll
         for (int c = 0; c < CT; c++) acc[c] = 0.f;
 #pragma unroll
@@ -191,7 +192,9 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
                 const float z = (u - m) / sg;
                 gk = expf(-0.5f * z * z);
             }
-            if (p.maintain) alpha = alpha && ((p.alpha_on ? u : hh * gk) > eps_u);
+            const float t = p.alpha_on ? u : hh * gk;
+            tsum += t;
+            if (p.maintain) alpha = alpha && (t > eps_u);
             const float G = p.growth_form == 0 ? hh * (2.f * gk - 1.f) : hh * gk;
             const int d = p.kt.dst[k];
 #pragma unroll
@@ -221,6 +224,7 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
                     p.P_out[(size_t)pk * N + i] = (p.maintain && !alpha) ? 0.f : ph[pk];
             }
             if (p.alpha_out) p.alpha_out[i] = alpha ? 1 : 0;
+            if (p.empty_out) p.empty_out[i] = tsum > eps_u ? 0 : 1;
         }
     }
     if (p.partials) block_stats<CT>(st, CT, p.partials);
@@ -270,6 +274,7 @@ __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
             ph[pk] = v;
         }
         float acc[kMaxChannels];
+        float tsum = 0.f;                  // sum of the alpha tests (Delta_sum)
         for (int c = 0; c < C; c++) acc[c] = 0.f;
         for (int k = 0; k < K; k++) {
             const float u = __ldg(&p.U[(size_t)k * N + i]);
@@ -281,7 +286,9 @@ __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
                 const float z = (u - m) / sg;
                 gk = expf(-0.5f * z * z);
             }
-            if (p.maintain) alpha = alpha && ((p.alpha_on ? u : hh * gk) > p.eps_u);
+            const float t = p.alpha_on ? u : hh * gk;
+            tsum += t;
+            if (p.maintain) alpha = alpha && (t > p.eps_u);
             acc[p.kt.dst[k]] += p.growth_form == 0 ? hh * (2.f * gk - 1.f) : hh * gk;
         }
         if (!p.maintain) alpha = true;
@@ -302,6 +309,7 @@ __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
                 for (int pk = 0; pk < npk; pk++)
                     p.P_out[(size_t)pk * N + i] = (p.maintain && !alpha) ? 0.f : ph[pk];
             if (p.alpha_out) p.alpha_out[i] = alpha ? 1 : 0;
+            if (p.empty_out) p.empty_out[i] = tsum > p.eps_u ? 0 : 1;
         }
     }
     if (p.partials) block_stats<kMaxChannels>(st, C, p.partials);

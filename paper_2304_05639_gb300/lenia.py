@@ -27,8 +27,8 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_last_error", "lenia_status_string", "lenia_destroy", "lenia_profile_start",
            "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes", "lenia_batch_init",
            "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy",
-           "lenia_selftest_wait_timeout")
-PROFILE_KINDS = 7
+           "lenia_selftest_wait_timeout", "lenia_set_walls", "lenia_step_evolve")
+PROFILE_KINDS = 10
 
 
 class LeniaError(RuntimeError):
@@ -54,6 +54,23 @@ class LeniaKernelDesc(ctypes.Structure):
                 ("n_shells", ctypes.c_int32), ("beta", ctypes.c_double * 4),
                 ("bump", ctypes.c_double * 6), ("h", ctypes.c_float),
                 ("mu", ctypes.c_float), ("sigma", ctypes.c_float)]
+
+
+class LeniaEvents(ctypes.Structure):
+    _fields_ = [("mut_plane", ctypes.c_int32), ("mut_kernel", ctypes.c_int32),
+                ("mut_x0", ctypes.c_int32), ("mut_y0", ctypes.c_int32), ("mut_half", ctypes.c_int32),
+                ("mut_delta", ctypes.c_double), ("gamma_mut", ctypes.c_double),
+                ("pen_plane", ctypes.c_int32), ("pen_kernel", ctypes.c_int32),
+                ("pen_delta", ctypes.c_double), ("gamma_pen", ctypes.c_double),
+                ("eps_pen", ctypes.c_double), ("r_oxy", ctypes.c_int32)]
+
+
+def events_struct(ev: dict) -> LeniaEvents:
+    """LeniaEvents from a dict of one step's random choices (the keys of
+    inputs.evolution_events)."""
+    return LeniaEvents(ev["mut_p"], ev["mut_k"], ev["mut_x0"], ev["mut_y0"], ev["mut_half"],
+                       ev["mut_delta"], ev["gamma_mut"], ev["pen_p"], ev["pen_k"], ev["pen_delta"],
+                       ev["gamma_pen"], ev["eps_pen"], ev["r_oxy"])
 
 
 _lib = None
@@ -125,6 +142,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_selftest_wait_timeout.restype = st
     lib.lenia_set_genes.argtypes = [vp, vp]
     lib.lenia_set_genes.restype = st
+    lib.lenia_set_walls.argtypes = [vp, vp]
+    lib.lenia_set_walls.restype = st
+    lib.lenia_step_evolve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(LeniaEvents), vp, vp, vp, vp]
+    lib.lenia_step_evolve.restype = st
     lib.lenia_check.argtypes = [vp, vp]
     lib.lenia_check.restype = st
     lib.lenia_destroy.argtypes = [vp]
@@ -274,6 +295,23 @@ def lenia_update_from_potentials(ctx, A_in, P_in, U_in, A_out, P_out, alpha_out=
     _check(ctx, load().lenia_update_from_potentials(ctx, _ptr(A_in), _ptr(P_in), _ptr(U_in),
                                                     _ptr(A_out), _ptr(P_out), _ptr(alpha_out),
                                                     _stream(stream)))
+
+
+def lenia_set_walls(ctx, mask):
+    """mask: host [H, W] array (non-zero = wall) or None to remove the walls."""
+    if mask is None:
+        _check(ctx, load().lenia_set_walls(ctx, None))
+        return
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    _check(ctx, load().lenia_set_walls(ctx, m.ctypes.data))
+
+
+def lenia_step_evolve(ctx, A, P, A_out, P_out, events, stats_out=None, alpha_out=None, epen_out=None,
+                      stream=None):
+    """events: a LeniaEvents or a dict with the keys of inputs.evolution_events."""
+    ev = events if isinstance(events, LeniaEvents) else events_struct(events)
+    _check(ctx, load().lenia_step_evolve(ctx, _ptr(A), _ptr(P), _ptr(A_out), _ptr(P_out), ctypes.byref(ev),
+                                         _ptr(stats_out), _ptr(alpha_out), _ptr(epen_out), _stream(stream)))
 
 
 def lenia_step_host(ctx, A_in, P_in, A_out, P_out, stats_out=None, stream=None):

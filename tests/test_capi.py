@@ -79,3 +79,29 @@ def test_status_strings(lib):
     assert lib.lenia_status_string(1) == b"invalid argument"
     assert lib.lenia_last_error(None) == b"null context"
     lib.lenia_destroy(None)               # no-op
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of lenia_config, lenia_kernel_desc and lenia_events
+    have the C compiler's sizes and field offsets."""
+    structs = {"lenia_config": lenia.LeniaConfig, "lenia_kernel_desc": lenia.LeniaKernelDesc,
+               "lenia_events": lenia.LeniaEvents}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lenia.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, v = line.split()
+        got[(cname, field)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
