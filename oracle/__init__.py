@@ -30,7 +30,7 @@ _LIB_PATH = os.path.join(_BUILD, "liblenia_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LOC_MU, LOC_SIGMA, LOC_H = 1, 2, 4
+LOC_MU, LOC_SIGMA, LOC_H, LOC_KERNEL = 1, 2, 4, 8
 
 
 class OracleCfg(ctypes.Structure):
@@ -39,7 +39,7 @@ class OracleCfg(ctypes.Structure):
                 ("growth_form", ctypes.c_int), ("localized", ctypes.c_int),
                 ("maintain", ctypes.c_int), ("r_diff", ctypes.c_int),
                 ("alpha_on", ctypes.c_int), ("eps_u", ctypes.c_double),
-                ("eps_p", ctypes.c_double)]
+                ("eps_p", ctypes.c_double), ("n_rings", ctypes.c_int)]
 
 
 class OracleEvo(ctypes.Structure):
@@ -93,6 +93,15 @@ def _load():
                                               ip, ip, dp, dp, dp, dp, ctypes.POINTER(ctypes.c_ubyte)]
             lib.oracle_step_sites.restype = ctypes.c_int
             lib.oracle_stats.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+            lib.oracle_ring_counts.argtypes = [ctypes.c_int, ctypes.c_int, dp]
+            lib.oracle_ring_potentials.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp]
+            ub = ctypes.POINTER(ctypes.c_ubyte)
+            lib.oracle_ring_step.argtypes = [ctypes.POINTER(OracleCfg), ip, ip, ctypes.c_int, dp, dp, dp, dp, dp,
+                                             dp, dp, dp, ub]
+            lib.oracle_ring_step.restype = ctypes.c_int
+            lib.oracle_ring_update.argtypes = [ctypes.POINTER(OracleCfg), ip, ip, ctypes.c_int, dp, dp, dp, dp, dp,
+                                               dp, dp, dp, dp, ub, dp]
+            lib.oracle_ring_update.restype = ctypes.c_int
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -174,7 +183,8 @@ class _Args:
         self.Kw = _f64(np.concatenate([k.ravel() for k in ks]))
         self.cfg = OracleCfg(world.height, world.width, world.n_channels, K, float(world.dt),
                              world.growth_form, world.localized, world.maintain_genes, world.r_diff,
-                             world.alpha_on, float(world.eps_u), float(world.eps_p))
+                             world.alpha_on, float(world.eps_u), float(world.eps_p),
+                             int(getattr(world, "n_rings", 0)))
         ia = lambda v: np.ascontiguousarray(np.asarray(v, np.int32))
         self.src = ia([k.src for k in world.kernels])
         self.dst = ia([k.dst for k in world.kernels])
@@ -286,6 +296,70 @@ def evolve_step(world, events, walls=None, A=None, P=None, return_tsum=False):
         raise RuntimeError("oracle_evolve_step failed")
     out = (A_out, P_out, alpha, epen)
     return out + (tsum,) if return_tsum else out
+
+
+def ring_counts(R: int, n: int) -> np.ndarray:
+    """Pixel count of each of the n rings of a radius-R disk (Section 2.4)."""
+    out = np.zeros(n)
+    _load().oracle_ring_counts(int(R), int(n), _dp(out))
+    return out
+
+
+def ring_potentials(X, R: int, n: int) -> np.ndarray:
+    """K_r * X for the n rings of a radius-R disk: [n, H, W] (Section 2.4)."""
+    X = _f64(X)
+    H, W = X.shape
+    out = np.zeros((n, H, W))
+    _load().oracle_ring_potentials(H, W, _dp(X), int(R), int(n), _dp(out))
+    return out
+
+
+def _ring_radius(world):
+    radii = {k.radius for k in world.kernels}
+    if len(radii) != 1:
+        raise ValueError("ring decomposition needs one kernel radius")
+    return radii.pop()
+
+
+def ring_step(world, A=None, P=None, return_u=False, return_alpha=False):
+    """One step of a world with ring-wise localized kernel genes (Algorithm 2
+    with Section 2.4's ring decomposition).  Returns (A', P') and, on request,
+    the recombined potentials U[K, H, W] and alpha[H, W]."""
+    lib = _load()
+    args = _Args(world)
+    A = _f64(world.A if A is None else A)
+    Pp = _f64(world.P if P is None else P)
+    A_out, P_out = np.zeros_like(A), np.zeros_like(Pp)
+    H, W = A.shape[1:]
+    U = np.zeros((world.n_kernels, H, W))
+    alpha = np.zeros((H, W), np.uint8)
+    rc = lib.oracle_ring_step(ctypes.byref(args.cfg), args.ip(args.src), args.ip(args.dst), _ring_radius(world),
+                              _dp(args.h), _dp(args.mu), _dp(args.sg), _dp(A), _dp(Pp), _dp(A_out), _dp(P_out),
+                              _dp(U), _bp(alpha))
+    if rc != 0:
+        raise RuntimeError("oracle_ring_step failed")
+    out = [A_out, P_out]
+    if return_u:
+        out.append(U)
+    if return_alpha:
+        out.append(alpha)
+    return tuple(out)
+
+
+def ring_update(world, A, P, V, return_alpha=False):
+    """The ring step after the ring convolutions, from given ring potentials
+    V[C, n_rings, H, W]."""
+    lib = _load()
+    args = _Args(world)
+    A, Pp, V = _f64(A), _f64(P), _f64(V)
+    A_out, P_out = np.zeros_like(A), np.zeros_like(Pp)
+    alpha = np.zeros(A.shape[1:], np.uint8)
+    rc = lib.oracle_ring_update(ctypes.byref(args.cfg), args.ip(args.src), args.ip(args.dst), _ring_radius(world),
+                                _dp(args.h), _dp(args.mu), _dp(args.sg), _dp(A), _dp(Pp), _dp(V), _dp(A_out),
+                                _dp(P_out), _NULL_D, _bp(alpha), _NULL_D)
+    if rc != 0:
+        raise RuntimeError("oracle_ring_update failed")
+    return (A_out, P_out, alpha) if return_alpha else (A_out, P_out)
 
 
 def step_sites(world, ys, xs, A=None, P=None):

@@ -44,6 +44,16 @@
  *  R18 penalisation: p is the mu or the sigma plane, delta > 0 for mu and
  *     delta < 0 for sigma (Figure 3's arrows); no clip after either operator
  *     (the next step's diffusion clips to [0, 1]).
+ *  R19 rings (Section 2.4): ring r of a radius-R kernel in n rings holds the
+ *     offsets with r <= n |d|_2 / R < r + 1 and |d|_2 < R (binary masks, so
+ *     K_r * 1 is the ring's point count); every kernel shares one radius.
+ *  R20 the ring weight evaluates the kernel function at r / n (the ring's
+ *     inner radius), as written; k(x; r, w, b) = 0 where w <= 0.
+ *  R21 the weighted sum uses the diffused, unmasked kernel genes (it comes
+ *     between diffusion and alpha in Algorithm 2); U = 0 where the
+ *     normalising sum is <= 0.
+ *  R22 gene planes: m, s, h (the localized ones), then r1, w1, b1, r2, w2, b2;
+ *     all of them take part in diffusion, Delta_all(P) and masking.
  */
 #include <math.h>
 #include <stdint.h>
@@ -53,6 +63,8 @@
 #define LOC_MU 1
 #define LOC_SIGMA 2
 #define LOC_H 4
+#define LOC_KERNEL 8      /* ring-wise kernel genes r1, w1, b1, r2, w2, b2 (Section 2.4) */
+#define MAX_PK 576        /* 9 gene types x 64 kernels */
 
 /* Lenia kernel core (original Lenia, cited in Section 1.2): a smooth bump on
  * (0,1) with value 1 at q = 1/2 and limit 0 at both ends. */
@@ -182,10 +194,13 @@ typedef struct {
     double dt;
     int growth_form, localized, maintain, r_diff, alpha_on;
     double eps_u, eps_p;
+    int n_rings;          /* > 0 with LOC_KERNEL: ring decomposition, Section 2.4 */
 } oracle_cfg;
 
+/* Gene planes in P, in this order: the localized growth genes m, s, h, then
+ * (LOC_KERNEL) the six kernel genes r1, w1, b1, r2, w2, b2 of Section 2.1. */
 typedef struct {
-    int n_p, p_mu, p_sigma, p_h;
+    int n_p, p_mu, p_sigma, p_h, p_kern;
 } plane_map;
 
 static plane_map planes_of(int loc)
@@ -195,7 +210,89 @@ static plane_map planes_of(int loc)
     m.p_mu = (loc & LOC_MU) ? 0 : -1;
     m.p_sigma = (loc & LOC_SIGMA) ? ((loc & LOC_MU) ? 1 : 0) : -1;
     m.p_h = (loc & LOC_H) ? m.n_p - 1 : -1;
+    m.p_kern = -1;
+    if (loc & LOC_KERNEL) {
+        m.p_kern = m.n_p;
+        m.n_p += 6;
+    }
     return m;
+}
+
+/* Ring of offset (dy, dx) for a radius-R kernel cut into n rings
+ * (Section 2.4): the ring index r with r <= n |d|_2 / R < r + 1, for
+ * |d|_2 < R; -1 outside.  Decided in integers: r = max{m : m^2 R^2 <= n^2 |d|^2}. */
+static int ring_of(int dy, int dx, int R, int n)
+{
+    const long long q = (long long)dy * dy + (long long)dx * dx;
+    if (q >= (long long)R * R) return -1;
+    int m = (int)floor((double)n * sqrt((double)q) / (double)R);
+    while ((long long)(m + 1) * (m + 1) * R * R <= (long long)n * n * q) m++;
+    while (m > 0 && (long long)m * m * R * R > (long long)n * n * q) m--;
+    return m;
+}
+
+/* Pixel count of every ring, K_r * 1 = sum over the ring (Section 2.4). */
+void oracle_ring_counts(int R, int n, double* cnt)
+{
+    for (int r = 0; r < n; r++) cnt[r] = 0.0;
+    for (int dy = -R; dy <= R; dy++)
+        for (int dx = -R; dx <= R; dx++) {
+            int r = ring_of(dy, dx, R, n);
+            if (r >= 0) cnt[r] += 1.0;
+        }
+}
+
+/* Ring potentials K_r * A of one plane for every ring r (Section 2.4,
+ * "the rings are convolved with the phenospace"): V[r][y][x] =
+ * sum_{d in ring r} A(y - dy, x - dx), periodic.  One pass over the disk per
+ * site, each tap added to its ring's sum. */
+void oracle_ring_potentials(int H, int W, const double* A, int R, int n, double* V)
+{
+    const size_t N = (size_t)H * W;
+    #pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; y++) {
+        double acc[256];
+        for (int x = 0; x < W; x++) {
+            for (int r = 0; r < n; r++) acc[r] = 0.0;
+            for (int dy = -R; dy <= R; dy++) {
+                const double* arow = A + (size_t)wrap(y - dy, H) * W;
+                for (int dx = -R; dx <= R; dx++) {
+                    int r = ring_of(dy, dx, R, n);
+                    if (r < 0) continue;
+                    acc[r] += arow[wrap(x - dx, W)];
+                }
+            }
+            for (int r = 0; r < n; r++) V[(size_t)r * N + (size_t)y * W + x] = acc[r];
+        }
+    }
+}
+
+/* Kernel function of Section 2.4, k(x; r, w, b) = b exp(-(x - r)^2 / 2 w^2);
+ * 0 where w <= 0 (as for a zero growth width, R9). */
+static double kernel_fn(double x, double r, double w, double b)
+{
+    if (!(w > 0.0)) return 0.0;
+    return b * exp(-(x - r) * (x - r) / (2.0 * w * w));
+}
+
+/* Potential of kernel k at one site from the ring potentials (Section 2.4):
+ *   k_r = sum_i k(r / n_ring; r_i, w_i, b_i) with the site's kernel genes,
+ *   U = sum_r k_r (K_r * A) / sum_r k_r (K_r * 1),  0 where the denominator is <= 0.
+ * vr[r] holds (K_r * A_src(k)) at the site; ph the site's (diffused) genes. */
+static double ring_recombine(int n, const double* vr, const double* cnt, const double* ph,
+                             plane_map pm, int K, int k)
+{
+    const double r1 = ph[(pm.p_kern + 0) * K + k], w1 = ph[(pm.p_kern + 1) * K + k];
+    const double b1 = ph[(pm.p_kern + 2) * K + k], r2 = ph[(pm.p_kern + 3) * K + k];
+    const double w2 = ph[(pm.p_kern + 4) * K + k], b2 = ph[(pm.p_kern + 5) * K + k];
+    double num = 0.0, den = 0.0;
+    for (int r = 0; r < n; r++) {
+        const double x = (double)r / (double)n;
+        const double kr = kernel_fn(x, r1, w1, b1) + kernel_fn(x, r2, w2, b2);
+        num += kr * vr[r];
+        den += kr * cnt[r];
+    }
+    return den > 0.0 ? num / den : 0.0;
 }
 
 /* Growth, alpha mask, genospace masking and clipped update at one site.
@@ -252,16 +349,22 @@ static int site_update(const oracle_cfg* cfg, plane_map pm, const int* dst, cons
     return alpha;
 }
 
-/* The step after the convolution, on the whole grid, from given potentials
- * U[K][H][W]: diffusion (or plain genes), then site_update everywhere. */
-int oracle_update(const oracle_cfg* cfg, const int* dst, const double* h, const double* mu,
-                  const double* sigma, const double* A, const double* P, const double* U,
-                  double* A_out, double* P_out, unsigned char* alpha_out, double* tsum_out)
+/* The step after the convolution on the whole grid: diffusion (or plain
+ * genes), then site_update everywhere.  Without rings U holds the potentials
+ * U[K][H][W]; with rings (ring_cnt != NULL) it holds the ring potentials
+ * V[C][n_rings][H][W] and each site's U_k is recombined from them with the
+ * site's diffused kernel genes (Algorithm 2: the weighted sum comes after the
+ * diffusion and before alpha).  U_out (nullable) receives U_k. */
+static int update_grid(const oracle_cfg* cfg, const int* src, const int* dst, const double* h,
+                       const double* mu, const double* sigma, const double* A, const double* P,
+                       const double* U, const double* ring_cnt, double* A_out, double* P_out,
+                       double* U_out, unsigned char* alpha_out, double* tsum_out)
 {
-    const int H = cfg->H, W = cfg->W, C = cfg->C, K = cfg->K;
+    const int H = cfg->H, W = cfg->W, C = cfg->C, K = cfg->K, n = cfg->n_rings;
     const size_t N = (size_t)H * W;
     const plane_map pm = planes_of(cfg->localized);
-    if (K > 64 || C > 64) return -1;
+    if (K > 64 || C > 64 || pm.n_p * K > MAX_PK) return -1;
+    if (ring_cnt && (pm.p_kern < 0 || n < 1 || n > 256 || !src)) return -1;
 
     /* Algorithm 2: diffuse the genospace. */
     double* Ph = NULL;
@@ -276,20 +379,78 @@ int oracle_update(const oracle_cfg* cfg, const int* dst, const double* h, const 
     }
     #pragma omp parallel for schedule(static)
     for (long i = 0; i < (long)N; i++) {
-        double u[64], ph[192], a_in[64], a_out[64], p_out[192];
-        for (int k = 0; k < K; k++) u[k] = U[(size_t)k * N + i];
+        double u[64], ph[MAX_PK], a_in[64], a_out[64], p_out[MAX_PK], vr[256];
         for (int pk = 0; pk < pm.n_p * K; pk++) ph[pk] = Ph[(size_t)pk * N + i];
+        for (int k = 0; k < K; k++) {
+            if (ring_cnt) {
+                for (int r = 0; r < n; r++) vr[r] = U[((size_t)src[k] * n + r) * N + i];
+                u[k] = ring_recombine(n, vr, ring_cnt, ph, pm, K, k);
+            } else {
+                u[k] = U[(size_t)k * N + i];
+            }
+        }
         for (int c = 0; c < C; c++) a_in[c] = A[(size_t)c * N + i];
         double ts = 0.0;
         int alpha = site_update(cfg, pm, dst, h, mu, sigma, u, ph, a_in, a_out, p_out, &ts);
         for (int c = 0; c < C; c++) A_out[(size_t)c * N + i] = a_out[c];
         if (P_out)
             for (int pk = 0; pk < pm.n_p * K; pk++) P_out[(size_t)pk * N + i] = p_out[pk];
+        if (U_out)
+            for (int k = 0; k < K; k++) U_out[(size_t)k * N + i] = u[k];
         if (alpha_out) alpha_out[i] = (unsigned char)alpha;
         if (tsum_out) tsum_out[i] = ts;
     }
     free(Ph);
     return 0;
+}
+
+/* The step after the convolution from given potentials U[K][H][W]. */
+int oracle_update(const oracle_cfg* cfg, const int* dst, const double* h, const double* mu,
+                  const double* sigma, const double* A, const double* P, const double* U,
+                  double* A_out, double* P_out, unsigned char* alpha_out, double* tsum_out)
+{
+    if (cfg->localized & LOC_KERNEL) return -1;
+    return update_grid(cfg, NULL, dst, h, mu, sigma, A, P, U, NULL, A_out, P_out, NULL, alpha_out,
+                       tsum_out);
+}
+
+/* Ring potentials of every channel, V[C][n_rings][H][W]. */
+static double* ring_potentials_all(const oracle_cfg* cfg, int R, const double* A)
+{
+    const size_t N = (size_t)cfg->H * cfg->W;
+    const int n = cfg->n_rings;
+    double* V = (double*)malloc(sizeof(double) * (size_t)cfg->C * n * N);
+    for (int c = 0; c < cfg->C; c++)
+        oracle_ring_potentials(cfg->H, cfg->W, A + (size_t)c * N, R, n, V + (size_t)c * n * N);
+    return V;
+}
+
+/* The step after the ring convolutions, from given ring potentials
+ * V[C][n_rings][H][W] of a radius-R kernel set (Section 2.4). */
+int oracle_ring_update(const oracle_cfg* cfg, const int* src, const int* dst, int R, const double* h,
+                       const double* mu, const double* sigma, const double* A, const double* P,
+                       const double* V, double* A_out, double* P_out, double* U_out,
+                       unsigned char* alpha_out, double* tsum_out)
+{
+    double cnt[256];
+    if (cfg->n_rings < 1 || cfg->n_rings > 256) return -1;
+    oracle_ring_counts(R, cfg->n_rings, cnt);
+    return update_grid(cfg, src, dst, h, mu, sigma, A, P, V, cnt, A_out, P_out, U_out, alpha_out,
+                       tsum_out);
+}
+
+/* One full step with ring-wise localized kernel genes (Algorithm 2 with the
+ * ring decomposition of Section 2.4): every kernel has radius R; the kernel
+ * of kernel k at a site is sum_r k_r K_r with the site's genes. */
+int oracle_ring_step(const oracle_cfg* cfg, const int* src, const int* dst, int R, const double* h,
+                     const double* mu, const double* sigma, const double* A, const double* P,
+                     double* A_out, double* P_out, double* U_out, unsigned char* alpha_out)
+{
+    if (cfg->n_rings < 1 || cfg->n_rings > 256 || !(cfg->localized & LOC_KERNEL)) return -1;
+    double* V = ring_potentials_all(cfg, R, A);
+    int rc = oracle_ring_update(cfg, src, dst, R, h, mu, sigma, A, P, V, A_out, P_out, U_out, alpha_out, NULL);
+    free(V);
+    return rc;
 }
 
 /* One full step.
@@ -308,6 +469,7 @@ int oracle_step(const oracle_cfg* cfg, const int* src, const int* dst, const int
 {
     const int H = cfg->H, W = cfg->W, K = cfg->K;
     const size_t N = (size_t)H * W;
+    if (cfg->localized & LOC_KERNEL) return -1;
     double* U = (double*)malloc(sizeof(double) * (size_t)K * N);
     for (int k = 0; k < K; k++)
         oracle_potential(H, W, A + (size_t)src[k] * N, R[k], Kw + kw_off[k], U + (size_t)k * N, 0);
@@ -331,11 +493,11 @@ int oracle_step_sites(const oracle_cfg* cfg, const int* src, const int* dst, con
     const size_t N = (size_t)H * W;
     const plane_map pm = planes_of(cfg->localized);
     const int rd = cfg->r_diff;
-    if (K > 64 || C > 64) return -1;
+    if (K > 64 || C > 64 || (cfg->localized & LOC_KERNEL)) return -1;
     #pragma omp parallel for schedule(dynamic, 1)
     for (long i = 0; i < n; i++) {
         const int y = ys[i], x = xs[i];
-        double u[64], ph[192], a_in[64], a_out[64], p_out[192];
+        double u[64], ph[MAX_PK], a_in[64], a_out[64], p_out[MAX_PK];
         for (int k = 0; k < K; k++) {
             const int r = R[k], nn = 2 * r + 1;
             const double* Kk = Kw + kw_off[k];
@@ -447,12 +609,19 @@ int oracle_evolve_step(const oracle_cfg* cfg, const int* src, const int* dst, co
     double* Pw = nP ? (double*)malloc(sizeof(double) * nP) : NULL;
     for (size_t i = 0; i < C * N; i++) Aw[i] = (walls && walls[i % N]) ? 0.0 : A[i];
     for (size_t i = 0; i < nP; i++) Pw[i] = (walls && walls[i % N]) ? 0.0 : P[i];
-    double* U = (double*)malloc(sizeof(double) * (size_t)K * N);
-    for (int k = 0; k < K; k++)
-        oracle_potential(H, W, Aw + (size_t)src[k] * N, R[k], Kw + kw_off[k], U + (size_t)k * N, 0);
     unsigned char* al = (unsigned char*)malloc(N);
     double* tsum = (double*)malloc(sizeof(double) * N);
-    int rc = oracle_update(cfg, dst, h, mu, sigma, Aw, Pw, U, A_out, P_out, al, tsum);
+    double* U = NULL;
+    int rc;
+    if (cfg->n_rings > 0) {
+        U = ring_potentials_all(cfg, R[0], Aw);
+        rc = oracle_ring_update(cfg, src, dst, R[0], h, mu, sigma, Aw, Pw, U, A_out, P_out, NULL, al, tsum);
+    } else {
+        U = (double*)malloc(sizeof(double) * (size_t)K * N);
+        for (int k = 0; k < K; k++)
+            oracle_potential(H, W, Aw + (size_t)src[k] * N, R[k], Kw + kw_off[k], U + (size_t)k * N, 0);
+        rc = oracle_update(cfg, dst, h, mu, sigma, Aw, Pw, U, A_out, P_out, al, tsum);
+    }
     double* empty = (double*)malloc(sizeof(double) * N);
     double* eoxy = (double*)malloc(sizeof(double) * N);
     double* epen = (double*)malloc(sizeof(double) * N);

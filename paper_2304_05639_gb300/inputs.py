@@ -29,6 +29,7 @@ BASE_SEED = 230405639
 GROWTH_SIGNED = 0      # 2*exp(-(u-m)^2/(2 s^2)) - 1, scaled by h
 GROWTH_PAPER = 1       # h*exp(-(u-m)^2/(2 s^2))   (Section 2.4 form)
 LOC_MU, LOC_SIGMA, LOC_H = 1, 2, 4
+LOC_KERNEL = 8         # ring-wise kernel genes r1, w1, b1, r2, w2, b2 (six planes)
 KERNEL_SHELLS, KERNEL_BUMPS = 0, 1
 
 
@@ -104,6 +105,7 @@ class World:
     A: np.ndarray | None = None      # float32 [C, H, W]
     P: np.ndarray | None = None      # float32 [n_p, K, H, W] or None
     name: str = ""
+    n_rings: int = 0                 # ring decomposition (with LOC_KERNEL)
 
     @property
     def n_kernels(self) -> int:
@@ -111,7 +113,7 @@ class World:
 
     @property
     def n_planes(self) -> int:
-        return bin(self.localized).count("1")
+        return bin(self.localized & 7).count("1") + (6 if self.localized & LOC_KERNEL else 0)
 
     @property
     def sites(self) -> int:
@@ -283,6 +285,46 @@ def workload(name: str) -> World:
     if name == "c5":
         return global_multi_channel()
     raise KeyError(name)
+
+
+def ring_world(H=512, W=1024, R=12, n_rings=24, n_channels=3, patch=96, n_geno=8, seed_index=6,
+               dt=0.2, localized=LOC_MU | LOC_SIGMA | LOC_H | LOC_KERNEL, live=True, name="rings") -> World:
+    """The paper's configuration (Section 2.1): a 512 x 1024 torus, 3 channels,
+    15 kernels in the paper's topology, each kernel two Gaussian bumps cut into
+    n_rings rings of a radius-R disk (Section 2.4), every gene localized:
+    growth m, s, h and kernel r1, w1, b1, r2, w2, b2 per kernel and site.
+    n_geno genotypes fill square patches (as in the other worlds); per kernel
+    r1 ~ U[0.1, 0.5), w1 ~ U[0.05, 0.15), b1 ~ U[0.5, 1), r2 ~ U[0.5, 0.9),
+    w2 ~ U[0.05, 0.15), b2 ~ U[0.1, 0.6), m ~ U[0.1, 0.4), s ~ U[0.01, 0.06),
+    h ~ U[0.1, 1).  A is U[0, 1) noise on each patch (U[0, 2 m) with live)."""
+    rng = Rng(BASE_SEED + seed_index)
+    topo = paper_topology(n_channels)
+    K = len(topo)
+    ranges = {"mu": (0.10, 0.40), "sigma": (0.01, 0.06), "h": (0.1, 1.0), "r1": (0.1, 0.5), "w1": (0.05, 0.15),
+              "b1": (0.5, 1.0), "r2": (0.5, 0.9), "w2": (0.05, 0.15), "b2": (0.1, 0.6)}
+    geno = {g: rng.uniform(n_geno * K, *ranges[g]).reshape(n_geno, K) for g in ranges}
+    kernels = []
+    for k, (src, dst) in enumerate(topo):
+        bump = tuple(float(np.mean(geno[g][:, k])) for g in ("r1", "w1", "b1", "r2", "w2", "b2"))
+        kernels.append(KernelDesc(src, dst, R, KERNEL_BUMPS, (1.0,), bump=bump, h=float(np.mean(geno["h"][:, k])),
+                                  mu=float(np.mean(geno["mu"][:, k])), sigma=float(np.mean(geno["sigma"][:, k]))))
+    order = [g for g, bit in (("mu", LOC_MU), ("sigma", LOC_SIGMA), ("h", LOC_H)) if localized & bit]
+    if localized & LOC_KERNEL:
+        order += ["r1", "w1", "b1", "r2", "w2", "b2"]
+    A = np.zeros((n_channels, H, W), np.float32)
+    P = np.zeros((len(order), K, H, W), np.float32)
+    for g, (ry, rx, my, mx) in enumerate(_place_patches(rng, H, W, patch, n_geno, R)):
+        for p, name_ in enumerate(order):
+            for k in range(K):
+                P[p, k][np.ix_(my, mx)] = geno[name_][g, k]
+        for c in range(n_channels):
+            noise = rng.uniform(len(ry) * len(rx)).reshape(len(ry), len(rx))
+            if live:
+                m = float(np.mean([geno["mu"][g, k] for k, (s_, d_) in enumerate(topo) if s_ == c]))
+                noise = (noise * np.float32(2.0 * m)).astype(np.float32)
+            A[c][np.ix_(ry, rx)] = noise
+    return World(H, W, n_channels, kernels, dt, localized=localized, maintain_genes=1, A=A, P=P, name=name,
+                 n_rings=n_rings)
 
 
 def evolution_events(world: World, step: int, seed_index: int = 5, gamma_mut=1.0, gamma_pen=0.2,
