@@ -241,6 +241,56 @@ def evolve_leg(torch, lenia, inputs, stream, plain_ms, steps=100):
             "stats_finite": bool(torch.isfinite(st).all())}
 
 
+def rings_leg(torch, lenia, inputs, stream, steps=100):
+    """The paper's own configuration (Section 2.1, 2.4): 512 x 1024 torus,
+    3 channels, 15 two-bump kernels of radius 12 cut into 24 rings, all nine
+    gene types localized per kernel and site (135 gene planes), maintenance
+    on, potential alpha test."""
+    w = inputs.ring_world()
+    w.alpha_on = 1
+    cfg, ks = lenia.config_from_world(w)
+    ctx = lenia.lenia_init(cfg, ks, stream)
+    try:
+        bufs = [(torch.from_numpy(w.A).cuda(), torch.from_numpy(w.P).cuda())]
+        bufs.append((torch.empty_like(bufs[0][0]), torch.empty_like(bufs[0][1])))
+        st = torch.zeros((steps + 3, w.n_channels, 3), dtype=torch.float32, device="cuda")
+
+        def step(i):
+            (a, p), (a2, p2) = bufs[i % 2], bufs[(i + 1) % 2]
+            lenia.lenia_step(ctx, a, p, a2, p2, st[i], stream)
+
+        for i in range(3):
+            step(i)
+        torch.cuda.synchronize()
+        lenia.lenia_profile_start(ctx, 8 * steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            step(3 + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = lenia.lenia_profile_stop(ctx)
+        lenia.lenia_check(ctx)
+        ms = e0.elapsed_time(e1) / steps
+        path = lenia.lenia_conv_path(ctx)
+    finally:
+        lenia.lenia_destroy(ctx)
+    sites = w.sites
+    n_planes = w.n_planes * w.n_kernels
+    alg = 3 * 4 * 2 + n_planes * 4 * 2
+    epi = prof.get("epilogue", (0.0, 1))
+    epi_ms = epi[0] / max(1, epi[1])
+    return {"workload": "512x1024, 3 channels, 15 two-bump kernels R=12 in 24 rings, all 9 gene types localized "
+                        f"({n_planes} gene planes)",
+            "steps": steps, "ms_per_step": ms, "value": sites / (ms / 1e3), "unit": UNIT,
+            "conv_path": "fft" if path == lenia.CONV_FFT else "direct",
+            "ring_planes": w.n_channels * w.n_rings, "alg_bytes_per_site": alg,
+            "epilogue_frac_of_hbm": (alg * sites / (epi_ms / 1e3) / 1e9) / _peaks()[0] if epi_ms > 0 else None,
+            "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
+            "real_time_goal_steps_per_s": 20, "steps_per_s": 1e3 / ms,
+            "stats_finite": bool(torch.isfinite(st).all())}
+
+
 def max_over_ranks(values, torch, device=None):
     """Element-wise max of a list of floats over all ranks (identity at N = 1)."""
     import torch.distributed as dist
@@ -458,6 +508,7 @@ def run_ours(args):
         line["adjoint"] = adjoint_leg(torch, lenia, inputs, stream)
         line["batched"] = batched_leg(torch, lenia, inputs, stream)
         line["evolve"] = evolve_leg(torch, lenia, inputs, stream, t_max / args.steps)
+        line["rings"] = rings_leg(torch, lenia, inputs, stream)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -474,7 +525,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched-world and evolution legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched-world, evolution and ring legs")
     ap.add_argument("--size", type=int, default=2048, help="torus side (2048 = the benchmark workload)")
     ap.add_argument("--conv-path", type=int, default=0, help="0 auto, 1 fft, 2 direct")
     args = ap.parse_args()

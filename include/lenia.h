@@ -61,7 +61,9 @@ typedef enum {
 
 enum { LENIA_KERNEL_SHELLS = 0, LENIA_KERNEL_BUMPS = 1 };
 enum { LENIA_GROWTH_SIGNED = 0, LENIA_GROWTH_PAPER = 1 };
-enum { LENIA_LOC_MU = 1, LENIA_LOC_SIGMA = 2, LENIA_LOC_H = 4 };
+/* LENIA_LOC_KERNEL: ring-wise kernel genes (Section 2.4), six planes r1, w1,
+ * b1, r2, w2, b2 after the growth planes; needs n_rings > 0. */
+enum { LENIA_LOC_MU = 1, LENIA_LOC_SIGMA = 2, LENIA_LOC_H = 4, LENIA_LOC_KERNEL = 8 };
 enum { LENIA_CONV_AUTO = 0, LENIA_CONV_FFT = 1, LENIA_CONV_DIRECT = 2 };
 
 /* One kernel k (Section 2.1: kernels with their growth mappings).
@@ -91,7 +93,9 @@ typedef struct {
  *   dt: time step multiplying the growth sum (the paper's update is dt = 1).
  *   growth_form: LENIA_GROWTH_SIGNED, h (2g - 1); LENIA_GROWTH_PAPER, h g
  *     (Section 2.4), g = exp(-(u - m)^2 / (2 s^2)) and g = 0 where s <= 0.
- *   localized: OR of LENIA_LOC_* - the genes read per site from P.
+ *   localized: OR of LENIA_LOC_* - the genes read per site from P.  P holds
+ *     the localized growth genes mu, sigma, h (in that order), then with
+ *     LENIA_LOC_KERNEL the kernel genes r1, w1, b1, r2, w2, b2.
  *   maintain_genes: 1 runs diffusion (Section 2.3) and the alpha mask
  *     (Section 2.2); needs localized != 0.
  *   eps_u: alpha threshold on the growth h g (or on U when alpha_on = 1);
@@ -99,7 +103,16 @@ typedef struct {
  *   r_diff: radius of the diffusion disk |d|_2 <= r_diff, 0..8.
  *   conv_path: LENIA_CONV_* (AUTO picks FFT for power-of-two worlds).
  *   max_rollout_steps, ckpt_every: adjoint buffers for lenia_backward (0 = none;
- *     global genes only); states kept every ckpt_every steps (0 -> 8). */
+ *     global genes only); states kept every ckpt_every steps (0 -> 8).
+ *   n_rings: with LENIA_LOC_KERNEL, the ring decomposition of Section 2.4
+ *     (0 otherwise): every kernel has the same radius R; ring r holds the
+ *     offsets with r <= n_rings |d|_2 / R < r + 1 and |d|_2 < R; at each site
+ *     kernel k's potential is sum_r k_r (K_r * A_src) / sum_r k_r (K_r * 1)
+ *     with k_r = sum_i b_i exp(-(r / n_rings - r_i)^2 / (2 w_i^2)) from the
+ *     site's diffused kernel genes (a term is 0 where w_i <= 0; U = 0 where
+ *     the denominator is <= 0).  1 <= n_rings <= 64, n_channels * n_rings <= 256.
+ *     The convolution stage then produces the ring potentials K_r * A_c,
+ *     [C][n_rings][H][W] (lenia_potentials returns those). */
 typedef struct {
     int32_t height, width, n_channels, n_kernels;
     float dt;
@@ -111,6 +124,7 @@ typedef struct {
     int32_t alpha_on;
     int32_t conv_path;
     int32_t max_rollout_steps, ckpt_every;
+    int32_t n_rings;
 } lenia_config;
 
 /* Validate cfg and kernels[0..n_kernels), build the normalised kernels in
@@ -161,12 +175,14 @@ LENIA_API lenia_status lenia_stats(lenia_ctx* ctx, const float* A, float* out, v
 
 /* Potentials U_k = K~_k * A_src(k) for every kernel (Algorithm 2, convolve
  * and normalised sum; note after Algorithm 2 for the FFT route) into U_out
- * [K][H][W], through the context's convolution path. */
+ * [K][H][W], through the context's convolution path.  With n_rings > 0 the
+ * ring potentials K_r * A_c instead, [C][n_rings][H][W] (Section 2.4). */
 LENIA_API lenia_status lenia_potentials(lenia_ctx* ctx, const float* A_in, float* U_out, void* stream);
 
 /* The step after the convolution: diffusion, growth, alpha mask, masking and
  * clipped update (Sections 2.2-2.4, Algorithm 2) from given potentials
- * U_in [K][H][W].  alpha_out (nullable) receives one byte per site. */
+ * U_in [K][H][W] (ring potentials [C][n_rings][H][W] with n_rings > 0).
+ * alpha_out (nullable) receives one byte per site. */
 LENIA_API lenia_status lenia_update_from_potentials(lenia_ctx* ctx, const float* A_in, const float* P_in,
                                           const float* U_in, float* A_out, float* P_out,
                                           uint8_t* alpha_out, void* stream);

@@ -448,7 +448,7 @@ static cudaError_t launch_rows(const EpiParams& p, int num_sms, int* status, cud
 
 bool epilogue_rows_supported(const EpiParams& p)
 {
-    if (p.W % ER_CH != 0 || (p.maintain && p.r_diff != 1)) return false;
+    if (p.W % ER_CH != 0 || (p.maintain && p.r_diff != 1) || p.n_rings > 0) return false;
     // 32-bit site indexing of every plane
     const long long N = (long long)p.H * p.W;
     if (N * (p.n_p * p.kt.K > p.kt.K ? p.n_p * p.kt.K : p.kt.K) >= (1LL << 31) || N * p.kt.C >= (1LL << 31))

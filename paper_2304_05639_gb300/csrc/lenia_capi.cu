@@ -18,8 +18,13 @@ struct lenia_ctx {
     lenia_config cfg;
     std::vector<lenia_kernel_desc> kd;
     std::vector<std::vector<double>> kw;   // normalised FP64 kernels, row-major dy, dx
+    // what the convolution stage computes: the kernels, or (ring decomposition)
+    // one binary ring mask per (channel, ring), plane c * n_rings + r
+    std::vector<std::vector<double>> conv_w;
+    std::vector<int> conv_src, conv_R;
+    std::vector<double> ring_cnt;          // K_r * 1 per ring
     int path = LENIA_CONV_DIRECT;
-    int n_p = 0, p_mu = -1, p_sigma = -1, p_h = -1;
+    int n_p = 0, p_mu = -1, p_sigma = -1, p_h = -1, p_kern = -1;
     int max_R = 0;
     size_t N = 0;                          // sites
     // device scratch (library-owned)
@@ -150,7 +155,15 @@ lenia_status validate(const lenia_config* c, const lenia_kernel_desc* ks, std::s
     if (!isfinite(c->dt) || c->dt < 0.f) return bad("dt must be finite and >= 0");
     if (c->growth_form != LENIA_GROWTH_SIGNED && c->growth_form != LENIA_GROWTH_PAPER)
         return bad("unknown growth_form");
-    if (c->localized & ~7) return bad("localized has unknown bits");
+    if (c->localized & ~15) return bad("localized has unknown bits");
+    if ((c->localized & LENIA_LOC_KERNEL) != 0) {
+        if (c->n_rings < 1 || c->n_rings > kMaxRings) return bad("n_rings must be 1..64 with LENIA_LOC_KERNEL");
+        if (c->n_channels * c->n_rings > kMaxConvPlanes) return bad("n_channels * n_rings must be <= 256");
+        for (int k = 1; k < c->n_kernels; k++)
+            if (ks[k].radius != ks[0].radius) return bad("the ring decomposition needs one radius for every kernel");
+    } else if (c->n_rings != 0) {
+        return bad("n_rings needs LENIA_LOC_KERNEL");
+    }
     if (c->maintain_genes != 0 && c->maintain_genes != 1) return bad("maintain_genes must be 0 or 1");
     if (c->maintain_genes && !c->localized) return bad("maintain_genes needs localized genes");
     if (c->r_diff < 0 || c->r_diff > 8 || 2 * c->r_diff + 1 > c->height || 2 * c->r_diff + 1 > c->width)
@@ -306,6 +319,9 @@ EpiParams epi_params(lenia_ctx* c)
     ep.eps_u = c->cfg.eps_u;
     ep.eps_p = c->cfg.eps_p;
     ep.kt = c->kt;
+    ep.n_rings = c->cfg.n_rings;
+    ep.p_kern = c->p_kern;
+    for (int r = 0; r < c->cfg.n_rings; r++) ep.ring_cnt[r] = (float)c->ring_cnt[r];
     for (int ch = 0; ch < c->cfg.n_channels; ch++) {
         float a0 = 0.f;
         if (c->cfg.growth_form == LENIA_GROWTH_SIGNED && c->p_h < 0)
@@ -481,17 +497,51 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
     c->p_mu = (loc & LENIA_LOC_MU) ? 0 : -1;
     c->p_sigma = (loc & LENIA_LOC_SIGMA) ? ((loc & LENIA_LOC_MU) ? 1 : 0) : -1;
     c->p_h = (loc & LENIA_LOC_H) ? c->n_p - 1 : -1;
+    if (loc & LENIA_LOC_KERNEL) {
+        c->p_kern = c->n_p;
+        c->n_p += 6;
+    }
+    const int n_rings = cfg->n_rings;
 
-    // kernels in FP64, normalised to sum 1
+    // kernels in FP64, normalised to sum 1 (with rings the kernels are made per
+    // site from the ring masks instead)
     c->kw.resize(K);
     for (int k = 0; k < K; k++) {
-        if (!build_kernel(c->kd[k], c->kw[k])) {
+        if (!n_rings && !build_kernel(c->kd[k], c->kw[k])) {
             lenia_destroy(c);
             fprintf(stderr, "lenia_init: kernel %d sums to zero\n", k);
             return LENIA_EINVAL;
         }
         c->max_R = std::max(c->max_R, c->kd[k].radius);
     }
+    if (n_rings) {
+        // ring r holds the offsets with r <= n |d| / R < r + 1, |d| < R, decided in
+        // integers: the largest m with m^2 R^2 <= n^2 |d|^2
+        const int R = c->kd[0].radius, nw = 2 * R + 1;
+        c->conv_w.assign((size_t)C * n_rings, std::vector<double>((size_t)nw * nw, 0.0));
+        c->ring_cnt.assign(n_rings, 0.0);
+        for (int dy = -R; dy <= R; dy++)
+            for (int dx = -R; dx <= R; dx++) {
+                const long long q = (long long)dy * dy + (long long)dx * dx;
+                if (q >= (long long)R * R) continue;
+                int m = 0;
+                while ((long long)(m + 1) * (m + 1) * R * R <= (long long)n_rings * n_rings * q) m++;
+                c->ring_cnt[m] += 1.0;
+                for (int ch = 0; ch < C; ch++) c->conv_w[(size_t)ch * n_rings + m][(size_t)(dy + R) * nw + (dx + R)] = 1.0;
+            }
+        for (int ch = 0; ch < C; ch++)
+            for (int r = 0; r < n_rings; r++) {
+                c->conv_src.push_back(ch);
+                c->conv_R.push_back(R);
+            }
+    } else {
+        c->conv_w = c->kw;
+        for (int k = 0; k < K; k++) {
+            c->conv_src.push_back(c->kd[k].src_channel);
+            c->conv_R.push_back(c->kd[k].radius);
+        }
+    }
+    const int NC = (int)c->conv_w.size();      // convolution output planes
     memset(&c->kt, 0, sizeof(c->kt));
     c->kt.K = K;
     c->kt.C = C;
@@ -534,7 +584,7 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
     } while (0)
 
     const size_t nA = c->N * C, nP = c->N * c->n_p * K;
-    ALLOC(c->d_U, c->N * K);
+    ALLOC(c->d_U, c->N * NC);
     ALLOC(c->d_A2, nA);
     ALLOC(c->d_A3, nA);
     if (nP) {
@@ -570,25 +620,25 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         CK_INIT(cudaMemcpy(c->d_trig, trig.data(), trig.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
 
-    // per-channel kernel lists
+    // per-channel lists of the convolution planes each channel feeds
     int kcount[kMaxChannels] = {0};
     int klist[kMaxChannels][kMaxKernels];
-    for (int k = 0; k < K; k++) {
-        const int sc = c->kd[k].src_channel;
+    for (int k = 0; k < NC; k++) {
+        const int sc = c->conv_src[k];
         klist[sc][kcount[sc]++] = k;
     }
 
     if (path == LENIA_CONV_DIRECT) {
         std::vector<float> w;
-        std::vector<int> woff(K), yr, yroff(K);
-        for (int k = 0; k < K; k++) {
-            const int R = c->kd[k].radius, n = 2 * R + 1;
+        std::vector<int> woff(NC), yr, yroff(NC);
+        for (int k = 0; k < NC; k++) {
+            const int R = c->conv_R[k], n = 2 * R + 1;
             woff[k] = (int)w.size();
             yroff[k] = (int)yr.size();
             for (int dx = -R; dx <= R; dx++) {
                 int r = -1;
                 for (int dy = -R; dy <= R; dy++) {
-                    const double v = c->kw[k][(size_t)(dy + R) * n + (dx + R)];
+                    const double v = c->conv_w[k][(size_t)(dy + R) * n + (dx + R)];
                     w.push_back((float)v);
                     if (v != 0.0) r = std::max(r, std::abs(dy));
                 }
@@ -596,13 +646,13 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
             }
         }
         ALLOC(c->d_w, w.size());
-        ALLOC(c->d_w_off, (size_t)K);
+        ALLOC(c->d_w_off, (size_t)NC);
         ALLOC(c->d_yr, yr.size());
-        ALLOC(c->d_yr_off, (size_t)K);
+        ALLOC(c->d_yr_off, (size_t)NC);
         CK_INIT(cudaMemcpy(c->d_w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CK_INIT(cudaMemcpy(c->d_w_off, woff.data(), K * sizeof(int), cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_w_off, woff.data(), NC * sizeof(int), cudaMemcpyHostToDevice));
         CK_INIT(cudaMemcpy(c->d_yr, yr.data(), yr.size() * sizeof(int), cudaMemcpyHostToDevice));
-        CK_INIT(cudaMemcpy(c->d_yr_off, yroff.data(), K * sizeof(int), cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_yr_off, yroff.data(), NC * sizeof(int), cudaMemcpyHostToDevice));
         memset(&c->cp, 0, sizeof(c->cp));
         c->cp.w = c->d_w;
         c->cp.w_off = c->d_w_off;
@@ -611,15 +661,15 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         c->cp.H = H;
         c->cp.W = W;
         c->cp.C = C;
-        c->cp.K = K;
-        for (int k = 0; k < K; k++) c->cp.R[k] = c->kd[k].radius;
+        c->cp.K = NC;
+        for (int k = 0; k < NC; k++) c->cp.R[k] = c->conv_R[k];
         memcpy(c->cp.kcount, kcount, sizeof(kcount));
         memcpy(c->cp.klist, klist, sizeof(klist));
     } else {
         const int M = W / 2, HS = H / 2 + 1;
         ALLOC(c->d_Ahat, (size_t)C * H * M);
-        ALLOC(c->d_Uhat, (size_t)K * H * M);
-        ALLOC(c->d_S, (size_t)K * (M + 1) * HS);
+        ALLOC(c->d_Uhat, (size_t)NC * H * M);
+        ALLOC(c->d_S, (size_t)NC * (M + 1) * HS);
         std::vector<float2> twM = pass_twiddles(M, ROW_RMAX), twW = twiddles(W, M + 1), twH = pass_twiddles(H, 16);
         ALLOC(c->d_twM, twM.size());
         ALLOC(c->d_twW, twW.size());
@@ -640,11 +690,11 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         cudaError_t e = ok ? cudaSuccess : cudaErrorMemoryAllocation;
         if (e == cudaSuccess) e = cudaMemcpy(d_cosH, cosH.data(), H * sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d_cosW, cosW.data(), W * sizeof(double), cudaMemcpyHostToDevice);
-        for (int k = 0; k < K && e == cudaSuccess; k++) {
-            e = cudaMemcpyAsync(d_Kd, c->kw[k].data(), c->kw[k].size() * sizeof(double),
+        for (int k = 0; k < NC && e == cudaSuccess; k++) {
+            e = cudaMemcpyAsync(d_Kd, c->conv_w[k].data(), c->conv_w[k].size() * sizeof(double),
                                 cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess)
-                e = launch_spectra(d_Kd, c->kd[k].radius, H, W, d_cosH, d_cosW, d_T,
+                e = launch_spectra(d_Kd, c->conv_R[k], H, W, d_cosH, d_cosW, d_T,
                                    c->d_S + (size_t)k * (M + 1) * HS, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         }
@@ -663,7 +713,7 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         c->fp.H = H;
         c->fp.W = W;
         c->fp.C = C;
-        c->fp.K = K;
+        c->fp.K = NC;
         memcpy(c->fp.kcount, kcount, sizeof(kcount));
         memcpy(c->fp.klist, klist, sizeof(klist));
     }
@@ -1039,6 +1089,7 @@ const char* lenia_profile_kind_name(int32_t kind)
 lenia_status lenia_kernel_weights(const lenia_ctx* c, int32_t k, double* out)
 {
     if (!c || !out || k < 0 || k >= c->cfg.n_kernels) return LENIA_EINVAL;
+    if (c->cfg.n_rings) return LENIA_ENOTSUP;     // kernels are made per site from the rings
     memcpy(out, c->kw[k].data(), c->kw[k].size() * sizeof(double));
     return LENIA_OK;
 }

@@ -7,7 +7,9 @@ namespace lenia {
 
 constexpr int kMaxKernels = 64;
 constexpr int kMaxChannels = 8;
-constexpr int kMaxPlanes = 3;   // mu, sigma, h
+constexpr int kMaxPlanes = 9;   // mu, sigma, h, then the ring-wise kernel genes r1, w1, b1, r2, w2, b2
+constexpr int kMaxRings = 64;
+constexpr int kMaxConvPlanes = 256;   // convolution outputs: kernels, or channels x rings
 constexpr int ROW_RMAX = 32;     // largest radix of the row transforms (column transforms: 16)
 
 // Per-kernel scalars, passed by value to the kernels that need them.
@@ -40,6 +42,10 @@ struct EpiParams {
     // growth sum of channel c at sites where alpha = 0 (genes masked to zero):
     // -sum_{dst(k)=c} h_k for the signed form with global h, else 0
     float acc0[kMaxChannels];
+    // ring decomposition (Section 2.4): U holds the ring potentials
+    // [C][n_rings][H][W]; the kernel genes start at plane p_kern
+    int n_rings, p_kern;
+    float ring_cnt[kMaxRings];  // K_r * 1 (pixels per ring)
     KernelTable kt;
 };
 
@@ -70,7 +76,7 @@ struct ConvParams {
     const int* yr;             // per kernel, per dx: largest |dy| with a non-zero tap (-1: none)
     const int* yr_off;         // offset of kernel k in yr
     int H, W, C, K;
-    int R[kMaxKernels];
+    int R[kMaxConvPlanes];
     int kcount[kMaxChannels];
     int klist[kMaxChannels][kMaxKernels];
 };

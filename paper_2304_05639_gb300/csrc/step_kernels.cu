@@ -230,8 +230,33 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
     if (p.partials) block_stats<CT>(st, CT, p.partials);
 }
 
+// Potential of kernel k at site i from the ring potentials (Section 2.4):
+//   k_r = sum_i b_i exp(-(r/n - r_i)^2 / (2 w_i^2))  (a term is 0 where w_i <= 0),
+//   U = sum_r k_r (K_r * A_src) / sum_r k_r (K_r * 1),  0 where the denominator is <= 0,
+// with the site's diffused kernel genes ph (planes p_kern .. p_kern + 5).
+__device__ float ring_potential(const EpiParams& p, const float* ph, int K, int k, size_t i, size_t N)
+{
+    const int kb = p.p_kern;
+    const float r1 = ph[(kb + 0) * K + k], w1 = ph[(kb + 1) * K + k], b1 = ph[(kb + 2) * K + k];
+    const float r2 = ph[(kb + 3) * K + k], w2 = ph[(kb + 4) * K + k], b2 = ph[(kb + 5) * K + k];
+    const bool on1 = w1 > 0.f, on2 = w2 > 0.f;
+    const float c1 = on1 ? 0.5f / (w1 * w1) : 0.f, c2 = on2 ? 0.5f / (w2 * w2) : 0.f;
+    const int n = p.n_rings;
+    const float* V = p.U + (size_t)p.kt.src[k] * n * N + i;
+    float num = 0.f, den = 0.f;
+    for (int r = 0; r < n; r++) {
+        const float x = (float)r / (float)n;
+        const float d1 = x - r1, d2 = x - r2;
+        const float kr = (on1 ? b1 * expf(-(d1 * d1) * c1) : 0.f) + (on2 ? b2 * expf(-(d2 * d2) * c2) : 0.f);
+        num = fmaf(kr, __ldg(V + (size_t)r * N), num);
+        den = fmaf(kr, p.ring_cnt[r], den);
+    }
+    return den > 0.f ? num / den : 0.f;
+}
+
 // General path: any diffusion radius, kernel count, channel count and gene
-// layout (runtime loops; per-site arrays may live in local memory).
+// layout, and the ring decomposition (runtime loops; per-site arrays may
+// live in local memory).
 __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
 {
     const int K = p.kt.K, C = p.kt.C, n_p = p.n_p;
@@ -277,7 +302,7 @@ __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
         float tsum = 0.f;                  // sum of the alpha tests (Delta_sum)
         for (int c = 0; c < C; c++) acc[c] = 0.f;
         for (int k = 0; k < K; k++) {
-            const float u = __ldg(&p.U[(size_t)k * N + i]);
+            const float u = p.n_rings > 0 ? ring_potential(p, ph, K, k, i, N) : __ldg(&p.U[(size_t)k * N + i]);
             const float m = p.p_mu >= 0 ? ph[p.p_mu * K + k] : p.kt.mu[k];
             const float sg = p.p_sigma >= 0 ? ph[p.p_sigma * K + k] : p.kt.sigma[k];
             const float hh = p.p_h >= 0 ? ph[p.p_h * K + k] : p.kt.h[k];
@@ -327,7 +352,7 @@ cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks)
     if (n_blocks) *n_blocks = grid.x * grid.y;
     const int K = p.kt.K, C = p.kt.C;
     const int loc = (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
-    const bool r1 = p.r_diff == 1 || !p.maintain;
+    const bool r1 = (p.r_diff == 1 || !p.maintain) && p.n_rings == 0;
     if (r1 && K == 15 && C == 3 && loc == 3) k_epilogue_r1<15, 3, 3><<<grid, block, 0, s>>>(p);
     else if (r1 && K == 15 && C == 3 && loc == 0) k_epilogue_r1<15, 3, 0><<<grid, block, 0, s>>>(p);
     else if (r1 && K == 1 && C == 1 && loc == 3) k_epilogue_r1<1, 1, 3><<<grid, block, 0, s>>>(p);

@@ -45,7 +45,7 @@ class LeniaConfig(ctypes.Structure):
                 ("eps_u", ctypes.c_float), ("eps_p", ctypes.c_float),
                 ("r_diff", ctypes.c_int32), ("alpha_on", ctypes.c_int32),
                 ("conv_path", ctypes.c_int32), ("max_rollout_steps", ctypes.c_int32),
-                ("ckpt_every", ctypes.c_int32)]
+                ("ckpt_every", ctypes.c_int32), ("n_rings", ctypes.c_int32)]
 
 
 class LeniaKernelDesc(ctypes.Structure):
@@ -364,7 +364,7 @@ def config_from_world(world: "_inputs.World", conv_path: int = CONV_AUTO, max_ro
     cfg = LeniaConfig(world.height, world.width, world.n_channels, world.n_kernels,
                       float(world.dt), world.growth_form, world.localized, world.maintain_genes,
                       float(world.eps_u), float(world.eps_p), world.r_diff, world.alpha_on,
-                      conv_path, max_rollout_steps, ckpt_every)
+                      conv_path, max_rollout_steps, ckpt_every, int(getattr(world, "n_rings", 0)))
     ks = []
     for k in world.kernels:
         d = LeniaKernelDesc()

@@ -74,6 +74,20 @@ def test_init_rejects_invalid_config(lib, over):
     assert out is None
 
 
+@pytest.mark.parametrize("over", [
+    dict(n_rings=0),                      # kernel genes need the ring decomposition
+    dict(n_rings=65),
+    dict(localized=7),                    # rings without kernel genes
+    dict(n_channels=8, n_rings=40),       # 320 ring planes > 256
+    dict(k0_radius=5),                    # one radius for every kernel
+])
+def test_init_rejects_invalid_ring_config(lib, over):
+    w = inputs.ring_world(H=64, W=64, R=6, n_rings=12, patch=16, n_geno=2)
+    st, out = _init_status(lib, w, **over)
+    assert st == lenia.LENIA_EINVAL
+    assert out is None
+
+
 def test_status_strings(lib):
     assert lib.lenia_status_string(0) == b"ok"
     assert lib.lenia_status_string(1) == b"invalid argument"
