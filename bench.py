@@ -528,12 +528,32 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched-world, evolution and ring legs")
     ap.add_argument("--size", type=int, default=2048, help="torus side (2048 = the benchmark workload)")
     ap.add_argument("--conv-path", type=int, default=0, help="0 auto, 1 fft, 2 direct")
+    ap.add_argument("--leg", default=None, choices=["adjoint", "batched", "rings"],
+                    help="run only this extra leg (N = 1) and print its JSON object (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg:
+        return run_leg(args)
     return run_ours(args)
+
+
+def run_leg(args):
+    import torch
+    from paper_2304_05639_gb300 import build, inputs, lenia
+    torch.cuda.set_device(0)
+    build.build()
+    stream = torch.cuda.current_stream()
+    if args.leg == "adjoint":
+        out = adjoint_leg(torch, lenia, inputs, stream)
+    elif args.leg == "batched":
+        out = batched_leg(torch, lenia, inputs, stream, steps=args.steps)
+    else:
+        out = rings_leg(torch, lenia, inputs, stream, steps=args.steps)
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

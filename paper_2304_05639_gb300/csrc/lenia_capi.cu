@@ -321,7 +321,10 @@ EpiParams epi_params(lenia_ctx* c)
     ep.kt = c->kt;
     ep.n_rings = c->cfg.n_rings;
     ep.p_kern = c->p_kern;
-    for (int r = 0; r < c->cfg.n_rings; r++) ep.ring_cnt[r] = (float)c->ring_cnt[r];
+    for (int r = 0; r < c->cfg.n_rings; r++) {
+        ep.ring_cnt[r] = (float)c->ring_cnt[r];
+        ep.ring_x[r] = (float)((double)r / (double)c->cfg.n_rings);
+    }
     for (int ch = 0; ch < c->cfg.n_channels; ch++) {
         float a0 = 0.f;
         if (c->cfg.growth_form == LENIA_GROWTH_SIGNED && c->p_h < 0)
@@ -602,7 +605,7 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         CK_INIT(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     }
     // stats records: the larger of the tiled epilogue's blocks and one per SM-resident CTA
-    c->n_part_blocks = std::max(epilogue_blocks(H, W), 8 * c->num_sms);
+    c->n_part_blocks = std::max(std::max(epilogue_blocks(H, W), ring_epilogue_blocks(H, W)), 8 * c->num_sms);
     ALLOC(c->d_partials, (size_t)c->n_part_blocks * C * 5);
 
     // circular-mean tables

@@ -46,6 +46,7 @@ struct EpiParams {
     // [C][n_rings][H][W]; the kernel genes start at plane p_kern
     int n_rings, p_kern;
     float ring_cnt[kMaxRings];  // K_r * 1 (pixels per ring)
+    float ring_x[kMaxRings];    // r / n_rings, where the kernel function is evaluated
     KernelTable kt;
 };
 
@@ -135,6 +136,7 @@ bool epilogue_rows_supported(const EpiParams& p);
 cudaError_t launch_epilogue_rows(const EpiParams& p, int num_sms, int* status, cudaStream_t s, int* n_blocks);
 bool fft_size_supported(int H, int W);
 int epilogue_blocks(int H, int W);
+int ring_epilogue_blocks(int H, int W);   // stats records of the ring epilogue
 // pass 1: Delta_sum complement -> counts; pass 2: E_pen, mutation, penalisation
 cudaError_t launch_disk_pass(const EvoParams& p, int pass, cudaStream_t s);
 cudaError_t launch_walls_zero(const int* idx, int n, float* A, int C, float* P, int npk, size_t N,

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include "lenia_internal.cuh"
+#include "ptx_util.cuh"
 
 namespace lenia {
 
@@ -340,6 +341,144 @@ __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
     if (p.partials) block_stats<kMaxChannels>(st, C, p.partials);
 }
 
+// Ring decomposition fast path (Section 2.4): diffusion radius 1, compile-time
+// kernel and channel counts, ring count and gene layout; one site per thread
+// (32 x 8 sites per block).  The ring potentials of one source channel sit in
+// registers while every kernel reading that channel diffuses its own NP genes,
+// forms its ring weights and its potential.  Once alpha is known the genes
+// are diffused again (their lines are still in L1/L2) and written once:
+// the diffused values where alpha = 1, zeros elsewhere.  Ring weights use the
+// hardware base-2 exponential: k_r = sum_i b_i 2^(-(r/n - r_i)^2 log2(e) / (2 w_i^2)).
+constexpr int RG_TY = 8;     // rows per block of the ring epilogue (one site per thread)
+
+template <int NP, int KT>
+__device__ __forceinline__ float diffuse5(const float* P, int pk, size_t N, size_t ru, size_t rc, size_t rd,
+                                          int xm, int xc, int xp, float eps_p)
+{
+    const float* pl = P + (size_t)pk * N;
+    // disk |d| <= 1 in the order (-1,0), (0,-1), (0,0), (0,1), (1,0)
+    const float v0 = __ldg(pl + ru + xc), v1 = __ldg(pl + rc + xm), v2 = __ldg(pl + rc + xc);
+    const float v3 = __ldg(pl + rc + xp), v4 = __ldg(pl + rd + xc);
+    const float sm = (((v0 + v1) + v2) + v3) + v4;
+    const int n = (v0 > eps_p) + (v1 > eps_p) + (v2 > eps_p) + (v3 > eps_p) + (v4 > eps_p);
+    return n > 0 ? fminf(fmaxf(sm / (float)n, 0.f), 1.f) : 0.f;
+}
+
+template <int KT, int CT, int NR, int LOC>
+__global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
+{
+    constexpr int NG = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
+    constexpr int NP = NG + 6;
+    constexpr int PMU = (LOC & 1) ? 0 : -1;
+    constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
+    constexpr int PH = (LOC & 4) ? NG - 1 : -1;
+    constexpr int PK = NG;
+    constexpr float LOG2E = 1.4426950408889634f;
+    const int H = p.H, W = p.W;
+    const size_t N = (size_t)H * W;
+    const int x = blockIdx.x * EP_TX + threadIdx.x;
+    const int y = blockIdx.y * RG_TY + threadIdx.y;
+    const bool in = x < W && y < H;
+    const int xc = x < W ? x : W - 1, yc = y < H ? y : H - 1;
+    const int xm = xc == 0 ? W - 1 : xc - 1;
+    const int xp = xc == W - 1 ? 0 : xc + 1;
+    const float eps_p = p.eps_p, eps_u = p.eps_u;
+    const size_t rc = (size_t)yc * W;
+    const size_t ru = (size_t)(yc == 0 ? H - 1 : yc - 1) * W;
+    const size_t rd = (size_t)(yc == H - 1 ? 0 : yc + 1) * W;
+    const size_t i = rc + xc;
+    bool alpha = true;
+    float tsum = 0.f;
+    float acc[CT];
+#pragma unroll
+    for (int c = 0; c < CT; c++) acc[c] = 0.f;
+#pragma unroll 1
+    for (int c = 0; c < CT; c++) {
+        // the channel's ring potentials: read again by each kernel of the
+        // channel (L1 hits after the first)
+        const float* V = p.U + (size_t)c * NR * N + i;
+#pragma unroll 1
+        for (int k = 0; k < KT; k++) {
+            if (p.kt.src[k] != c) continue;
+            float g[NP];
+#pragma unroll
+            for (int pp = 0; pp < NP; pp++) {
+                const float val = p.maintain ? diffuse5<NP, KT>(p.P, pp * KT + k, N, ru, rc, rd, xm, xc, xp, eps_p)
+                                             : __ldg(p.P + (size_t)(pp * KT + k) * N + i);
+                alpha = alpha && (!p.maintain || val > eps_p);
+                g[pp] = val;
+            }
+            // ring weights and the potential
+            const float w1 = g[PK + 1], w2 = g[PK + 4];
+            const float b1 = w1 > 0.f ? g[PK + 2] : 0.f, b2 = w2 > 0.f ? g[PK + 5] : 0.f;
+            const float a1 = w1 > 0.f ? -0.5f * LOG2E / (w1 * w1) : 0.f;
+            const float a2 = w2 > 0.f ? -0.5f * LOG2E / (w2 * w2) : 0.f;
+            const float c1 = g[PK + 0], c2 = g[PK + 3];
+            float num = 0.f, den = 0.f;
+#pragma unroll 4
+            for (int r = 0; r < NR; r++) {
+                const float xr = p.ring_x[r];
+                const float d1 = xr - c1, d2 = xr - c2;
+                const float kr = b1 * ex2_approx((d1 * d1) * a1) + b2 * ex2_approx((d2 * d2) * a2);
+                num = fmaf(kr, __ldg(V + (size_t)r * N), num);
+                den = fmaf(kr, p.ring_cnt[r], den);
+            }
+            const float u = den > 0.f ? num / den : 0.f;
+            // growth (as in the other epilogues)
+            const float m = PMU >= 0 ? g[PMU >= 0 ? PMU : 0] : p.kt.mu[k];
+            const float sg = PSG >= 0 ? g[PSG >= 0 ? PSG : 0] : p.kt.sigma[k];
+            const float hh = PH >= 0 ? g[PH >= 0 ? PH : 0] : p.kt.h[k];
+            float gk = 0.f;
+            if (sg > 0.f) {
+                const float z = (u - m) / sg;
+                gk = expf(-0.5f * z * z);
+            }
+            const float t = p.alpha_on ? u : hh * gk;
+            tsum += t;
+            if (p.maintain) alpha = alpha && (t > eps_u);
+            const float G = p.growth_form == 0 ? hh * (2.f * gk - 1.f) : hh * gk;
+            const int d = p.kt.dst[k];
+#pragma unroll
+            for (int cc = 0; cc < CT; cc++)
+                if (cc == d) acc[cc] += G;
+        }
+    }
+    if (!p.maintain) alpha = true;
+    float st[CT * 5];
+#pragma unroll
+    for (int v = 0; v < CT * 5; v++) st[v] = 0.f;
+    if (in) {
+        if (p.P_out) {
+#pragma unroll 1
+            for (int pk = 0; pk < NP * KT; pk++) {
+                float val = 0.f;
+                if (alpha)
+                    val = p.maintain ? diffuse5<NP, KT>(p.P, pk, N, ru, rc, rd, xm, xc, xp, eps_p)
+                                     : __ldg(p.P + (size_t)pk * N + i);
+                p.P_out[(size_t)pk * N + i] = val;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CT; c++) {
+            const float a = __ldg(&p.A[(size_t)c * N + i]) + p.dt * (alpha ? acc[c] : p.acc0[c]);
+            const float an = fminf(fmaxf(a, 0.f), 1.f);
+            p.A_out[(size_t)c * N + i] = an;
+            if (p.partials) {
+                st[c * 5 + 0] = an;
+                st[c * 5 + 1] = an * __ldg(&p.sin_y[y]);
+                st[c * 5 + 2] = an * __ldg(&p.cos_y[y]);
+                st[c * 5 + 3] = an * __ldg(&p.sin_x[x]);
+                st[c * 5 + 4] = an * __ldg(&p.cos_x[x]);
+            }
+        }
+        if (p.alpha_out) p.alpha_out[i] = alpha ? 1 : 0;
+        if (p.empty_out) p.empty_out[i] = tsum > eps_u ? 0 : 1;
+    }
+    if (p.partials) block_stats<CT>(st, CT, p.partials);
+}
+
+int ring_epilogue_blocks(int H, int W) { return ((W + EP_TX - 1) / EP_TX) * ((H + RG_TY - 1) / RG_TY); }
+
 int epilogue_blocks(int H, int W)
 {
     return ((W + EP_TX - 1) / EP_TX) * ((H + EP_TY * EP_RY - 1) / (EP_TY * EP_RY));
@@ -352,7 +491,20 @@ cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks)
     if (n_blocks) *n_blocks = grid.x * grid.y;
     const int K = p.kt.K, C = p.kt.C;
     const int loc = (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
-    const bool r1 = (p.r_diff == 1 || !p.maintain) && p.n_rings == 0;
+    const bool rd1 = p.r_diff == 1 || !p.maintain;
+    const bool r1 = rd1 && p.n_rings == 0;
+    const int locr = loc | (p.p_kern >= 0 ? 8 : 0);
+    if (rd1 && p.n_rings > 0 && locr == 15 &&
+        ((p.n_rings == 24 && K == 15 && C == 3) || (p.n_rings == 24 && K == 1 && C == 1) ||
+         (p.n_rings == 12 && K == 15 && C == 3))) {
+        const dim3 rgrid((p.W + EP_TX - 1) / EP_TX, (p.H + RG_TY - 1) / RG_TY);
+        if (n_blocks) *n_blocks = rgrid.x * rgrid.y;
+        const dim3 rblock(EP_TX, RG_TY);
+        if (p.n_rings == 24 && K == 15) k_epilogue_rings<15, 3, 24, 15><<<rgrid, rblock, 0, s>>>(p);
+        else if (p.n_rings == 24) k_epilogue_rings<1, 1, 24, 15><<<rgrid, rblock, 0, s>>>(p);
+        else k_epilogue_rings<15, 3, 12, 15><<<rgrid, rblock, 0, s>>>(p);
+        return cudaGetLastError();
+    }
     if (r1 && K == 15 && C == 3 && loc == 3) k_epilogue_r1<15, 3, 3><<<grid, block, 0, s>>>(p);
     else if (r1 && K == 15 && C == 3 && loc == 0) k_epilogue_r1<15, 3, 0><<<grid, block, 0, s>>>(p);
     else if (r1 && K == 1 && C == 1 && loc == 3) k_epilogue_r1<1, 1, 3><<<grid, block, 0, s>>>(p);
