@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint_epilogue(AdjParams p)
     }
 }
 
-// gA_c = gpre_c + sum_{k: src(k) = c} V_k  (V_k = K~_k (x) gU_k, in kernel order)
+// gA_c = gpre_c + sum_{k: src(k) = c} V_k  (V_k = K~_k (x) gU_k, in kernel order),
+// or gpre_c + V_c when the sum over kernels was taken in the frequency domain
 __global__ void __launch_bounds__(256) k_adjoint_gather(AdjParams p)
 {
     const size_t N = (size_t)p.H * p.W;
@@ -92,8 +93,12 @@ __global__ void __launch_bounds__(256) k_adjoint_gather(AdjParams p)
     if (i >= N) return;
     for (int c = 0; c < p.kt.C; c++) {
         float s = __ldg(&p.gpre[(size_t)c * N + i]);
-        for (int k = 0; k < p.kt.K; k++)
-            if (p.kt.src[k] == c) s += __ldg(&p.V[(size_t)k * N + i]);
+        if (p.v_per_channel) {
+            s += __ldg(&p.V[(size_t)c * N + i]);
+        } else {
+            for (int k = 0; k < p.kt.K; k++)
+                if (p.kt.src[k] == c) s += __ldg(&p.V[(size_t)k * N + i]);
+        }
         p.gA_out[(size_t)c * N + i] = s;
     }
 }

@@ -165,6 +165,58 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
     }
 }
 
+// ---------------------------------- columns, transposed: sum_k K^_k x fwd(col_k), inv
+// The adjoint of the convolution stage for every source channel c at once:
+// V_c = sum_{k: src(k) = c} K~_k (x) G_k.  Per spectrum column: forward column
+// FFT of each kernel's gradient plane (Ahat plane k), times the kernel's real
+// spectrum, accumulated in the frequency domain; one inverse column FFT per
+// channel (Uhat plane c).  Same packed (DC, Nyquist) handling as k_cols_conv.
+template <int H, int T>
+__global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_adj(FftParams p)
+{
+    extern __shared__ float2 sm[];
+    constexpr int SZ = swz_size(H);
+    float2* F = sm;
+    float2* Acc = sm + SZ;
+    const int c = blockIdx.y;
+    const int kx = blockIdx.x;
+    const int M = p.W / 2;
+    const int HS = H / 2 + 1;
+    for (int i = threadIdx.x; i < H; i += T) Acc[swz(i)] = make_float2(0.f, 0.f);
+    auto sldF = [&](int, int i) { return F[swz(i)]; };
+    auto sstF = [&](int, int i, float2 v) { F[swz(i)] = v; };
+    const int nk = p.kcount[c];
+    for (int t = 0; t < nk; t++) {
+        const int k = p.klist[c][t];
+        const float2* src = p.Ahat + ((size_t)k * M + kx) * H;
+        auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
+        fft_run<H, 1, T, false, false>(p.tw_H, ld_g, sldF, sstF, sstF);
+        const float* Sk = p.S + (size_t)k * (M + 1) * HS;
+        // each thread updates its own entries of Acc (no barrier needed between
+        // the zeroing and the updates); F is complete after fft_run's barrier
+        for (int i = threadIdx.x; i < H; i += T) {
+            const int kyr = i <= H / 2 ? i : H - i;
+            const float2 f = F[swz(i)];
+            float2 v;
+            if (kx == 0) {
+                const float s0 = __ldg(&Sk[kyr]);
+                const float sn = __ldg(&Sk[(size_t)M * HS + kyr]);
+                const float2 fm = cconj(F[swz((H - i) & (H - 1))]);
+                const float a = 0.5f * (s0 + sn), bb = 0.5f * (s0 - sn);
+                v = make_float2(f.x * a + fm.x * bb, f.y * a + fm.y * bb);
+            } else {
+                v = cscale(f, __ldg(&Sk[(size_t)kx * HS + kyr]));
+            }
+            Acc[swz(i)] = cadd(Acc[swz(i)], v);
+        }
+    }
+    __syncthreads();
+    float2* dst = p.Uhat + ((size_t)c * M + kx) * H;
+    auto ld_acc = [&](int, int i) { return Acc[swz(i)]; };
+    auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
+    fft_run<H, 1, T, true, false>(p.tw_H, ld_acc, sldF, sstF, st_g);
+}
+
 // ------------------------------------------------------------ dispatch
 template <int M>
 static cudaError_t rows_launch(const FftParams& p, cudaStream_t s, bool inverse)
@@ -189,12 +241,12 @@ static cudaError_t rows_launch(const FftParams& p, cudaStream_t s, bool inverse)
 }
 
 template <int H>
-static cudaError_t cols_launch(const FftParams& p, cudaStream_t s)
+static cudaError_t cols_launch(const FftParams& p, cudaStream_t s, bool transposed = false)
 {
     constexpr int T = H / 16 >= 64 ? H / 16 : 64;
     const size_t smem = 2 * (size_t)swz_size(H) * sizeof(float2);
     const int M = p.W / 2;
-    auto kern = k_cols_conv<H, T>;
+    auto kern = transposed ? k_cols_adj<H, T> : k_cols_conv<H, T>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<dim3(M, p.C), T, smem, s>>>(p);
     return cudaGetLastError();
@@ -214,16 +266,16 @@ static cudaError_t rows_dispatch(const FftParams& p, cudaStream_t s, bool invers
     return cudaErrorInvalidValue;
 }
 
-static cudaError_t cols_dispatch(const FftParams& p, cudaStream_t s)
+static cudaError_t cols_dispatch(const FftParams& p, cudaStream_t s, bool transposed = false)
 {
     switch (p.H) {
-        case 64: return cols_launch<64>(p, s);
-        case 128: return cols_launch<128>(p, s);
-        case 256: return cols_launch<256>(p, s);
-        case 512: return cols_launch<512>(p, s);
-        case 1024: return cols_launch<1024>(p, s);
-        case 2048: return cols_launch<2048>(p, s);
-        case 4096: return cols_launch<4096>(p, s);
+        case 64: return cols_launch<64>(p, s, transposed);
+        case 128: return cols_launch<128>(p, s, transposed);
+        case 256: return cols_launch<256>(p, s, transposed);
+        case 512: return cols_launch<512>(p, s, transposed);
+        case 1024: return cols_launch<1024>(p, s, transposed);
+        case 2048: return cols_launch<2048>(p, s, transposed);
+        case 4096: return cols_launch<4096>(p, s, transposed);
     }
     return cudaErrorInvalidValue;
 }
@@ -236,6 +288,7 @@ bool fft_size_supported(int H, int W)
 
 cudaError_t launch_fft_rows_r2c(const FftParams& p, cudaStream_t s) { return rows_dispatch(p, s, false); }
 cudaError_t launch_fft_cols(const FftParams& p, cudaStream_t s) { return cols_dispatch(p, s); }
+cudaError_t launch_fft_cols_adj(const FftParams& p, cudaStream_t s) { return cols_dispatch(p, s, true); }
 cudaError_t launch_fft_rows_c2r(const FftParams& p, cudaStream_t s) { return rows_dispatch(p, s, true); }
 
 // ------------------------------------------------------- kernel spectra (FP64)

@@ -65,7 +65,7 @@ struct lenia_ctx {
     float* d_V = nullptr;
     double* d_gene_part = nullptr;
     double* d_gene_acc = nullptr;
-    float2* d_Ahat_t = nullptr;            // spectra of up to 8 gradient planes (transposed conv)
+    float2* d_Ahat_t = nullptr;            // spectra of the K gradient planes (transposed conv)
     float2* d_Uhat_t = nullptr;
     // evolutionary operators (lenia_set_walls, lenia_step_evolve)
     int* d_walls = nullptr;                // wall site indices
@@ -393,44 +393,44 @@ lenia_status step_impl(lenia_ctx* c, const float* A_in, const float* P_in, float
     return LENIA_OK;
 }
 
-// V_k = K~_k (x) gU_k for every kernel (the transpose of the convolution;
-// the kernels are point symmetric), in groups of at most kMaxChannels
-// kernels that the forward convolution kernels treat as channels.
-lenia_status transposed_conv(lenia_ctx* c, const float* gU, float* V, cudaStream_t s)
+// The transpose of the convolution stage (the kernels are point symmetric, so
+// each kernel's transpose is the same convolution).  FFT path: per source
+// channel c, V_c = sum_{k: src(k) = c} K~_k (x) gU_k, summed in the frequency
+// domain (forward transforms of the K gradient planes, one inverse transform
+// per channel); returns true in *per_channel.  Direct path: V_k for every
+// kernel, in groups of at most kMaxChannels kernels treated as channels.
+lenia_status transposed_conv(lenia_ctx* c, const float* gU, float* V, cudaStream_t s, bool* per_channel)
 {
     const int K = c->cfg.n_kernels;
+    if (c->path == LENIA_CONV_FFT) {
+        FftParams fp = c->fp;
+        fp.A = gU;
+        fp.U = V;
+        fp.Ahat = c->d_Ahat_t;        // K planes
+        fp.Uhat = c->d_Uhat_t;        // C planes
+        fp.C = K;                      // the row pass transforms every gradient plane
+        CUDA_OR_FAIL(c, launch_fft_rows_r2c(fp, s));
+        fp.C = c->cfg.n_channels;      // one column block row per source channel
+        CUDA_OR_FAIL(c, launch_fft_cols_adj(fp, s));
+        fp.K = c->cfg.n_channels;      // inverse row pass of the C summed planes
+        CUDA_OR_FAIL(c, launch_fft_rows_c2r(fp, s));
+        *per_channel = true;
+        return LENIA_OK;
+    }
     for (int k0 = 0; k0 < K; k0 += kMaxChannels) {
         const int g = std::min(kMaxChannels, K - k0);
-        if (c->path == LENIA_CONV_FFT) {
-            FftParams fp = c->fp;
-            fp.A = gU + (size_t)k0 * c->N;
-            fp.U = V + (size_t)k0 * c->N;
-            fp.Ahat = c->d_Ahat_t;
-            fp.Uhat = c->d_Uhat_t;
-            fp.C = g;
-            fp.K = g;
-            for (int j = 0; j < kMaxChannels; j++) fp.kcount[j] = 0;
-            for (int j = 0; j < g; j++) {
-                fp.kcount[j] = 1;
-                fp.klist[j][0] = k0 + j;
-            }
-            fp.k_base = k0;   // the group's spectra and outputs are planes 0 .. g-1
-            CUDA_OR_FAIL(c, launch_fft_rows_r2c(fp, s));
-            CUDA_OR_FAIL(c, launch_fft_cols(fp, s));
-            CUDA_OR_FAIL(c, launch_fft_rows_c2r(fp, s));
-        } else {
-            ConvParams cp = c->cp;
-            cp.A = gU + (size_t)k0 * c->N;
-            cp.U = V;   // kernel k writes plane k
-            cp.C = g;
-            for (int j = 0; j < kMaxChannels; j++) cp.kcount[j] = 0;
-            for (int j = 0; j < g; j++) {
-                cp.kcount[j] = 1;
-                cp.klist[j][0] = k0 + j;
-            }
-            CUDA_OR_FAIL(c, launch_direct_conv(cp, c->max_R, s));
+        ConvParams cp = c->cp;
+        cp.A = gU + (size_t)k0 * c->N;
+        cp.U = V;   // kernel k writes plane k
+        cp.C = g;
+        for (int j = 0; j < kMaxChannels; j++) cp.kcount[j] = 0;
+        for (int j = 0; j < g; j++) {
+            cp.kcount[j] = 1;
+            cp.klist[j][0] = k0 + j;
         }
+        CUDA_OR_FAIL(c, launch_direct_conv(cp, c->max_R, s));
     }
+    *per_channel = false;
     return LENIA_OK;
 }
 
@@ -737,9 +737,8 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         ALLOC(c->d_gene_part, (size_t)adjoint_blocks(H, W) * K * 3);
         ALLOC(c->d_gene_acc, (size_t)K * 3);
         if (path == LENIA_CONV_FFT) {
-            const int g = std::min(K, kMaxChannels);
-            ALLOC(c->d_Ahat_t, (size_t)g * (W / 2) * H);
-            ALLOC(c->d_Uhat_t, (size_t)g * (W / 2) * H);
+            ALLOC(c->d_Ahat_t, (size_t)K * (W / 2) * H);     // spectra of the K gradient planes
+            ALLOC(c->d_Uhat_t, (size_t)C * (W / 2) * H);     // their per-channel sums
         }
     }
     CK_INIT(cudaStreamSynchronize(s));
@@ -844,8 +843,10 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
             ap.dt = c->cfg.dt;
             ap.kt = c->kt;
             CUDA_OR_FAIL(c, launch_adjoint_epilogue(ap, s));
-            st = transposed_conv(c, c->d_gU, c->d_V, s);
+            bool per_channel = false;
+            st = transposed_conv(c, c->d_gU, c->d_V, s, &per_channel);
             if (st != LENIA_OK) return st;
+            ap.v_per_channel = per_channel ? 1 : 0;
             CUDA_OR_FAIL(c, launch_adjoint_gather(ap, s));
             cur ^= 1;
         }

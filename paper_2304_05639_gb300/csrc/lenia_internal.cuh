@@ -105,7 +105,8 @@ struct AdjParams {
     const float* gA_next;      // dL/dA_{t+1} [C][H][W]
     float* gpre;               // clip-masked dL/dA_{t+1} [C][H][W]
     float* gU;                 // dL/dU [K][H][W]
-    const float* V;            // K~_k (x) gU_k [K][H][W]
+    const float* V;            // K~_k (x) gU_k [K][H][W], or summed per source channel [C][H][W]
+    int v_per_channel;         // 1: V holds sum_{src(k) = c} K~_k (x) gU_k per channel c
     float* gA_out;             // dL/dA_t [C][H][W]
     double* gene_partials;     // [blocks][K][3]
     double* gene_acc;          // [K][3]: d/dmu, d/dsigma, d/dh
@@ -118,6 +119,8 @@ struct AdjParams {
 cudaError_t launch_direct_conv(const ConvParams& p, int max_R, cudaStream_t s);
 cudaError_t launch_fft_rows_r2c(const FftParams& p, cudaStream_t s);
 cudaError_t launch_fft_cols(const FftParams& p, cudaStream_t s);
+// transposed column pass: Uhat plane c = inv( sum_{k in klist[c]} S_k fwd(Ahat plane k) ), grid (M, C)
+cudaError_t launch_fft_cols_adj(const FftParams& p, cudaStream_t s);
 cudaError_t launch_fft_rows_c2r(const FftParams& p, cudaStream_t s);
 cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks);
 cudaError_t launch_stats_partials(const float* A, int C, int H, int W, const float* sin_y,

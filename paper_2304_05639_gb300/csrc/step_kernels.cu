@@ -360,12 +360,13 @@ __device__ __forceinline__ float diffuse5(const float* P, int pk, size_t N, size
     const float v0 = __ldg(pl + ru + xc), v1 = __ldg(pl + rc + xm), v2 = __ldg(pl + rc + xc);
     const float v3 = __ldg(pl + rc + xp), v4 = __ldg(pl + rd + xc);
     const float sm = (((v0 + v1) + v2) + v3) + v4;
-    const int n = (v0 > eps_p) + (v1 > eps_p) + (v2 > eps_p) + (v3 > eps_p) + (v4 > eps_p);
-    return n > 0 ? fminf(fmaxf(sm / (float)n, 0.f), 1.f) : 0.f;
+    const float n = (float)(v0 > eps_p) + (float)(v1 > eps_p) + (float)(v2 > eps_p) + (float)(v3 > eps_p) +
+                    (float)(v4 > eps_p);
+    return n > 0.f ? __saturatef(sm * rcp_approx(n)) : 0.f;
 }
 
 template <int KT, int CT, int NR, int LOC>
-__global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
+__global__ void __launch_bounds__(256, 5) k_epilogue_rings(EpiParams p)
 {
     constexpr int NG = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
     constexpr int NP = NG + 6;
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
     for (int c = 0; c < CT; c++) {
         // the channel's ring potentials: read again by each kernel of the
         // channel (L1 hits after the first)
-        const float* V = p.U + (size_t)c * NR * N + i;
+        const float* V0 = p.U + (size_t)c * NR * N + i;
 #pragma unroll 1
         for (int k = 0; k < KT; k++) {
             if (p.kt.src[k] != c) continue;
@@ -415,12 +416,13 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
             const float a2 = w2 > 0.f ? -0.5f * LOG2E / (w2 * w2) : 0.f;
             const float c1 = g[PK + 0], c2 = g[PK + 3];
             float num = 0.f, den = 0.f;
+            const float* V = V0;
 #pragma unroll 4
-            for (int r = 0; r < NR; r++) {
+            for (int r = 0; r < NR; r++, V += N) {
                 const float xr = p.ring_x[r];
                 const float d1 = xr - c1, d2 = xr - c2;
                 const float kr = b1 * ex2_approx((d1 * d1) * a1) + b2 * ex2_approx((d2 * d2) * a2);
-                num = fmaf(kr, __ldg(V + (size_t)r * N), num);
+                num = fmaf(kr, __ldg(V), num);
                 den = fmaf(kr, p.ring_cnt[r], den);
             }
             const float u = den > 0.f ? num / den : 0.f;
