@@ -9,9 +9,11 @@
 //   dL/dmu_k    = sum gpre dt h_k F' g (U - mu) / sigma^2
 //   dL/dsigma_k = sum gpre dt h_k F' g (U - mu)^2 / sigma^3
 //   dL/dh_k     = sum gpre dt F(g)
-// as block partials reduced in FP64 in a fixed order.  The transposed
-// convolution (gA_src += K~_k (x) gU_k; K~ is point symmetric, so it is the
-// same convolution) runs on the forward machinery; k_adjoint_gather adds it.
+// as block partials reduced in FP64 in a fixed order by the block that
+// finishes last.  The transposed convolution (gA_src += K~_k (x) gU_k; K~ is
+// point symmetric, so it is the same convolution) runs on the forward
+// machinery; its inverse row pass adds gpre (FFT path) or k_adjoint_gather
+// adds it (direct path).
 #include "lenia_internal.cuh"
 #include "ptx_util.cuh"
 
@@ -82,6 +84,25 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint_epilogue(AdjParams p)
         for (int w = 0; w < ADJ_THREADS / 32; w++) s += (double)red[w][v];
         p.gene_partials[(size_t)blockIdx.x * K * 3 + v] = s;
     }
+    // the block that finishes last adds every block's partials to gene_acc,
+    // blocks in order (deterministic), and re-arms the ticket
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(p.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // one warp per value: lane l sums blocks l, l + 32, ... in order, then a
+    // fixed shuffle tree (the same order every launch)
+    for (int v = warp; v < K * 3; v += ADJ_THREADS / 32) {
+        double s = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(&p.gene_partials[(size_t)b * K * 3 + v]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) p.gene_acc[v] += s;
+    }
+    if (threadIdx.x == 0) *p.ticket = 0u;
 }
 
 // gA_c = gpre_c + sum_{k: src(k) = c} V_k  (V_k = K~_k (x) gU_k, in kernel order),
@@ -103,16 +124,6 @@ __global__ void __launch_bounds__(256) k_adjoint_gather(AdjParams p)
     }
 }
 
-// gene_acc[v] += sum_b partials[b][v], one thread per value, blocks in order.
-__global__ void k_adjoint_gene_reduce(const double* partials, int n_blocks, int nv, double* gene_acc)
-{
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    double s = 0.0;
-    for (int b = 0; b < n_blocks; b++) s += partials[(size_t)b * nv + v];
-    gene_acc[v] += s;
-}
-
 __global__ void k_adjoint_gene_out(const double* gene_acc, int nv, float* out)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -124,10 +135,6 @@ int adjoint_blocks(int H, int W) { return (int)(((size_t)H * W + ADJ_THREADS - 1
 cudaError_t launch_adjoint_epilogue(const AdjParams& p, cudaStream_t s)
 {
     k_adjoint_epilogue<<<adjoint_blocks(p.H, p.W), ADJ_THREADS, 0, s>>>(p);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int nv = p.kt.K * 3;
-    k_adjoint_gene_reduce<<<(nv + 63) / 64, 64, 0, s>>>(p.gene_partials, adjoint_blocks(p.H, p.W), nv, p.gene_acc);
     return cudaGetLastError();
 }
 

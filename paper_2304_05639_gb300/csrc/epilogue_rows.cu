@@ -418,15 +418,35 @@ bool plane_map(CUtensorMap* out, const float* base, int W, int H, int planes, in
 
 }  // namespace
 
+// Shared-memory limit and resident CTAs per SM of one instantiation, found
+// once per device.
+template <auto Kern>
+static cudaError_t rows_occupancy(size_t bytes, int* per_sm)
+{
+    static std::atomic<int> occ[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int v = occ[dev].load(std::memory_order_relaxed);
+    if (v > 0) {
+        *per_sm = v;
+        return cudaSuccess;
+    }
+    cudaError_t e = smem_limit<Kern>(bytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, Kern, ER_THREADS, bytes);
+    if (e != cudaSuccess) return e;
+    occ[dev].store(v);
+    *per_sm = v;
+    return cudaSuccess;
+}
+
 template <int KT, int CT, int LOC, int TOPO = 0>
 static cudaError_t launch_rows(const EpiParams& p, int num_sms, int* status, cudaStream_t s, int* n_blocks)
 {
     using L = ErLayout<KT, CT, LOC>;
     auto kern = p.eps_p == 0.f ? k_epilogue_rows<KT, CT, LOC, TOPO, 1> : k_epilogue_rows<KT, CT, LOC, TOPO, 0>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
-    if (e != cudaSuccess) return e;
     int per_sm = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ER_THREADS, L::bytes);
+    cudaError_t e = p.eps_p == 0.f ? rows_occupancy<k_epilogue_rows<KT, CT, LOC, TOPO, 1>>(L::bytes, &per_sm)
+                                   : rows_occupancy<k_epilogue_rows<KT, CT, LOC, TOPO, 0>>(L::bytes, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int n_chunks = p.W / ER_CH;

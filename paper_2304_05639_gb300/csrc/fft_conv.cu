@@ -113,14 +113,24 @@ __global__ void __launch_bounds__(T) k_rows_c2r(FftParams p)
     }
     __syncthreads();
     float2* out = reinterpret_cast<float2*>(p.U + ((size_t)k * p.H + y0) * W);
+    const float2* addp = p.add ? reinterpret_cast<const float2*>(p.add + ((size_t)k * p.H + y0) * W) : nullptr;
     auto sld = [&](int b, int i) { return sm[b * SZ + swz32(i)]; };
     auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz32(i)] = v; };
-    auto st_g = [&](int b, int i, float2 v) { out[(size_t)b * M + i] = v; };
+    auto st_g = [&](int b, int i, float2 v) {
+        if (addp) {
+            const float2 a = __ldg(&addp[(size_t)b * M + i]);
+            v = make_float2(a.x + v.x, a.y + v.y);
+        }
+        out[(size_t)b * M + i] = v;
+    };
     fft_run<M, NB, T, true, false, ROW_RMAX>(p.tw_M, sld, sld, sst, st_g);
 }
 
 // ------------------------------------------------------- columns: fwd, x K^, inv
-template <int H, int T>
+// PERK: one block per (column, channel, kernel of that channel), grid z = the
+// longest kernel list: shorter serial chains for small grids, at the cost of
+// repeating the forward column transform for every kernel of a channel.
+template <int H, int T, bool PERK>
 __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(FftParams p)
 {
     extern __shared__ float2 sm[];
@@ -131,6 +141,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
     const int kx = blockIdx.x;
     const int M = p.W / 2;
     const int HS = H / 2 + 1;
+    if (PERK && (int)blockIdx.z >= p.kcount[c]) return;     // uniform over the block
 
     const float2* src = p.Ahat + ((size_t)c * M + kx) * H;
     auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
@@ -138,8 +149,9 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
     auto sstF = [&](int, int i, float2 v) { F[swz(i)] = v; };
     fft_run<H, 1, T, false, false>(p.tw_H, ld_g, sldF, sstF, sstF);
 
-    const int nk = p.kcount[c];
-    for (int t = 0; t < nk; t++) {
+    const int t0 = PERK ? (int)blockIdx.z : 0;
+    const int nk = PERK ? t0 + 1 : p.kcount[c];
+    for (int t = t0; t < nk; t++) {
         const int k = p.klist[c][t];
         const float* Sk = p.S + (size_t)k * (M + 1) * HS;
         auto ld_mul = [&](int, int i) {
@@ -218,26 +230,37 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_adj(Fft
 }
 
 // ------------------------------------------------------------ dispatch
+template <int M, int NB>
+static cudaError_t rows_launch_nb(const FftParams& p, cudaStream_t s, bool inverse)
+{
+    constexpr int T0 = NB * M / ROW_RMAX;
+    constexpr int T = T0 < 32 ? 32 : (T0 < 512 ? T0 : 512);
+    const size_t smem = (size_t)NB * row_pitch(M) * sizeof(float2);
+    if (p.H % NB) return cudaErrorInvalidValue;
+    if (!inverse) {
+        cudaError_t e = smem_limit<k_rows_r2c<M, T, NB>>(smem);
+        if (e != cudaSuccess) return e;
+        k_rows_r2c<M, T, NB><<<dim3(p.H / NB, p.C), T, smem, s>>>(p);
+    } else {
+        cudaError_t e = smem_limit<k_rows_c2r<M, T, NB>>(smem);
+        if (e != cudaSuccess) return e;
+        k_rows_c2r<M, T, NB><<<dim3(p.H / NB, p.K), T, smem, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
 template <int M>
 static cudaError_t rows_launch(const FftParams& p, cudaStream_t s, bool inverse)
 {
     // at least 8 rows per block (64-byte runs of the column-major spectra) and
-    // at least 4096 complex values; one radix-ROW_RMAX butterfly per thread
+    // at least 4096 complex values; one radix-ROW_RMAX butterfly per thread.
+    // Grids that would have fewer than 256 blocks (small worlds, few planes)
+    // take 8 rows per block instead, for parallelism.
     constexpr int NB0 = (4096 / M) > 8 ? (4096 / M) : 8;
     constexpr int NB = NB0 < 64 ? NB0 : 64;
-    constexpr int T = (NB * M / ROW_RMAX) < 512 ? (NB * M / ROW_RMAX) : 512;
-    const size_t smem = (size_t)NB * row_pitch(M) * sizeof(float2);
-    if (p.H % NB) return cudaErrorInvalidValue;
-    if (!inverse) {
-        auto kern = k_rows_r2c<M, T, NB>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<dim3(p.H / NB, p.C), T, smem, s>>>(p);
-    } else {
-        auto kern = k_rows_c2r<M, T, NB>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<dim3(p.H / NB, p.K), T, smem, s>>>(p);
-    }
-    return cudaGetLastError();
+    const int planes = inverse ? p.K : p.C;
+    if (NB > 8 && (p.H / NB) * planes < 256) return rows_launch_nb<M, 8>(p, s, inverse);
+    return rows_launch_nb<M, NB>(p, s, inverse);
 }
 
 template <int H>
@@ -246,9 +269,24 @@ static cudaError_t cols_launch(const FftParams& p, cudaStream_t s, bool transpos
     constexpr int T = H / 16 >= 64 ? H / 16 : 64;
     const size_t smem = 2 * (size_t)swz_size(H) * sizeof(float2);
     const int M = p.W / 2;
-    auto kern = transposed ? k_cols_adj<H, T> : k_cols_conv<H, T>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<dim3(M, p.C), T, smem, s>>>(p);
+    if (transposed) {
+        cudaError_t e = smem_limit<k_cols_adj<H, T>>(smem);
+        if (e != cudaSuccess) return e;
+        k_cols_adj<H, T><<<dim3(M, p.C), T, smem, s>>>(p);
+        return cudaGetLastError();
+    }
+    int kmax = 0;
+    for (int c = 0; c < p.C; c++) kmax = p.kcount[c] > kmax ? p.kcount[c] : kmax;
+    // fewer than ~4 blocks per SM of a 152-SM part: one block per kernel
+    if (M * p.C < 608 && kmax > 1) {
+        cudaError_t e = smem_limit<k_cols_conv<H, T, true>>(smem);
+        if (e != cudaSuccess) return e;
+        k_cols_conv<H, T, true><<<dim3(M, p.C, kmax), T, smem, s>>>(p);
+    } else {
+        cudaError_t e = smem_limit<k_cols_conv<H, T, false>>(smem);
+        if (e != cudaSuccess) return e;
+        k_cols_conv<H, T, false><<<dim3(M, p.C), T, smem, s>>>(p);
+    }
     return cudaGetLastError();
 }
 

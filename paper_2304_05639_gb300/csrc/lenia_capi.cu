@@ -59,6 +59,8 @@ struct lenia_ctx {
     int ckpt = 0, max_steps = 0;
     float* d_ckpt = nullptr;               // [n_ckpt][C][H][W]
     float* d_seg = nullptr;                // [max(ckpt, 2)][C][H][W]
+    float* d_Useg = nullptr;               // [ckpt][K][H][W] potentials of the segment's states
+    unsigned int* d_adj_ticket = nullptr;  // last-block ticket of the gene-gradient reduction
     float* d_gA[2] = {nullptr, nullptr};
     float* d_gpre = nullptr;
     float* d_gU = nullptr;
@@ -397,15 +399,18 @@ lenia_status step_impl(lenia_ctx* c, const float* A_in, const float* P_in, float
 // each kernel's transpose is the same convolution).  FFT path: per source
 // channel c, V_c = sum_{k: src(k) = c} K~_k (x) gU_k, summed in the frequency
 // domain (forward transforms of the K gradient planes, one inverse transform
-// per channel); returns true in *per_channel.  Direct path: V_k for every
-// kernel, in groups of at most kMaxChannels kernels treated as channels.
-lenia_status transposed_conv(lenia_ctx* c, const float* gU, float* V, cudaStream_t s, bool* per_channel)
+// per channel); returns true in *per_channel, and with `out` writes
+// out_c = add_c + V_c instead of V.  Direct path: V_k for every kernel, in
+// groups of at most kMaxChannels kernels treated as channels.
+lenia_status transposed_conv(lenia_ctx* c, const float* gU, float* V, cudaStream_t s, bool* per_channel,
+                             const float* add = nullptr, float* out = nullptr)
 {
     const int K = c->cfg.n_kernels;
     if (c->path == LENIA_CONV_FFT) {
         FftParams fp = c->fp;
         fp.A = gU;
-        fp.U = V;
+        fp.U = out ? out : V;          // with out: out_c = add_c + V_c in the inverse row pass
+        fp.add = out ? add : nullptr;
         fp.Ahat = c->d_Ahat_t;        // K planes
         fp.Uhat = c->d_Uhat_t;        // C planes
         fp.C = K;                      // the row pass transforms every gradient plane
@@ -471,7 +476,7 @@ void lenia_destroy(lenia_ctx* c)
                     c->d_A3, c->d_P3, c->d_stats, c->d_status, c->d_ckpt, c->d_seg, c->d_gA[0],
                     c->d_gA[1], c->d_gpre, c->d_gU, c->d_V, c->d_gene_part, c->d_gene_acc,
                     c->d_Ahat_t, c->d_Uhat_t, c->d_ticket, c->d_walls, c->d_alpha_e, c->d_empty,
-                    c->d_cnt};
+                    c->d_cnt, c->d_Useg, c->d_adj_ticket};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -729,6 +734,9 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         const size_t nA1 = c->N * C;
         ALLOC(c->d_ckpt, (size_t)n_ckpt * nA1);
         ALLOC(c->d_seg, (size_t)std::max(c->ckpt, 2) * nA1);
+        ALLOC(c->d_Useg, (size_t)c->ckpt * K * c->N);
+        ALLOC(c->d_adj_ticket, 1);
+        CK_INIT(cudaMemset(c->d_adj_ticket, 0, sizeof(unsigned int)));
         ALLOC(c->d_gA[0], nA1);
         ALLOC(c->d_gA[1], nA1);
         ALLOC(c->d_gpre, nA1);
@@ -810,26 +818,28 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
         prev = dst;
     }
     // backward, segment by segment from the last: recompute the segment's
-    // states from its checkpoint, then apply the step adjoint in reverse
+    // states and their potentials from its checkpoint, then apply the step
+    // adjoint in reverse
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_gene_acc, 0, (size_t)K * 3 * sizeof(double), s));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_gA[0], gA_T, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    auto useg = [&](int j) { return c->d_Useg + (size_t)j * K * c->N; };
     int cur = 0;
     const int n_seg = (n_steps + L - 1) / L;
     for (int sg = n_seg - 1; sg >= 0; sg--) {
         const int s0 = sg * L, s1 = std::min(n_steps, s0 + L);
-        for (int j = 1; j < s1 - s0; j++) {
-            lenia_status st = step_impl(c, j == 1 ? ckpt(sg) : seg(j - 1), nullptr, seg(j), nullptr, nullptr,
-                                        nullptr, nullptr, s);
+        for (int j = 0; j < s1 - s0; j++) {
+            const float* Aj = j == 0 ? ckpt(sg) : seg(j);
+            lenia_status st = potentials(c, Aj, useg(j), s);
+            if (st == LENIA_OK && j + 1 < s1 - s0)
+                st = step_impl(c, Aj, nullptr, seg(j + 1), nullptr, nullptr, nullptr, useg(j), s);
             if (st != LENIA_OK) return st;
         }
         for (int t = s1 - 1; t >= s0; t--) {
             const float* At = t == s0 ? ckpt(sg) : seg(t - s0);
-            lenia_status st = potentials(c, At, c->d_U, s);
-            if (st != LENIA_OK) return st;
             AdjParams ap;
             memset(&ap, 0, sizeof(ap));
             ap.A = At;
-            ap.U = c->d_U;
+            ap.U = useg(t - s0);
             ap.gA_next = c->d_gA[cur];
             ap.gpre = c->d_gpre;
             ap.gU = c->d_gU;
@@ -837,6 +847,7 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
             ap.gA_out = c->d_gA[cur ^ 1];
             ap.gene_partials = c->d_gene_part;
             ap.gene_acc = c->d_gene_acc;
+            ap.ticket = c->d_adj_ticket;
             ap.H = c->cfg.height;
             ap.W = c->cfg.width;
             ap.growth_form = c->cfg.growth_form;
@@ -844,10 +855,9 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
             ap.kt = c->kt;
             CUDA_OR_FAIL(c, launch_adjoint_epilogue(ap, s));
             bool per_channel = false;
-            st = transposed_conv(c, c->d_gU, c->d_V, s, &per_channel);
+            lenia_status st = transposed_conv(c, c->d_gU, c->d_V, s, &per_channel, c->d_gpre, c->d_gA[cur ^ 1]);
             if (st != LENIA_OK) return st;
-            ap.v_per_channel = per_channel ? 1 : 0;
-            CUDA_OR_FAIL(c, launch_adjoint_gather(ap, s));
+            if (!per_channel) CUDA_OR_FAIL(c, launch_adjoint_gather(ap, s));
             cur ^= 1;
         }
     }

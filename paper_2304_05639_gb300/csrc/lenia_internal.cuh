@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace lenia {
 
 constexpr int kMaxKernels = 64;
@@ -11,6 +13,25 @@ constexpr int kMaxPlanes = 9;   // mu, sigma, h, then the ring-wise kernel genes
 constexpr int kMaxRings = 64;
 constexpr int kMaxConvPlanes = 256;   // convolution outputs: kernels, or channels x rings
 constexpr int ROW_RMAX = 32;     // largest radix of the row transforms (column transforms: 16)
+
+// Raises kernel Kern's dynamic shared-memory limit to `bytes` the first time a
+// launch needs it on the current device; the attribute persists, so later
+// launches skip the driver call.
+template <auto Kern>
+inline cudaError_t smem_limit(size_t bytes)
+{
+    static std::atomic<int> done[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (done[dev].load(std::memory_order_relaxed) >= (int)bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) {
+        int cur = done[dev].load();
+        while (cur < (int)bytes && !done[dev].compare_exchange_weak(cur, (int)bytes)) {
+        }
+    }
+    return e;
+}
 
 // Per-kernel scalars, passed by value to the kernels that need them.
 struct KernelTable {
@@ -94,6 +115,7 @@ struct FftParams {
     const float2* tw_H;        // per-pass twiddle tables of the length-H column transforms
     int H, W, C, K;
     int k_base;                // the column pass writes Uhat plane k - k_base (0 for the forward step)
+    const float* add;          // inverse row pass: added to its output, same layout as U (nullable)
     int kcount[kMaxChannels];
     int klist[kMaxChannels][kMaxKernels];
 };
@@ -110,6 +132,7 @@ struct AdjParams {
     float* gA_out;             // dL/dA_t [C][H][W]
     double* gene_partials;     // [blocks][K][3]
     double* gene_acc;          // [K][3]: d/dmu, d/dsigma, d/dh
+    unsigned int* ticket;      // completion counter of the gene reduction (0 between launches)
     int H, W, growth_form;
     float dt;
     KernelTable kt;

@@ -76,7 +76,8 @@ cudaError_t launch_direct_conv(const ConvParams& p, int max_R, cudaStream_t s)
 {
     const size_t smem = (size_t)(DC_TX + 2 * max_R) * (DC_TY + 2 * max_R) * sizeof(float);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(k_direct_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_limit<k_direct_conv>(smem);
+    if (e != cudaSuccess) return e;
     dim3 grid((p.W + DC_TX - 1) / DC_TX, (p.H + DC_TY - 1) / DC_TY, p.C);
     k_direct_conv<<<grid, dim3(32, DC_TY / DC_ROWS), smem, s>>>(p, max_R);
     return cudaGetLastError();
