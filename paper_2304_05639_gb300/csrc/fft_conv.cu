@@ -234,17 +234,18 @@ template <int M, int NB>
 static cudaError_t rows_launch_nb(const FftParams& p, cudaStream_t s, bool inverse)
 {
     constexpr int T0 = NB * M / ROW_RMAX;
-    constexpr int T = T0 < 32 ? 32 : (T0 < 512 ? T0 : 512);
+    constexpr int T1 = T0 < 32 ? 32 : (T0 < 512 ? T0 : 512);
+    constexpr int TI = T1;
     const size_t smem = (size_t)NB * row_pitch(M) * sizeof(float2);
     if (p.H % NB) return cudaErrorInvalidValue;
     if (!inverse) {
-        cudaError_t e = smem_limit<k_rows_r2c<M, T, NB>>(smem);
+        cudaError_t e = smem_limit<k_rows_r2c<M, T1, NB>>(smem);
         if (e != cudaSuccess) return e;
-        k_rows_r2c<M, T, NB><<<dim3(p.H / NB, p.C), T, smem, s>>>(p);
+        k_rows_r2c<M, T1, NB><<<dim3(p.H / NB, p.C), T1, smem, s>>>(p);
     } else {
-        cudaError_t e = smem_limit<k_rows_c2r<M, T, NB>>(smem);
+        cudaError_t e = smem_limit<k_rows_c2r<M, TI, NB>>(smem);
         if (e != cudaSuccess) return e;
-        k_rows_c2r<M, T, NB><<<dim3(p.H / NB, p.K), T, smem, s>>>(p);
+        k_rows_c2r<M, TI, NB><<<dim3(p.H / NB, p.K), TI, smem, s>>>(p);
     }
     return cudaGetLastError();
 }
