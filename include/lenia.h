@@ -241,10 +241,23 @@ LENIA_API lenia_status lenia_selftest_wait_timeout(lenia_ctx* ctx, int32_t limit
 
 /* lenia_step with HOST buffers: copies A_in/P_in host->device into library
  * buffers, steps, and copies A_out/P_out (and stats_out, C*3 floats, nullable)
- * back; returns after the stream has finished.  Page-locked host memory
- * makes the copies fast; pageable memory works. */
+ * back; returns after the copies have finished (lenia_step_host_async
+ * followed by lenia_host_wait).  Page-locked host memory makes the copies
+ * fast; pageable memory works. */
 LENIA_API lenia_status lenia_step_host(lenia_ctx* ctx, const float* A_in, const float* P_in,
                              float* A_out, float* P_out, float* stats_out, void* stream);
+
+/* The same step enqueued without waiting, for independent host worlds in a
+ * row (a serving loop): the phenospace upload and the convolution run on
+ * `stream` while the genes upload on a library stream; the downloads run on
+ * another library stream and overlap the next call's uploads.  Host buffers
+ * must stay valid and unmodified (inputs) / unread (outputs) until
+ * lenia_host_wait returns.  Each call's inputs must not be a previous call's
+ * pending outputs. */
+LENIA_API lenia_status lenia_step_host_async(lenia_ctx* ctx, const float* A_in, const float* P_in,
+                                             float* A_out, float* P_out, float* stats_out, void* stream);
+/* Waits for every enqueued host step (downloads included), then lenia_check. */
+LENIA_API lenia_status lenia_host_wait(lenia_ctx* ctx, void* stream);
 
 /* Per-launch timing for benchmarks.  lenia_profile_start makes the library
  * record a CUDA event pair on the launching stream around each of its next

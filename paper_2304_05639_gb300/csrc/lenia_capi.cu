@@ -75,6 +75,11 @@ struct lenia_ctx {
     uint8_t* d_alpha_e = nullptr;          // [H][W] alpha of the evolving step
     uint8_t* d_empty = nullptr;            // [H][W] not Delta_sum(U)
     uint16_t* d_cnt = nullptr;             // [H][W] empty sites per K_oxy disk
+    // host-buffer steps (lenia_step_host[_async]): a stream for gene uploads and
+    // one for downloads, and the events that order them against the compute
+    cudaStream_t up_stream = nullptr, down_stream = nullptr;
+    cudaEvent_t ev_up = nullptr, ev_done = nullptr, ev_down = nullptr;
+    bool host_pending = false;             // a download has been enqueued since the last wait
     // optional per-launch timing (lenia_profile_start / lenia_profile_stop)
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -480,6 +485,10 @@ void lenia_destroy(lenia_ctx* c)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : {c->ev_up, c->ev_done, c->ev_down})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t t : {c->up_stream, c->down_stream})
+        if (t) cudaStreamDestroy(t);
     delete c;
 }
 
@@ -1038,26 +1047,71 @@ lenia_status lenia_selftest_wait_timeout(lenia_ctx* c, int32_t limit_mcycles, vo
     return LENIA_OK;
 }
 
-lenia_status lenia_step_host(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
-                             float* stats_out, void* stream)
+lenia_status lenia_step_host_async(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
+                                   float* stats_out, void* stream)
 {
     if (!c) return LENIA_EINVAL;
     if (!A_in || !A_out || (c->n_p && (!P_in || !P_out)))
         return fail(c, LENIA_EINVAL, "host A (and P with localized genes) must be non-null");
+    if (!c->up_stream) {
+        CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking));
+        CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->down_stream, cudaStreamNonBlocking));
+        CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming));
+        CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming));
+        CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_down, cudaEventDisableTiming));
+        // nothing recorded yet: record once so that the first waits are no-ops
+        CUDA_OR_FAIL(c, cudaEventRecord(c->ev_done, (cudaStream_t)stream));
+        CUDA_OR_FAIL(c, cudaEventRecord(c->ev_down, (cudaStream_t)stream));
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t ab = c->N * c->cfg.n_channels * sizeof(float);
     const size_t pb = c->N * c->n_p * c->cfg.n_kernels * sizeof(float);
+    // genes upload on their own stream once the previous step no longer reads
+    // the staging buffer; the phenospace upload and the convolution (which
+    // reads A only) proceed meanwhile on the compute stream
+    if (pb) {
+        CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->up_stream, c->ev_done, 0));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_P2, P_in, pb, cudaMemcpyHostToDevice, c->up_stream));
+        CUDA_OR_FAIL(c, cudaEventRecord(c->ev_up, c->up_stream));
+    }
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(s, c->ev_done, 0));      // (a caller may change streams)
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_A2, A_in, ab, cudaMemcpyHostToDevice, s));
-    if (pb) CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_P2, P_in, pb, cudaMemcpyHostToDevice, s));
-    lenia_status st = step_impl(c, c->d_A2, c->n_p ? c->d_P2 : nullptr, c->d_A3, c->n_p ? c->d_P3 : nullptr,
-                                stats_out ? c->d_stats : nullptr, nullptr, nullptr, s);
+    lenia_status st = potentials(c, c->d_A2, c->d_U, s);
     if (st != LENIA_OK) return st;
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(A_out, c->d_A3, ab, cudaMemcpyDeviceToHost, s));
-    if (pb) CUDA_OR_FAIL(c, cudaMemcpyAsync(P_out, c->d_P3, pb, cudaMemcpyDeviceToHost, s));
+    if (pb) CUDA_OR_FAIL(c, cudaStreamWaitEvent(s, c->ev_up, 0));
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(s, c->ev_down, 0));      // the previous download is done with d_A3/d_P3
+    st = step_impl(c, c->d_A2, c->n_p ? c->d_P2 : nullptr, c->d_A3, c->n_p ? c->d_P3 : nullptr,
+                   stats_out ? c->d_stats : nullptr, nullptr, c->d_U, s);
+    if (st != LENIA_OK) return st;
+    CUDA_OR_FAIL(c, cudaEventRecord(c->ev_done, s));
+    // downloads on their own stream, overlapping the next step's uploads
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->down_stream, c->ev_done, 0));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(A_out, c->d_A3, ab, cudaMemcpyDeviceToHost, c->down_stream));
+    if (pb) CUDA_OR_FAIL(c, cudaMemcpyAsync(P_out, c->d_P3, pb, cudaMemcpyDeviceToHost, c->down_stream));
     if (stats_out)
         CUDA_OR_FAIL(c, cudaMemcpyAsync(stats_out, c->d_stats, c->cfg.n_channels * 3 * sizeof(float),
-                                        cudaMemcpyDeviceToHost, s));
+                                        cudaMemcpyDeviceToHost, c->down_stream));
+    CUDA_OR_FAIL(c, cudaEventRecord(c->ev_down, c->down_stream));
+    c->host_pending = true;
+    return LENIA_OK;
+}
+
+lenia_status lenia_host_wait(lenia_ctx* c, void* stream)
+{
+    if (!c) return LENIA_EINVAL;
+    if (c->host_pending) {
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->down_stream));
+        c->host_pending = false;
+    }
     return lenia_check(c, stream);
+}
+
+lenia_status lenia_step_host(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
+                             float* stats_out, void* stream)
+{
+    lenia_status st = lenia_step_host_async(c, A_in, P_in, A_out, P_out, stats_out, stream);
+    if (st != LENIA_OK) return st;
+    return lenia_host_wait(c, stream);
 }
 
 lenia_status lenia_profile_start(lenia_ctx* c, int32_t max_launches)

@@ -27,7 +27,8 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_last_error", "lenia_status_string", "lenia_destroy", "lenia_profile_start",
            "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes", "lenia_batch_init",
            "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy",
-           "lenia_selftest_wait_timeout", "lenia_set_walls", "lenia_step_evolve")
+           "lenia_selftest_wait_timeout", "lenia_set_walls", "lenia_step_evolve",
+           "lenia_step_host_async", "lenia_host_wait")
 PROFILE_KINDS = 10
 
 
@@ -109,6 +110,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_update_from_potentials.restype = st
     lib.lenia_step_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.lenia_step_host.restype = st
+    lib.lenia_step_host_async.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.lenia_step_host_async.restype = st
+    lib.lenia_host_wait.argtypes = [vp, vp]
+    lib.lenia_host_wait.restype = st
     lib.lenia_kernel_weights.argtypes = [vp, ctypes.c_int32, vp]
     lib.lenia_kernel_weights.restype = st
     lib.lenia_conv_path.argtypes = [vp]
@@ -312,6 +317,15 @@ def lenia_step_evolve(ctx, A, P, A_out, P_out, events, stats_out=None, alpha_out
     ev = events if isinstance(events, LeniaEvents) else events_struct(events)
     _check(ctx, load().lenia_step_evolve(ctx, _ptr(A), _ptr(P), _ptr(A_out), _ptr(P_out), ctypes.byref(ev),
                                          _ptr(stats_out), _ptr(alpha_out), _ptr(epen_out), _stream(stream)))
+
+
+def lenia_step_host_async(ctx, A_in, P_in, A_out, P_out, stats_out=None, stream=None):
+    _check(ctx, load().lenia_step_host_async(ctx, _ptr(A_in), _ptr(P_in), _ptr(A_out), _ptr(P_out),
+                                             _ptr(stats_out), _stream(stream)))
+
+
+def lenia_host_wait(ctx, stream=None):
+    _check(ctx, load().lenia_host_wait(ctx, _stream(stream)))
 
 
 def lenia_step_host(ctx, A_in, P_in, A_out, P_out, stats_out=None, stream=None):

@@ -335,6 +335,35 @@ def test_step_host_matches_step():
         lenia.lenia_destroy(ctx)
 
 
+def test_step_host_async_pipeline_matches_step():
+    """Several independent host worlds enqueued back to back (uploads of one
+    overlapping downloads of the previous): each output equals lenia_step of
+    its own input, stats included."""
+    torch = torch_mod()
+    worlds = [w_c3_small(), inputs.multi_channel(H=128, W=128, R=18, patch=40, n_geno=4, seed_index=12, live=True),
+              inputs.multi_channel(H=128, W=128, R=18, patch=40, n_geno=4, seed_index=13, live=True)]
+    cfg, ks = lenia.config_from_world(worlds[0], lenia.CONV_FFT)
+    ctx = lenia.lenia_init(cfg, ks)
+    try:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        ins = [(pin(w.A), pin(w.P)) for w in worlds] * 2              # six calls, inputs reused
+        outs = [(torch.empty_like(a).pin_memory(), torch.empty_like(p).pin_memory(),
+                 torch.zeros((3, 3), dtype=torch.float32).pin_memory()) for (a, p) in ins]
+        for (a, p), (ao, po, so) in zip(ins, outs):
+            lenia.lenia_step_host_async(ctx, a, p, ao, po, so)
+        lenia.lenia_host_wait(ctx)
+        for j, ((a, p), (ao, po, so)) in enumerate(zip(ins, outs)):
+            A_in, P_in = a.cuda(), p.cuda()
+            A2, P2 = torch.empty_like(A_in), torch.empty_like(P_in)
+            st = torch.zeros((3, 3), dtype=torch.float32, device="cuda")
+            lenia.lenia_step(ctx, A_in, P_in, A2, P2, st)
+            torch.cuda.synchronize()
+            assert torch.equal(ao, A2.cpu()) and torch.equal(po, P2.cpu()), j
+            assert torch.equal(so, st.cpu()), j
+    finally:
+        lenia.lenia_destroy(ctx)
+
+
 # ------------------------------------------------------- errors and edges
 
 def test_argument_errors():
