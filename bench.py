@@ -235,7 +235,7 @@ def evolve_leg(torch, lenia, inputs, stream, plain_ms, steps=100):
     disk_bytes = sites * (1 + 2) + sites * (2 + 1)
     return {"workload": "2048x2048, 3 channels, 15 kernels R=18, walls + mutation + penalisation each step",
             "steps": steps, "ms_per_step": ms, "value": sites / (ms / 1e3), "unit": UNIT,
-            "over_plain_step": ms / plain_ms,
+            "over_plain_step": ms / plain_ms if plain_ms else None,
             "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
             "disk_passes_gbs": disk_bytes / (disk_ms / 1e3) / 1e9 if disk_ms > 0 else None,
             "stats_finite": bool(torch.isfinite(st).all())}
@@ -534,7 +534,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched-world, evolution and ring legs")
     ap.add_argument("--size", type=int, default=2048, help="torus side (2048 = the benchmark workload)")
     ap.add_argument("--conv-path", type=int, default=0, help="0 auto, 1 fft, 2 direct")
-    ap.add_argument("--leg", default=None, choices=["adjoint", "batched", "rings"],
+    ap.add_argument("--leg", default=None, choices=["adjoint", "batched", "evolve", "rings"],
                     help="run only this extra leg (N = 1) and print its JSON object (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -556,6 +556,8 @@ def run_leg(args):
         out = adjoint_leg(torch, lenia, inputs, stream)
     elif args.leg == "batched":
         out = batched_leg(torch, lenia, inputs, stream, steps=args.steps)
+    elif args.leg == "evolve":
+        out = evolve_leg(torch, lenia, inputs, stream, None, steps=args.steps)
     else:
         out = rings_leg(torch, lenia, inputs, stream, steps=args.steps)
     print(json.dumps({"leg": args.leg, **out}), flush=True)

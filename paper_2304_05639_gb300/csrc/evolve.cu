@@ -21,8 +21,11 @@ namespace lenia {
 constexpr int DK_T = 32;        // output tile side
 constexpr int DK_THREADS = 256; // 32 x 8 threads, 4 output rows each
 
+// Periodic index; indices already inside [0, n) (all but the halo near the
+// world's edges) skip the division.
 __device__ __forceinline__ int wrap_i(int v, int n)
 {
+    if (v >= 0 && v < n) return v;
     v %= n;
     return v < 0 ? v + n : v;
 }
@@ -37,19 +40,42 @@ __global__ void __launch_bounds__(DK_THREADS) k_disk_pass(EvoParams p)
     const int S = DK_T + 2 * r;
     const int SP = S + 1;                       // odd row pitch: the row scans hit distinct banks
     const int y0 = blockIdx.y * DK_T - r, x0 = blockIdx.x * DK_T - r;
-    for (int e = threadIdx.x; e < S * S; e += DK_THREADS) {
-        const int ty = e / S, tx = e - ty * S;
-        const size_t gi = (size_t)wrap_i(y0 + ty, p.H) * p.W + wrap_i(x0 + tx, p.W);
-        pre[ty * SP + tx + 1] = PASS == 1 ? (int)p.empty[gi] : p.n_disk - (int)p.cnt_in[gi];
+    for (int ty = threadIdx.x >> 5; ty < S; ty += DK_THREADS / 32) {
+        const size_t row = (size_t)wrap_i(y0 + ty, p.H) * p.W;
+        for (int tx = threadIdx.x & 31; tx < S; tx += 32) {
+            const size_t gi = row + wrap_i(x0 + tx, p.W);
+            pre[ty * SP + tx + 1] = PASS == 1 ? (int)p.empty[gi] : p.n_disk - (int)p.cnt_in[gi];
+        }
     }
     __syncthreads();
-    for (int row = threadIdx.x; row < S; row += DK_THREADS) {
-        int* q = pre + row * SP;
-        int run = 0;
-        q[0] = 0;
-        for (int j = 1; j <= S; j++) {
-            run += q[j];
-            q[j] = run;
+    // prefix sums, one warp per tile row: each lane owns up to 3 consecutive
+    // entries (S <= 96), then a warp scan of the lanes' totals
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int per = (S + 31) / 32;
+        for (int row = warp; row < S; row += DK_THREADS / 32) {
+            int* q = pre + row * SP;
+            int part[3];
+            int sum = 0;
+#pragma unroll
+            for (int t = 0; t < 3; t++) {
+                const int j = lane * per + t;
+                sum += (t < per && j < S) ? q[j + 1] : 0;
+                part[t] = sum;
+            }
+            int incl = sum;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int n = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += n;
+            }
+            const int excl = incl - sum;
+#pragma unroll
+            for (int t = 0; t < 3; t++) {
+                const int j = lane * per + t;
+                if (t < per && j < S) q[j + 1] = excl + part[t];
+            }
+            if (lane == 0) q[0] = 0;
         }
     }
     __syncthreads();
