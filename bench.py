@@ -106,6 +106,15 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def workload_config(ws, conv_path, size=2048):
+    """The benchmark workload, named by what it is (both arms print the same;
+    other sizes are profiling runs of the same recipe)."""
+    return {"workload": WORKLOAD if size == 2048 else WORKLOAD.replace("2048x2048", f"{size}x{size}"),
+            "height": size, "width": size, "channels": 3, "kernels": 15, "radius": 18,
+            "gene_planes": 30, "worlds": ws, "parallelism": "replicas" if ws > 1 else "single",
+            "conv_path": conv_path, "l2": "inputs larger than L2 (A + P = 551 MB per world)"}
+
+
 def adjoint_leg(torch, lenia, inputs, stream):
     """Forward rollout vs rollout adjoint: 256^2, 3 channels, 15 kernels R=13,
     global genes, 64 steps, checkpoints every 8."""
@@ -371,8 +380,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 2048 * 2048 / v * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": 0,
-                       "parallelism": "replicas"},
+            "config": workload_config(ws, "direct FP64 sums (CPU oracle)"),
             "cpu_baseline": {**cb, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -486,12 +494,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "height": H, "width": W, "channels": world.n_channels,
-                   "kernels": world.n_kernels, "radius": 18, "gene_planes": 30,
-                   "global_batch": ws, "seq_len": 0,
-                   "parallelism": "replicas" if ws > 1 else "single",
-                   "conv_path": "fft" if path == lenia.CONV_FFT else "direct",
-                   "l2": "inputs larger than L2 (A + P = 551 MB per world)"},
+        "config": workload_config(ws, "fft" if path == lenia.CONV_FFT else "direct", args.size),
         "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic,
