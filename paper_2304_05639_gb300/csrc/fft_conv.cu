@@ -19,23 +19,55 @@
 // the stored kernel spectra.
 #include "fft_core.cuh"
 #include "lenia_internal.cuh"
+#include "ptx_util.cuh"
 
 namespace lenia {
 
 // ---------------------------------------------------------------- rows R2C
-template <int M, int T, int NB>
+// BULK: the block's NB rows are contiguous in A; one bulk copy stages them,
+// unswizzled, at the start of the work buffer, and the first pass reads them
+// from there (its stores follow the pass's barrier, so the two layouts may
+// share the buffer).  Otherwise the first pass reads A directly.
+template <int M, int T, int NB, bool BULK>
 __global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
 {
-    extern __shared__ float2 sm[];
+    extern __shared__ float4 sm4[];
+    float2* sm = reinterpret_cast<float2*>(sm4);
     constexpr int SZ = row_pitch(M);
     const int c = blockIdx.y;
     const int y0 = blockIdx.x * NB;
     const int W = 2 * M;
     const float2* src = reinterpret_cast<const float2*>(p.A + ((size_t)c * p.H + y0) * W);
-    auto ld_g = [&](int b, int i) { return __ldg(&src[(size_t)b * M + i]); };
     auto sld = [&](int b, int i) { return sm[b * SZ + swz32(i)]; };
     auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz32(i)] = v; };
-    fft_run<M, NB, T, false, false, ROW_RMAX>(p.tw_M, ld_g, sld, sst, sst);
+    if constexpr (BULK) {
+        __shared__ uint64_t bar;
+        constexpr uint32_t bytes = (uint32_t)NB * M * sizeof(float2);
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(&bar, bytes);
+            bulk_g2s(sm, src, bytes, &bar);
+        }
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0));
+        if (!ok) {
+            // the copy did not land in time: report it, give it a last bounded
+            // chance to finish before the block's shared memory is released
+            if (threadIdx.x == 0) {
+                if (p.status) atomicExch(p.status, kStatusWaitTimeout);
+                mbar_wait_bounded(&bar, 0);
+            }
+            return;
+        }
+        auto ld_s = [&](int b, int i) { return sm[b * M + i]; };
+        fft_run<M, NB, T, false, false, ROW_RMAX>(p.tw_M, ld_s, sld, sst, sst);
+    } else {
+        auto ld_g = [&](int b, int i) { return __ldg(&src[(size_t)b * M + i]); };
+        fft_run<M, NB, T, false, false, ROW_RMAX>(p.tw_M, ld_g, sld, sst, sst);
+    }
 
     // X[k] = E[k] + w_W^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i
     // Output column kx holds rows y0 .. y0 + NB - 1 contiguously (b fastest).
@@ -239,9 +271,16 @@ static cudaError_t rows_launch_nb(const FftParams& p, cudaStream_t s, bool inver
     const size_t smem = (size_t)NB * row_pitch(M) * sizeof(float2);
     if (p.H % NB) return cudaErrorInvalidValue;
     if (!inverse) {
-        cudaError_t e = smem_limit<k_rows_r2c<M, T1, NB>>(smem);
-        if (e != cudaSuccess) return e;
-        k_rows_r2c<M, T1, NB><<<dim3(p.H / NB, p.C), T1, smem, s>>>(p);
+        // bulk staging needs 16-byte aligned rows (always, for 16-byte aligned A)
+        if (((uintptr_t)p.A & 15) == 0) {
+            cudaError_t e = smem_limit<k_rows_r2c<M, T1, NB, true>>(smem);
+            if (e != cudaSuccess) return e;
+            k_rows_r2c<M, T1, NB, true><<<dim3(p.H / NB, p.C), T1, smem, s>>>(p);
+        } else {
+            cudaError_t e = smem_limit<k_rows_r2c<M, T1, NB, false>>(smem);
+            if (e != cudaSuccess) return e;
+            k_rows_r2c<M, T1, NB, false><<<dim3(p.H / NB, p.C), T1, smem, s>>>(p);
+        }
     } else {
         cudaError_t e = smem_limit<k_rows_c2r<M, TI, NB>>(smem);
         if (e != cudaSuccess) return e;

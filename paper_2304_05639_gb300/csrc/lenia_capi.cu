@@ -731,6 +731,7 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         c->fp.W = W;
         c->fp.C = C;
         c->fp.K = NC;
+        c->fp.status = c->d_status;
         memcpy(c->fp.kcount, kcount, sizeof(kcount));
         memcpy(c->fp.klist, klist, sizeof(klist));
     }

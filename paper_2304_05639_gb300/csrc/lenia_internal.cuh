@@ -116,6 +116,7 @@ struct FftParams {
     int H, W, C, K;
     int k_base;                // the column pass writes Uhat plane k - k_base (0 for the forward step)
     const float* add;          // inverse row pass: added to its output, same layout as U (nullable)
+    int* status;               // device status word for bounded waits (nullable)
     int kcount[kMaxChannels];
     int klist[kMaxChannels][kMaxKernels];
 };
