@@ -312,14 +312,17 @@ LENIA_API int32_t lenia_launches_per_step(const lenia_ctx* ctx);
  * paper itself).
  * lenia_batch_init makes one context per world from cfgs[0..n_worlds) and
  * kernels (world w's n_kernels descriptors follow world w-1's).  With
- * autotune != 0, worlds whose conv_path is AUTO get the faster of the FFT and
- * direct paths, timed once per distinct (size, channels, kernels, genes,
+ * autotune != 0, worlds whose conv_path is AUTO take the FFT path when several
+ * worlds share their (size, channels, kernels, genes) - so that they can step
+ * as a group, see lenia_batch_group_of - and otherwise the faster of the FFT
+ * and direct paths, timed once per distinct (size, channels, kernels, genes,
  * largest radius).  All scratch is allocated here.
  * lenia_batch_rollout advances every world n_steps in place: A and P are HOST
  * arrays of n_worlds DEVICE pointers (P[w] may be NULL for worlds without gene
  * maps; P itself may be NULL if no world has them).  The steps of all worlds
  * are captured once per pointer set into a CUDA graph whose branches run the
- * worlds concurrently; one graph launch advances every world two steps.  The
+ * groups and the remaining worlds concurrently; one graph launch advances
+ * every world two steps.  The
  * work is ordered after earlier work on `stream` and before later work.
  * Worlds must not share buffers.  No statistics are computed. */
 typedef struct lenia_batch lenia_batch;
@@ -328,6 +331,15 @@ LENIA_API lenia_status lenia_batch_init(int32_t n_worlds, const lenia_config* cf
                                         void* stream, lenia_batch** out);
 LENIA_API lenia_status lenia_batch_rollout(lenia_batch* batch, float* const* A, float* const* P,
                                            int32_t n_steps, void* stream);
+/* Group of world w (worlds on the FFT path of one size whose configuration and
+ * kernel topology are identical - kernel shapes may differ, and global genes
+ * that the gene maps replace are ignored - step together:
+ * one launch per stage for the whole group, the worlds along the launch's
+ * planes or grid z), or -1 when it steps on its own (or w is out of range).
+ * A grouped world's epilogue is the tiled kernel (FP32 division and expf),
+ * which can differ in the last bits from the streaming kernel a world of
+ * width 256 k would use on its own. */
+LENIA_API int32_t lenia_batch_group_of(const lenia_batch* batch, int32_t world);
 /* Convolution path chosen for world w (LENIA_CONV_FFT or LENIA_CONV_DIRECT), or -1. */
 LENIA_API int32_t lenia_batch_conv_path(const lenia_batch* batch, int32_t world);
 /* lenia_check over every world's context after synchronising `stream`. */

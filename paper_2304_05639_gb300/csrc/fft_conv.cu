@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
     const int c = blockIdx.y;
     const int y0 = blockIdx.x * NB;
     const int W = 2 * M;
-    const float2* src = reinterpret_cast<const float2*>(p.A + ((size_t)c * p.H + y0) * W);
+    const float* plane = p.A_list ? p.A_list[c / p.cw] + (size_t)(c % p.cw) * p.H * W : p.A + (size_t)c * p.H * W;
+    const float2* src = reinterpret_cast<const float2*>(plane + (size_t)y0 * W);
     auto sld = [&](int b, int i) { return sm[b * SZ + swz32(i)]; };
     auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz32(i)] = v; };
     if constexpr (BULK) {
@@ -169,13 +170,14 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
     constexpr int SZ = swz_size(H);
     float2* F = sm;
     float2* Wk = sm + SZ;
-    const int c = blockIdx.y;
+    const int plane = blockIdx.y;              // Ahat plane: channel c of world w
+    const int c = plane % p.cw, w = plane / p.cw;
     const int kx = blockIdx.x;
     const int M = p.W / 2;
     const int HS = H / 2 + 1;
     if (PERK && (int)blockIdx.z >= p.kcount[c]) return;     // uniform over the block
 
-    const float2* src = p.Ahat + ((size_t)c * M + kx) * H;
+    const float2* src = p.Ahat + ((size_t)plane * M + kx) * H;
     auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
     auto sldF = [&](int, int i) { return F[swz(i)]; };
     auto sstF = [&](int, int i, float2 v) { F[swz(i)] = v; };
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
     const int nk = PERK ? t0 + 1 : p.kcount[c];
     for (int t = t0; t < nk; t++) {
         const int k = p.klist[c][t];
-        const float* Sk = p.S + (size_t)k * (M + 1) * HS;
+        const float* Sk = (p.S_list ? p.S_list[w] : p.S) + (size_t)k * (M + 1) * HS;
         auto ld_mul = [&](int, int i) {
             const int ky = i;
             const int kyr = ky <= H / 2 ? ky : H - ky;
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
             const float s = __ldg(&Sk[(size_t)kx * HS + kyr]);
             return cscale(f, s);
         };
-        float2* dst = p.Uhat + ((size_t)(k - p.k_base) * M + kx) * H;
+        float2* dst = p.Uhat + ((size_t)(w * p.kpw + k - p.k_base) * M + kx) * H;
         auto sldW = [&](int, int i) { return Wk[swz(i)]; };
         auto sstW = [&](int, int i, float2 v) { Wk[swz(i)] = v; };
         auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
@@ -271,8 +273,9 @@ static cudaError_t rows_launch_nb(const FftParams& p, cudaStream_t s, bool inver
     const size_t smem = (size_t)NB * row_pitch(M) * sizeof(float2);
     if (p.H % NB) return cudaErrorInvalidValue;
     if (!inverse) {
-        // bulk staging needs 16-byte aligned rows (always, for 16-byte aligned A)
-        if (((uintptr_t)p.A & 15) == 0) {
+        // bulk staging needs 16-byte aligned rows (always, for 16-byte aligned A;
+        // a batched launch's caller checks every listed pointer)
+        if (p.A_list ? p.list_aligned != 0 : ((uintptr_t)p.A & 15) == 0) {
             cudaError_t e = smem_limit<k_rows_r2c<M, T1, NB, true>>(smem);
             if (e != cudaSuccess) return e;
             k_rows_r2c<M, T1, NB, true><<<dim3(p.H / NB, p.C), T1, smem, s>>>(p);
@@ -316,7 +319,7 @@ static cudaError_t cols_launch(const FftParams& p, cudaStream_t s, bool transpos
         return cudaGetLastError();
     }
     int kmax = 0;
-    for (int c = 0; c < p.C; c++) kmax = p.kcount[c] > kmax ? p.kcount[c] : kmax;
+    for (int c = 0; c < p.cw && c < kMaxChannels; c++) kmax = p.kcount[c] > kmax ? p.kcount[c] : kmax;
     // fewer than ~4 blocks per SM of a 152-SM part: one block per kernel
     if (M * p.C < 608 && kmax > 1) {
         cudaError_t e = smem_limit<k_cols_conv<H, T, true>>(smem);

@@ -1,10 +1,17 @@
 // Batched worlds: many independent Lenia worlds of uneven sizes, radii and
 // genotypes advanced together.  Each world keeps its own context (kernels,
-// spectra, scratch); the steps of all worlds are captured once into a CUDA
-// graph whose branches run the worlds concurrently on worker streams, and the
-// graph is replayed, so a rollout costs one graph launch per two steps.  An
-// autotuner times the FFT and direct paths once per distinct world shape and
-// keeps the faster one.
+// spectra, scratch).  Worlds on the FFT path of the same size whose
+// configuration and kernel topology are identical (they may differ in kernel
+// shapes, genotypes and state) form a group that steps in one launch per
+// stage: the row and column transforms treat the group's worlds as extra
+// planes (the column pass reads each world's kernel spectra through a list),
+// and the tiled epilogue takes the worlds along grid z, each reading and
+// writing through per-world pointer lists.  The steps of
+// all groups and remaining worlds are captured once into a CUDA graph whose
+// branches run concurrently on worker streams, and the graph is replayed, so
+// a rollout costs one graph launch per two steps.  Sizes shared by several
+// worlds take the FFT path (so that they group); an autotuner times the FFT
+// and direct paths once for every other shape and keeps the faster one.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -30,9 +37,29 @@ struct ShapeKey {
 
 }  // namespace
 
+// Worlds stepped together (identical configuration and kernel topology, FFT
+// path; kernel shapes may differ, each world's spectra come from a list).
+struct Group {
+    std::vector<int> worlds;
+    lenia::lenia_ctx_view v;               // the first world's parameters
+    float2* Ahat = nullptr;                // [n][C][M][H]
+    float2* Uhat = nullptr;                // [n][K][M][H]
+    float* U = nullptr;                    // [n][K][H][W]
+    const float** S = nullptr;             // per-world kernel spectra (worlds may differ in kernels)
+    // per-world pointer lists for the two ping-pong directions:
+    // [0] caller's state -> batch state, [1] batch state -> caller's state
+    const float** Ain[2] = {nullptr, nullptr};
+    const float** Pin[2] = {nullptr, nullptr};
+    float** Aout[2] = {nullptr, nullptr};
+    float** Pout[2] = {nullptr, nullptr};
+    bool aligned = false;                  // every listed A pointer is 16-byte aligned
+};
+
 struct lenia_batch {
     int n = 0;
     std::vector<lenia_ctx*> ctx;
+    std::vector<Group> groups;
+    std::vector<int> group_of;             // world -> group index or -1
     std::vector<size_t> abytes, pbytes;
     std::vector<float*> A2, P2;            // library-owned second state per world
     cudaStream_t origin = nullptr;
@@ -85,6 +112,48 @@ float time_path(const lenia_config& cfg0, const lenia_kernel_desc* ks, int path,
     return ms;
 }
 
+void free_group(Group& g)
+{
+    void* ptrs[] = {g.Ahat, g.Uhat, g.U, g.S, g.Ain[0], g.Ain[1], g.Pin[0], g.Pin[1], g.Aout[0], g.Aout[1],
+                    g.Pout[0], g.Pout[1]};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+// One step of every world of a group: A/P lists of direction `dir`.
+lenia_status group_step(const Group& g, int dir, cudaStream_t s)
+{
+    const int n = (int)g.worlds.size();
+    lenia::FftParams fp = g.v.fp;
+    fp.A = nullptr;
+    fp.A_list = g.Ain[dir];
+    fp.S_list = g.S;
+    fp.list_aligned = g.aligned ? 1 : 0;
+    fp.Ahat = g.Ahat;
+    fp.Uhat = g.Uhat;
+    fp.U = g.U;
+    fp.cw = g.v.C;
+    fp.kpw = g.v.K;
+    fp.C = n * g.v.C;                      // planes of the row and column passes
+    fp.K = n * g.v.K;                      // planes of the inverse row pass
+    if (lenia::launch_fft_rows_r2c(fp, s) != cudaSuccess) return LENIA_ECUDA;
+    if (lenia::launch_fft_cols(fp, s) != cudaSuccess) return LENIA_ECUDA;
+    if (lenia::launch_fft_rows_c2r(fp, s) != cudaSuccess) return LENIA_ECUDA;
+    lenia::EpiParams ep = g.v.ep;
+    ep.A = ep.P = nullptr;
+    ep.A_out = ep.P_out = nullptr;
+    ep.A_list = g.Ain[dir];
+    ep.P_list = g.Pin[dir];
+    ep.Aout_list = g.Aout[dir];
+    ep.Pout_list = g.Pout[dir];
+    ep.U = g.U;
+    ep.u_stride = (size_t)g.v.K * g.v.N;
+    ep.partials = nullptr;
+    ep.stats_out = nullptr;
+    ep.alpha_out = ep.empty_out = nullptr;
+    return lenia::launch_epilogue_batch(ep, n, s) == cudaSuccess ? LENIA_OK : LENIA_ECUDA;
+}
+
 void destroy_graphs(lenia_batch* b)
 {
     if (b->g2) cudaGraphExecDestroy(b->g2);
@@ -104,8 +173,23 @@ lenia_status capture(lenia_batch* b, float* const* A, float* const* P, int steps
     lenia_status st = LENIA_OK;
     cudaEventRecord(b->fork, b->origin);
     for (int w = 0; w < kWorkers; w++) cudaStreamWaitEvent(b->workers[w], b->fork, 0);
+    int lane = 0;
+    for (size_t gi = 0; gi < b->groups.size() && st == LENIA_OK; gi++) {
+        Group& g = b->groups[gi];
+        cudaStream_t s = b->workers[lane++ % kWorkers];
+        for (int t = 0; t < steps && st == LENIA_OK; t++) st = group_step(g, t % 2, s);
+        for (int i : g.worlds) {
+            if (st != LENIA_OK || !copy_back || !(steps % 2)) break;
+            if (cudaMemcpyAsync(A[i], b->A2[i], b->abytes[i], cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                st = LENIA_ECUDA;
+            if (b->pbytes[i] &&
+                cudaMemcpyAsync(P[i], b->P2[i], b->pbytes[i], cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                st = LENIA_ECUDA;
+        }
+    }
     for (int i = 0; i < b->n && st == LENIA_OK; i++) {
-        cudaStream_t s = b->workers[i % kWorkers];
+        if (b->group_of[i] >= 0) continue;
+        cudaStream_t s = b->workers[lane++ % kWorkers];
         const bool hasP = b->pbytes[i] > 0;
         for (int t = 0; t < steps && st == LENIA_OK; t++) {
             const bool even = (t % 2) == 0;
@@ -166,6 +250,7 @@ void lenia_batch_destroy(lenia_batch* b)
 {
     if (!b) return;
     destroy_graphs(b);
+    for (Group& g : b->groups) free_group(g);
     for (lenia_ctx* c : b->ctx) lenia_destroy(c);
     for (float* p : b->A2)
         if (p) cudaFree(p);
@@ -201,6 +286,22 @@ lenia_status lenia_batch_init(int32_t n_worlds, const lenia_config* cfgs, const 
         return LENIA_ECUDA;
     }
     std::map<ShapeKey, int> tuned;   // shape -> chosen path
+    // shapes shared by several worlds take the FFT path when it exists: their
+    // worlds can then step as one group (one launch per stage for all of them)
+    std::map<ShapeKey, int> shape_count;
+    {
+        size_t ko = 0;
+        for (int i = 0; i < n_worlds; i++) {
+            const lenia_kernel_desc* ks = kernels + ko;
+            if (cfgs[i].n_kernels < 1 || cfgs[i].n_kernels > 64) break;      // reported below
+            ko += cfgs[i].n_kernels;
+            int rmax = 0;
+            for (int k = 0; k < cfgs[i].n_kernels; k++) rmax = rmax > ks[k].radius ? rmax : ks[k].radius;
+            (void)rmax;
+            shape_count[ShapeKey{cfgs[i].height, cfgs[i].width, cfgs[i].n_channels, cfgs[i].n_kernels,
+                                 cfgs[i].localized, cfgs[i].maintain_genes, 0}]++;
+        }
+    }
     size_t koff = 0;
     for (int i = 0; i < n_worlds; i++) {
         lenia_config cfg = cfgs[i];
@@ -218,9 +319,14 @@ lenia_status lenia_batch_init(int32_t n_worlds, const lenia_config* cfgs, const 
                                cfg.maintain_genes, rmax};
             auto it = tuned.find(key);
             if (it == tuned.end()) {
-                const float t_direct = time_path(cfg, ks, LENIA_CONV_DIRECT, s);
-                const float t_fft = time_path(cfg, ks, LENIA_CONV_FFT, s);   // inf when unsupported
-                it = tuned.emplace(key, t_fft < t_direct ? LENIA_CONV_FFT : LENIA_CONV_DIRECT).first;
+                const ShapeKey size_key{key.H, key.W, key.C, key.K, key.loc, key.maintain, 0};
+                if (shape_count[size_key] > 1 && lenia::fft_size_supported(cfg.height, cfg.width) && cfg.n_rings == 0) {
+                    it = tuned.emplace(key, LENIA_CONV_FFT).first;
+                } else {
+                    const float t_direct = time_path(cfg, ks, LENIA_CONV_DIRECT, s);
+                    const float t_fft = time_path(cfg, ks, LENIA_CONV_FFT, s);   // inf when unsupported
+                    it = tuned.emplace(key, t_fft < t_direct ? LENIA_CONV_FFT : LENIA_CONV_DIRECT).first;
+                }
             }
             cfg.conv_path = it->second;
         }
@@ -245,6 +351,68 @@ lenia_status lenia_batch_init(int32_t n_worlds, const lenia_config* cfgs, const 
         b->A2.push_back(a2);
         b->P2.push_back(p2);
     }
+    // groups: worlds on the FFT path with a tiled epilogue whose configuration
+    // and kernels are identical field by field
+    b->group_of.assign(n_worlds, -1);
+    {
+        std::map<std::vector<double>, std::vector<int>> members;
+        size_t ko = 0;
+        for (int i = 0; i < n_worlds; i++) {
+            const lenia_config& c0 = cfgs[i];
+            const lenia_kernel_desc* ks = kernels + ko;
+            ko += c0.n_kernels;
+            lenia::lenia_ctx_view v;
+            if (!lenia::ctx_view(b->ctx[i], &v) || !lenia::epilogue_batch_supported(v.ep)) continue;
+            std::vector<double> key = {(double)c0.height, (double)c0.width, (double)c0.n_channels,
+                                       (double)c0.n_kernels, c0.dt, (double)c0.growth_form, (double)c0.localized,
+                                       (double)c0.maintain_genes, c0.eps_u, c0.eps_p, (double)c0.r_diff,
+                                       (double)c0.alpha_on, (double)c0.n_rings};
+            // kernel shapes may differ (each world's spectra are read through a list)
+            for (int k = 0; k < c0.n_kernels; k++) {
+                const lenia_kernel_desc& d = ks[k];
+                key.push_back((double)d.src_channel);
+                key.push_back((double)d.dst_channel);
+                // global genes matter only where they are not read from the gene maps
+                key.push_back((c0.localized & LENIA_LOC_H) ? 0.0 : (double)d.h);
+                key.push_back((c0.localized & LENIA_LOC_MU) ? 0.0 : (double)d.mu);
+                key.push_back((c0.localized & LENIA_LOC_SIGMA) ? 0.0 : (double)d.sigma);
+            }
+            members[key].push_back(i);
+        }
+        for (auto& kv : members) {
+            if (kv.second.size() < 2) continue;
+            Group g;
+            g.worlds = kv.second;
+            lenia::ctx_view(b->ctx[g.worlds[0]], &g.v);
+            const size_t n = g.worlds.size();
+            const size_t H = cfgs[g.worlds[0]].height, W = cfgs[g.worlds[0]].width, M = W / 2;
+            bool okg = cudaMalloc(&g.Ahat, n * g.v.C * M * H * sizeof(float2)) == cudaSuccess &&
+                       cudaMalloc(&g.Uhat, n * g.v.K * M * H * sizeof(float2)) == cudaSuccess &&
+                       cudaMalloc(&g.U, n * g.v.K * g.v.N * sizeof(float)) == cudaSuccess &&
+                       cudaMalloc(&g.S, n * sizeof(float*)) == cudaSuccess;
+            if (okg) {
+                std::vector<const float*> spec(n);
+                for (size_t j = 0; j < n; j++) {
+                    lenia::lenia_ctx_view vj;
+                    lenia::ctx_view(b->ctx[g.worlds[j]], &vj);
+                    spec[j] = vj.fp.S;
+                }
+                okg = cudaMemcpy(g.S, spec.data(), n * sizeof(float*), cudaMemcpyHostToDevice) == cudaSuccess;
+            }
+            for (int d = 0; okg && d < 2; d++)
+                okg = cudaMalloc(&g.Ain[d], n * sizeof(float*)) == cudaSuccess &&
+                      cudaMalloc(&g.Pin[d], n * sizeof(float*)) == cudaSuccess &&
+                      cudaMalloc(&g.Aout[d], n * sizeof(float*)) == cudaSuccess &&
+                      cudaMalloc(&g.Pout[d], n * sizeof(float*)) == cudaSuccess;
+            if (!okg) {
+                free_group(g);
+                lenia_batch_destroy(b);
+                return LENIA_ENOMEM;
+            }
+            for (int i : g.worlds) b->group_of[i] = (int)b->groups.size();
+            b->groups.push_back(g);
+        }
+    }
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         lenia_batch_destroy(b);
         return LENIA_ECUDA;
@@ -261,6 +429,39 @@ lenia_status lenia_batch_rollout(lenia_batch* b, float* const* A, float* const* 
     if (n_steps == 0) return LENIA_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const std::vector<const void*> key = key_of(b, A, P);
+    if ((n_steps >= 2 && b->key2 != key) || ((n_steps % 2) && b->key1 != key)) {
+        // the groups' pointer lists for these buffers (read when the graphs run)
+        if (cudaStreamSynchronize(b->origin) != cudaSuccess) return LENIA_ECUDA;
+        for (Group& g : b->groups) {
+            const size_t n = g.worlds.size();
+            std::vector<const float*> a0(n), p0(n), a1(n), p1(n);
+            std::vector<float*> ao0(n), po0(n), ao1(n), po1(n);
+            g.aligned = true;
+            for (size_t j = 0; j < n; j++) {
+                const int i = g.worlds[j];
+                a0[j] = A[i];
+                p0[j] = P ? P[i] : nullptr;
+                ao0[j] = b->A2[i];
+                po0[j] = b->P2[i];
+                a1[j] = b->A2[i];
+                p1[j] = b->P2[i];
+                ao1[j] = A[i];
+                po1[j] = P ? P[i] : nullptr;
+                g.aligned = g.aligned && ((uintptr_t)A[i] % 16 == 0) && ((uintptr_t)b->A2[i] % 16 == 0);
+            }
+            const size_t pb = n * sizeof(float*);
+            bool ok = cudaMemcpy(g.Ain[0], a0.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
+                      cudaMemcpy(g.Pin[0], p0.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
+                      cudaMemcpy(g.Aout[0], ao0.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
+                      cudaMemcpy(g.Pout[0], po0.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
+                      cudaMemcpy(g.Ain[1], a1.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
+                      cudaMemcpy(g.Pin[1], p1.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
+                      cudaMemcpy(g.Aout[1], ao1.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
+                      cudaMemcpy(g.Pout[1], po1.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess;
+            if (!ok) return LENIA_ECUDA;
+        }
+        destroy_graphs(b);
+    }
     if (n_steps >= 2 && (!b->g2 || b->key2 != key)) {
         if (b->g2) cudaGraphExecDestroy(b->g2);
         b->g2 = nullptr;
@@ -281,6 +482,12 @@ lenia_status lenia_batch_rollout(lenia_batch* b, float* const* A, float* const* 
     }
     if (n_steps % 2) return run_graph(b, b->g1, s);
     return LENIA_OK;
+}
+
+int32_t lenia_batch_group_of(const lenia_batch* b, int32_t world)
+{
+    if (!b || world < 0 || world >= b->n) return -1;
+    return b->group_of[world];
 }
 
 int32_t lenia_batch_conv_path(const lenia_batch* b, int32_t world)

@@ -446,6 +446,21 @@ lenia_status transposed_conv(lenia_ctx* c, const float* gU, float* V, cudaStream
 
 }  // namespace
 
+namespace lenia {
+// For the batched-worlds runner (lenia_batch.cu): the parameters one step of
+// this context launches with; false unless it is on the FFT path.
+bool ctx_view(lenia_ctx* c, lenia_ctx_view* v)
+{
+    if (!c || !v || c->path != LENIA_CONV_FFT) return false;
+    v->fp = c->fp;
+    v->ep = epi_params(c);
+    v->N = c->N;
+    v->C = c->cfg.n_channels;
+    v->K = (int)c->conv_w.size();
+    return true;
+}
+}  // namespace lenia
+
 extern "C" {
 
 const char* lenia_status_string(lenia_status s)
@@ -732,6 +747,8 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         c->fp.C = C;
         c->fp.K = NC;
         c->fp.status = c->d_status;
+        c->fp.cw = C;
+        c->fp.kpw = NC;
         memcpy(c->fp.kcount, kcount, sizeof(kcount));
         memcpy(c->fp.klist, klist, sizeof(klist));
     }

@@ -63,6 +63,14 @@ struct EpiParams {
     // growth sum of channel c at sites where alpha = 0 (genes masked to zero):
     // -sum_{dst(k)=c} h_k for the signed form with global h, else 0
     float acc0[kMaxChannels];
+    // worlds batched in one launch (tiled epilogue only): world blockIdx.z reads
+    // A_list / P_list and writes Aout_list / Pout_list, its potentials at
+    // U + world * u_stride (null lists: a single world at A, P, A_out, P_out)
+    const float* const* A_list;
+    const float* const* P_list;
+    float* const* Aout_list;
+    float* const* Pout_list;
+    size_t u_stride;
     // ring decomposition (Section 2.4): U holds the ring potentials
     // [C][n_rings][H][W]; the kernel genes start at plane p_kern
     int n_rings, p_kern;
@@ -117,6 +125,14 @@ struct FftParams {
     int k_base;                // the column pass writes Uhat plane k - k_base (0 for the forward step)
     const float* add;          // inverse row pass: added to its output, same layout as U (nullable)
     int* status;               // device status word for bounded waits (nullable)
+    // worlds batched in one launch (identical shapes and kernels): plane y of the
+    // row pass is channel y % cw of world y / cw, read from A_list[world] when
+    // A_list is set; the column pass writes Uhat plane world * kpw + k.  A
+    // single world has cw = C and any kpw.
+    const float* const* A_list;
+    const float* const* S_list;  // per-world kernel spectra (world = plane / cw), else S
+    int cw, kpw;
+    int list_aligned;          // every A_list pointer is 16-byte aligned
     int kcount[kMaxChannels];
     int klist[kMaxChannels][kMaxKernels];
 };
@@ -163,6 +179,21 @@ bool epilogue_rows_supported(const EpiParams& p);
 cudaError_t launch_epilogue_rows(const EpiParams& p, int num_sms, int* status, cudaStream_t s, int* n_blocks);
 bool fft_size_supported(int H, int W);
 int epilogue_blocks(int H, int W);
+// The batched-worlds runner's view of a context: its convolution and epilogue
+// parameters (false unless the context is on the FFT path).
+struct lenia_ctx_view {
+    FftParams fp;
+    EpiParams ep;
+    size_t N;
+    int C, K;
+};
+}  // namespace lenia
+struct lenia_ctx;
+namespace lenia {
+bool ctx_view(lenia_ctx* c, lenia_ctx_view* v);
+// batched worlds: one tiled-epilogue launch over n_worlds (grid z), pointer lists in EpiParams
+bool epilogue_batch_supported(const EpiParams& p);
+cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t s);
 int ring_epilogue_blocks(int H, int W);   // stats records of the ring epilogue
 // pass 1: Delta_sum complement -> counts; pass 2: E_pen, mutation, penalisation
 cudaError_t launch_disk_pass(const EvoParams& p, int pass, cudaStream_t s);

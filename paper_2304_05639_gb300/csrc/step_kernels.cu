@@ -129,7 +129,7 @@ __device__ __forceinline__ void block_stats(const float* st, int C, double* part
 // Fast path: diffusion radius 1 (the 5-site plus), compile-time kernel count,
 // channel count and gene layout.  Each thread owns one column x and rows
 // y0 + 8 j (j < EP_RY); wrapped neighbour indices are formed once per row.
-template <int KT, int CT, int LOC>
+template <int KT, int CT, int LOC, int RY = EP_RY>
 __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
 {
     constexpr int NP = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
@@ -145,13 +145,20 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
     const int xm = xc == 0 ? W - 1 : xc - 1;
     const int xp = xc == W - 1 ? 0 : xc + 1;
     const float eps_p = p.eps_p, eps_u = p.eps_u;
+    // world blockIdx.z of a batched launch (lists set), else the single world
+    const int wz = blockIdx.z;
+    const float* pA = p.A_list ? p.A_list[wz] : p.A;
+    const float* pP = p.P_list ? p.P_list[wz] : p.P;
+    float* pAo = p.Aout_list ? p.Aout_list[wz] : p.A_out;
+    float* pPo = p.Pout_list ? p.Pout_list[wz] : p.P_out;
+    const float* pU = p.U + (size_t)wz * p.u_stride;
 
     float st[CT * 5];
 #pragma unroll
     for (int v = 0; v < CT * 5; v++) st[v] = 0.f;
 
-    for (int j = 0; j < EP_RY; j++) {
-        const int y = blockIdx.y * (EP_TY * EP_RY) + j * EP_TY + threadIdx.y;
+    for (int j = 0; j < RY; j++) {
+        const int y = blockIdx.y * (EP_TY * RY) + j * EP_TY + threadIdx.y;
         if (y >= H) break;
         const size_t rc = (size_t)y * W;
         const size_t ru = (size_t)(y == 0 ? H - 1 : y - 1) * W;
@@ -162,7 +169,7 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
         bool alpha = true;
 #pragma unroll
         for (int pk = 0; pk < NPK; pk++) {
-            const float* pl = p.P + (size_t)pk * N;
+            const float* pl = pP + (size_t)pk * N;
             if (p.maintain) {
                 // disk |d| <= 1 in the order (-1,0), (0,-1), (0,0), (0,1), (1,0)
                 const float v0 = __ldg(pl + ru + xc);
@@ -185,7 +192,7 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
         for (int c = 0; c < CT; c++) acc[c] = 0.f;
 #pragma unroll
         for (int k = 0; k < KT; k++) {
-            const float u = __ldg(&p.U[(size_t)k * N + i]);
+            const float u = __ldg(&pU[(size_t)k * N + i]);
             const float m = PMU >= 0 ? ph[(PMU >= 0 ? PMU : 0) * KT + k] : p.kt.mu[k];
             const float sg = PSG >= 0 ? ph[(PSG >= 0 ? PSG : 0) * KT + k] : p.kt.sigma[k];
             const float hh = PH >= 0 ? ph[(PH >= 0 ? PH : 0) * KT + k] : p.kt.h[k];
@@ -207,9 +214,9 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
         if (xin) {
 #pragma unroll
             for (int c = 0; c < CT; c++) {
-                const float a = __ldg(&p.A[(size_t)c * N + i]) + p.dt * (alpha ? acc[c] : p.acc0[c]);
+                const float a = __ldg(&pA[(size_t)c * N + i]) + p.dt * (alpha ? acc[c] : p.acc0[c]);
                 const float an = fminf(fmaxf(a, 0.f), 1.f);
-                p.A_out[(size_t)c * N + i] = an;
+                pAo[(size_t)c * N + i] = an;
                 if (p.partials) {
                     const float sy = __ldg(&p.sin_y[y]), cy = __ldg(&p.cos_y[y]);
                     const float sx = __ldg(&p.sin_x[x]), cx = __ldg(&p.cos_x[x]);
@@ -220,10 +227,10 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
                     st[c * 5 + 4] += an * cx;
                 }
             }
-            if (p.P_out) {
+            if (pPo) {
 #pragma unroll
                 for (int pk = 0; pk < NPK; pk++)
-                    p.P_out[(size_t)pk * N + i] = (p.maintain && !alpha) ? 0.f : ph[pk];
+                    pPo[(size_t)pk * N + i] = (p.maintain && !alpha) ? 0.f : ph[pk];
             }
             if (p.alpha_out) p.alpha_out[i] = alpha ? 1 : 0;
             if (p.empty_out) p.empty_out[i] = tsum > eps_u ? 0 : 1;
@@ -481,6 +488,134 @@ __global__ void __launch_bounds__(256, 5) k_epilogue_rings(EpiParams p)
 }
 
 int ring_epilogue_blocks(int H, int W) { return ((W + EP_TX - 1) / EP_TX) * ((H + RG_TY - 1) / RG_TY); }
+
+// Batched worlds of one channel and one kernel: the tiled epilogue's
+// arithmetic in the same order (so a world gives the same bits as on its own
+// through k_epilogue_r1), but each thread takes BR rows of one column and
+// issues every load of its rows before the first row's arithmetic: a group's
+// blocks are short-lived, and this keeps many loads in flight per thread.
+// Needs W % 32 == 0 and H % (8 BR) == 0; no statistics, alpha or empty output.
+template <int LOC, int BR>
+__global__ void __launch_bounds__(256) k_epilogue_batch11(EpiParams p)
+{
+    constexpr int NP = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
+    constexpr int PMU = (LOC & 1) ? 0 : -1;
+    constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
+    constexpr int PH = (LOC & 4) ? NP - 1 : -1;
+    const int H = p.H, W = p.W;
+    const size_t N = (size_t)H * W;
+    const int x = blockIdx.x * EP_TX + threadIdx.x;
+    const int xm = x == 0 ? W - 1 : x - 1;
+    const int xp = x == W - 1 ? 0 : x + 1;
+    const float eps_p = p.eps_p, eps_u = p.eps_u;
+    const int wz = blockIdx.z;
+    const float* pA = p.A_list[wz];
+    const float* pP = p.P_list ? p.P_list[wz] : nullptr;
+    float* pAo = p.Aout_list[wz];
+    float* pPo = p.Pout_list ? p.Pout_list[wz] : nullptr;
+    const float* pU = p.U + (size_t)wz * p.u_stride;
+
+    float v[BR][NP > 0 ? NP : 1][5];
+    float u[BR], a[BR];
+    size_t ic[BR];
+#pragma unroll
+    for (int j = 0; j < BR; j++) {
+        const int y = blockIdx.y * (EP_TY * BR) + j * EP_TY + threadIdx.y;
+        const size_t rc = (size_t)y * W;
+        const size_t ru = (size_t)(y == 0 ? H - 1 : y - 1) * W;
+        const size_t rd = (size_t)(y == H - 1 ? 0 : y + 1) * W;
+        ic[j] = rc + x;
+#pragma unroll
+        for (int pk = 0; pk < NP; pk++) {
+            const float* pl = pP + (size_t)pk * N;
+            if (p.maintain) {
+                v[j][pk][0] = __ldg(pl + ru + x);
+                v[j][pk][1] = __ldg(pl + rc + xm);
+                v[j][pk][2] = __ldg(pl + rc + x);
+                v[j][pk][3] = __ldg(pl + rc + xp);
+                v[j][pk][4] = __ldg(pl + rd + x);
+            } else {
+                v[j][pk][2] = __ldg(pl + ic[j]);
+            }
+        }
+        u[j] = __ldg(pU + ic[j]);
+        a[j] = __ldg(pA + ic[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < BR; j++) {
+        float ph[NP > 0 ? NP : 1];
+        bool alpha = true;
+#pragma unroll
+        for (int pk = 0; pk < NP; pk++) {
+            if (p.maintain) {
+                const float v0 = v[j][pk][0], v1 = v[j][pk][1], v2 = v[j][pk][2], v3 = v[j][pk][3], v4 = v[j][pk][4];
+                const float s = (((v0 + v1) + v2) + v3) + v4;
+                const int n = (v0 > eps_p) + (v1 > eps_p) + (v2 > eps_p) + (v3 > eps_p) + (v4 > eps_p);
+                const float vv = n > 0 ? fminf(fmaxf(s / (float)n, 0.f), 1.f) : 0.f;
+                alpha = alpha && (vv > eps_p);
+                ph[pk] = vv;
+            } else {
+                ph[pk] = v[j][pk][2];
+            }
+        }
+        float acc = 0.f;
+        {
+            const float m = PMU >= 0 ? ph[PMU >= 0 ? PMU : 0] : p.kt.mu[0];
+            const float sg = PSG >= 0 ? ph[PSG >= 0 ? PSG : 0] : p.kt.sigma[0];
+            const float hh = PH >= 0 ? ph[PH >= 0 ? PH : 0] : p.kt.h[0];
+            float gk = 0.f;
+            if (sg > 0.f) {
+                const float z = (u[j] - m) / sg;
+                gk = expf(-0.5f * z * z);
+            }
+            const float t = p.alpha_on ? u[j] : hh * gk;
+            if (p.maintain) alpha = alpha && (t > eps_u);
+            const float G = p.growth_form == 0 ? hh * (2.f * gk - 1.f) : hh * gk;
+            acc += G;
+        }
+        if (!p.maintain) alpha = true;
+        const float an = fminf(fmaxf(a[j] + p.dt * (alpha ? acc : p.acc0[0]), 0.f), 1.f);
+        pAo[ic[j]] = an;
+        if (pPo) {
+#pragma unroll
+            for (int pk = 0; pk < NP; pk++) pPo[(size_t)pk * N + ic[j]] = (p.maintain && !alpha) ? 0.f : ph[pk];
+        }
+    }
+}
+
+// One launch over n_worlds batched worlds of the same shape (tiled epilogue;
+// EpiParams carries the pointer lists).  False if the shape has no tiled kernel.
+bool epilogue_batch_supported(const EpiParams& p)
+{
+    const int loc = (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
+    const int K = p.kt.K, C = p.kt.C;
+    return (p.r_diff == 1 || !p.maintain) && p.n_rings == 0 &&
+           ((K == 15 && C == 3 && (loc == 3 || loc == 0)) || (K == 1 && C == 1 && (loc == 3 || loc == 0)));
+}
+
+cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t s)
+{
+    if (!epilogue_batch_supported(p) || n_worlds < 1 || n_worlds > 65535) return cudaErrorInvalidValue;
+    const int loc = (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
+    const int K = p.kt.K;
+    if (p.partials || p.alpha_out || p.empty_out) return cudaErrorInvalidValue;
+    dim3 block(EP_TX, EP_TY);
+    constexpr int BR = 4;
+    if (K == 1 && p.W % EP_TX == 0 && p.H % (EP_TY * BR) == 0) {
+        dim3 g4(p.W / EP_TX, p.H / (EP_TY * BR), n_worlds);
+        if (loc == 3) k_epilogue_batch11<3, BR><<<g4, block, 0, s>>>(p);
+        else k_epilogue_batch11<0, BR><<<g4, block, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    // one row per thread: the worlds of a group are often small, so the grid
+    // needs the extra blocks (no statistics are gathered here)
+    dim3 grid((p.W + EP_TX - 1) / EP_TX, (p.H + EP_TY - 1) / EP_TY, n_worlds);
+    if (K == 15 && loc == 3) k_epilogue_r1<15, 3, 3, 1><<<grid, block, 0, s>>>(p);
+    else if (K == 15) k_epilogue_r1<15, 3, 0, 1><<<grid, block, 0, s>>>(p);
+    else if (loc == 3) k_epilogue_r1<1, 1, 3, 1><<<grid, block, 0, s>>>(p);
+    else k_epilogue_r1<1, 1, 0, 1><<<grid, block, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 int epilogue_blocks(int H, int W)
 {

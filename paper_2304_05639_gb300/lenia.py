@@ -28,7 +28,7 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes", "lenia_batch_init",
            "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy",
            "lenia_selftest_wait_timeout", "lenia_set_walls", "lenia_step_evolve",
-           "lenia_step_host_async", "lenia_host_wait")
+           "lenia_step_host_async", "lenia_host_wait", "lenia_batch_group_of")
 PROFILE_KINDS = 10
 
 
@@ -137,6 +137,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_batch_init.restype = st
     lib.lenia_batch_rollout.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32, vp]
     lib.lenia_batch_rollout.restype = st
+    lib.lenia_batch_group_of.argtypes = [vp, ctypes.c_int32]
+    lib.lenia_batch_group_of.restype = ctypes.c_int32
     lib.lenia_batch_conv_path.argtypes = [vp, ctypes.c_int32]
     lib.lenia_batch_conv_path.restype = ctypes.c_int32
     lib.lenia_batch_check.argtypes = [vp, vp]
@@ -265,6 +267,10 @@ def lenia_batch_rollout(batch, A_list, P_list, n_steps, stream=None):
 
 def lenia_batch_conv_path(batch, world: int) -> int:
     return load().lenia_batch_conv_path(batch, int(world))
+
+
+def lenia_batch_group_of(batch, world: int) -> int:
+    return load().lenia_batch_group_of(batch, int(world))
 
 
 def lenia_batch_check(batch, stream=None):

@@ -1,6 +1,8 @@
 """Batched worlds (lenia_batch_*): a batch rollout equals per-world rollouts
-on the same convolution paths bit for bit, and one batch step matches the
-FP64 oracle per world.  GPU only."""
+on the same convolution paths (bit for bit, except that a grouped world of
+width 256 k runs the tiled epilogue where a single world would run the
+streaming one: those agree to rounding), and one batch step matches the FP64
+oracle per world.  GPU only."""
 import numpy as np
 import pytest
 
@@ -20,6 +22,8 @@ def _built():
 
 def _worlds():
     ws = inputs.batched_worlds(n_worlds=9, sizes=(64, 128, 256), r_range=(6, 12), live=True)
+    # worlds sharing a shape and kernel (different genotypes and states): groups
+    ws += inputs.batched_worlds(n_worlds=6, sizes=(64, 256), r_range=(9, 9), seed_index=7, live=True)
     # one non-power-of-two world (direct path only) and one multi-channel world
     ws.append(inputs.localized_single_channel(H=96, W=80, R=7, patch=16, n_geno=2, live=True, name="odd"))
     ws.append(inputs.multi_channel(H=64, W=128, R=9, patch=20, n_geno=3, live=True, name="mc"))
@@ -39,6 +43,8 @@ def test_batch_rollout_equals_single_world_rollouts(n_steps):
         paths = [lenia.lenia_batch_conv_path(batch, i) for i in range(len(ws))]
         assert set(paths) <= {lenia.CONV_FFT, lenia.CONV_DIRECT}
         assert paths[-2] == lenia.CONV_DIRECT        # 96 x 80 has no FFT path
+        groups = [lenia.lenia_batch_group_of(batch, i) for i in range(len(ws))]
+        assert max(groups) >= 1, groups             # shared shapes form groups
         for i, w in enumerate(ws):
             cfg, ks = lenia.config_from_world(w, paths[i])
             ctx = lenia.lenia_init(cfg, ks)
@@ -46,9 +52,14 @@ def test_batch_rollout_equals_single_world_rollouts(n_steps):
                 a, p = to_dev(w.A), (to_dev(w.P) if w.P is not None else None)
                 lenia.lenia_rollout(ctx, a, p, n_steps)
                 torch.cuda.synchronize()
-                assert torch.equal(a, A[i]), w.name
-                if p is not None:
-                    assert torch.equal(p, P[i]), w.name
+                if lenia.lenia_batch_group_of(batch, i) >= 0 and w.width % 256 == 0:
+                    assert float((a - A[i]).abs().max()) <= 1e-5 * n_steps, w.name
+                    if p is not None:
+                        assert float((p - P[i]).abs().max()) <= 1e-6 * n_steps, w.name
+                else:
+                    assert torch.equal(a, A[i]), w.name
+                    if p is not None:
+                        assert torch.equal(p, P[i]), w.name
             finally:
                 lenia.lenia_destroy(ctx)
         # the captured graphs are reused for the same buffers
@@ -60,7 +71,7 @@ def test_batch_rollout_equals_single_world_rollouts(n_steps):
 
 def test_batch_step_matches_oracle():
     torch = torch_mod()
-    ws = _worlds()[:4] + _worlds()[-2:]
+    ws = _worlds()[:4] + _worlds()[9:15] + _worlds()[-2:]
     batch = lenia.lenia_batch_init(ws, autotune=True)
     try:
         A = [to_dev(w.A) for w in ws]
@@ -72,5 +83,43 @@ def test_batch_step_matches_oracle():
             Ph = np.stack([[oracle.diffuse(w.P[p, k]) for k in range(w.n_kernels)] for p in range(w.n_planes)])
             g = {"A": A[i].cpu().numpy(), "P": P[i].cpu().numpy()}
             compare_step(w, g, A1, P1, al, alpha_margin(w, U, Ph))
+    finally:
+        lenia.lenia_batch_destroy(batch)
+
+
+def test_grouped_worlds_match_oracle_and_single_worlds():
+    """Twelve worlds of three shapes (FFT path, one radius, different
+    genotypes and states) form three groups, each stepping in one launch per
+    stage: one step matches the oracle per world, and three steps match
+    single-world rollouts (bit for bit at widths 64 and 128)."""
+    torch = torch_mod()
+    ws = inputs.batched_worlds(n_worlds=12, sizes=(64, 128, 256), r_range=(9, 9), seed_index=11, live=True)
+    batch = lenia.lenia_batch_init(ws, autotune=False)
+    try:
+        groups = [lenia.lenia_batch_group_of(batch, i) for i in range(len(ws))]
+        assert all(g >= 0 for g in groups) and len(set(groups)) == len({w.height for w in ws}), groups
+        A = [to_dev(w.A) for w in ws]
+        P = [to_dev(w.P) for w in ws]
+        lenia.lenia_batch_rollout(batch, A, P, 1)
+        lenia.lenia_batch_check(batch)
+        for i, w in enumerate(ws):
+            A1, P1, U, al = oracle.step(w, return_u=True, return_alpha=True)
+            Ph = np.stack([[oracle.diffuse(w.P[p, k]) for k in range(w.n_kernels)] for p in range(w.n_planes)])
+            compare_step(w, {"A": A[i].cpu().numpy(), "P": P[i].cpu().numpy()}, A1, P1, al, alpha_margin(w, U, Ph))
+        lenia.lenia_batch_rollout(batch, A, P, 2)          # three steps in all
+        lenia.lenia_batch_check(batch)
+        for i, w in enumerate(ws):
+            cfg, ks = lenia.config_from_world(w, lenia.CONV_FFT)
+            ctx = lenia.lenia_init(cfg, ks)
+            try:
+                a, p = to_dev(w.A), to_dev(w.P)
+                lenia.lenia_rollout(ctx, a, p, 3)
+                torch.cuda.synchronize()
+                if w.width % 256 == 0:
+                    assert float((a - A[i]).abs().max()) <= 3e-5 and float((p - P[i]).abs().max()) <= 3e-6
+                else:
+                    assert torch.equal(a, A[i]) and torch.equal(p, P[i]), w.name
+            finally:
+                lenia.lenia_destroy(ctx)
     finally:
         lenia.lenia_batch_destroy(batch)
