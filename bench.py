@@ -117,42 +117,51 @@ def workload_config(ws, conv_path, size=2048):
 
 def adjoint_leg(torch, lenia, inputs, stream):
     """Forward rollout vs rollout adjoint: 256^2, 3 channels, 15 kernels R=13,
-    global genes, 64 steps, checkpoints every 8."""
+    global genes, 64 steps, checkpoints every 8; and the same with every state
+    kept (checkpoint every step: the reverse pass recomputes nothing)."""
     w = inputs.global_multi_channel()
-    n, ck = 64, 8
-    cfg, ks = lenia.config_from_world(w, lenia.CONV_AUTO, max_rollout_steps=n, ckpt_every=ck)
-    ctx = lenia.lenia_init(cfg, ks, stream)
-    try:
-        A0 = torch.from_numpy(w.A).cuda()
-        A = A0.clone()
-        gA_T = torch.ones_like(A0)
-        gA0 = torch.empty_like(A0)
-        gg = torch.empty((w.n_kernels, 3), dtype=torch.float32, device="cuda")
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        for _ in range(2):                                   # warm-up
-            A.copy_(A0)
-            lenia.lenia_rollout(ctx, A, None, n, None, stream)
-            lenia.lenia_backward(ctx, A0, None, n, gA_T, gA0, gg, stream)
-        reps = 5
-        torch.cuda.synchronize()
-        ev[0].record(stream)
-        for _ in range(reps):
-            A.copy_(A0)
-            lenia.lenia_rollout(ctx, A, None, n, None, stream)
-        ev[1].record(stream)
-        for _ in range(reps):
-            lenia.lenia_backward(ctx, A0, None, n, gA_T, gA0, gg, stream)
-        ev[2].record(stream)
-        torch.cuda.synchronize()
-        lenia.lenia_check(ctx)
-        fwd = ev[0].elapsed_time(ev[1]) / reps
-        bwd = ev[1].elapsed_time(ev[2]) / reps
-        return {"workload": "256x256, 3 channels, 15 kernels R=13, global genes, 64 steps, checkpoint every 8",
-                "fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_over_fwd": (fwd + bwd) / fwd,
-                "conv_path": "fft" if lenia.lenia_conv_path(ctx) == lenia.CONV_FFT else "direct",
-                "note": "bwd recomputes the forward from checkpoints inside lenia_backward"}
-    finally:
-        lenia.lenia_destroy(ctx)
+    n = 64
+    out = {"workload": "256x256, 3 channels, 15 kernels R=13, global genes, 64 steps, checkpoint every 8"}
+    for ck in (8, 1):
+        cfg, ks = lenia.config_from_world(w, lenia.CONV_AUTO, max_rollout_steps=n, ckpt_every=ck)
+        ctx = lenia.lenia_init(cfg, ks, stream)
+        try:
+            A0 = torch.from_numpy(w.A).cuda()
+            A = A0.clone()
+            gA_T = torch.ones_like(A0)
+            gA0 = torch.empty_like(A0)
+            gg = torch.empty((w.n_kernels, 3), dtype=torch.float32, device="cuda")
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            for _ in range(2):                                   # warm-up
+                A.copy_(A0)
+                lenia.lenia_rollout(ctx, A, None, n, None, stream)
+                lenia.lenia_backward(ctx, A0, None, n, gA_T, gA0, gg, stream)
+            reps = 5
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for _ in range(reps):
+                A.copy_(A0)
+                lenia.lenia_rollout(ctx, A, None, n, None, stream)
+            ev[1].record(stream)
+            for _ in range(reps):
+                lenia.lenia_backward(ctx, A0, None, n, gA_T, gA0, gg, stream)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            lenia.lenia_check(ctx)
+            fwd = ev[0].elapsed_time(ev[1]) / reps
+            bwd = ev[1].elapsed_time(ev[2]) / reps
+            path = "fft" if lenia.lenia_conv_path(ctx) == lenia.CONV_FFT else "direct"
+        finally:
+            lenia.lenia_destroy(ctx)
+        if ck == 8:
+            out.update({"fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_over_fwd": (fwd + bwd) / fwd,
+                        "conv_path": path,
+                        "note": "bwd recomputes the forward from checkpoints inside lenia_backward"})
+        else:
+            out["every_state_kept"] = {"fwd_ms": fwd, "bwd_ms": bwd, "fwd_plus_bwd_over_fwd": (fwd + bwd) / fwd,
+                                       "note": "checkpoint every step: the forward pass inside lenia_backward "
+                                               "keeps states and potentials, the reverse pass recomputes nothing"}
+    return out
 
 
 def batched_leg(torch, lenia, inputs, stream, steps=200):

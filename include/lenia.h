@@ -103,7 +103,9 @@ typedef struct {
  *   r_diff: radius of the diffusion disk |d|_2 <= r_diff, 0..8.
  *   conv_path: LENIA_CONV_* (AUTO picks FFT for power-of-two worlds).
  *   max_rollout_steps, ckpt_every: adjoint buffers for lenia_backward (0 = none;
- *     global genes only); states kept every ckpt_every steps (0 -> 8).
+ *     global genes only); states kept every ckpt_every steps (0 -> 8); with
+ *     ckpt_every = 1 every state and every step's potentials are kept
+ *     (max_rollout_steps x (C + K) planes) and nothing is recomputed.
  *   n_rings: with LENIA_LOC_KERNEL, the ring decomposition of Section 2.4
  *     (0 otherwise): every kernel has the same radius R; ring r holds the
  *     offsets with r <= n_rings |d|_2 / R < r + 1 and |d|_2 < R; at each site

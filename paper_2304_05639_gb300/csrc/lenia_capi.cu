@@ -761,7 +761,9 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         const size_t nA1 = c->N * C;
         ALLOC(c->d_ckpt, (size_t)n_ckpt * nA1);
         ALLOC(c->d_seg, (size_t)std::max(c->ckpt, 2) * nA1);
-        ALLOC(c->d_Useg, (size_t)c->ckpt * K * c->N);
+        // every state kept (ckpt_every = 1): the forward pass also keeps every
+        // step's potentials, so the reverse pass recomputes nothing
+        ALLOC(c->d_Useg, (size_t)(c->ckpt == 1 ? c->max_steps : c->ckpt) * K * c->N);
         ALLOC(c->d_adj_ticket, 1);
         CK_INIT(cudaMemset(c->d_adj_ticket, 0, sizeof(unsigned int)));
         ALLOC(c->d_gA[0], nA1);
@@ -838,6 +840,47 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
     // forward pass, keeping the states at multiples of the checkpoint interval
     CUDA_OR_FAIL(c, cudaMemcpyAsync(ckpt(0), A0, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
     const float* prev = ckpt(0);
+    if (L == 1) {
+        // every state and every step's potentials kept: reverse directly
+        auto uall = [&](int t) { return c->d_Useg + (size_t)t * K * c->N; };
+        for (int t = 0; t < n_steps; t++) {
+            lenia_status st = potentials(c, ckpt(t), uall(t), s);
+            if (st == LENIA_OK && t + 1 < n_steps)
+                st = step_impl(c, ckpt(t), nullptr, ckpt(t + 1), nullptr, nullptr, nullptr, uall(t), s);
+            if (st != LENIA_OK) return st;
+        }
+        CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_gene_acc, 0, (size_t)K * 3 * sizeof(double), s));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_gA[0], gA_T, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        int cur = 0;
+        for (int t = n_steps - 1; t >= 0; t--) {
+            AdjParams ap;
+            memset(&ap, 0, sizeof(ap));
+            ap.A = ckpt(t);
+            ap.U = uall(t);
+            ap.gA_next = c->d_gA[cur];
+            ap.gpre = c->d_gpre;
+            ap.gU = c->d_gU;
+            ap.V = c->d_V;
+            ap.gA_out = c->d_gA[cur ^ 1];
+            ap.gene_partials = c->d_gene_part;
+            ap.gene_acc = c->d_gene_acc;
+            ap.ticket = c->d_adj_ticket;
+            ap.H = c->cfg.height;
+            ap.W = c->cfg.width;
+            ap.growth_form = c->cfg.growth_form;
+            ap.dt = c->cfg.dt;
+            ap.kt = c->kt;
+            CUDA_OR_FAIL(c, launch_adjoint_epilogue(ap, s));
+            bool per_channel = false;
+            lenia_status st = transposed_conv(c, c->d_gU, c->d_V, s, &per_channel, c->d_gpre, c->d_gA[cur ^ 1]);
+            if (st != LENIA_OK) return st;
+            if (!per_channel) CUDA_OR_FAIL(c, launch_adjoint_gather(ap, s));
+            cur ^= 1;
+        }
+        if (gA0) CUDA_OR_FAIL(c, cudaMemcpyAsync(gA0, c->d_gA[cur], nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        if (g_genes) CUDA_OR_FAIL(c, launch_adjoint_gene_out(c->d_gene_acc, K * 3, g_genes, s));
+        return LENIA_OK;
+    }
     for (int t = 0; t + 1 < n_steps; t++) {
         float* dst = ((t + 1) % L == 0) ? ckpt((t + 1) / L) : seg((t + 1) & 1);
         lenia_status st = step_impl(c, prev, nullptr, dst, nullptr, nullptr, nullptr, nullptr, s);

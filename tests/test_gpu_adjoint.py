@@ -77,7 +77,7 @@ def _close(got, ref, name):
     assert err <= REL * scale, (name, got, ref)
 
 
-@pytest.mark.parametrize("path,n,ckpt", [(1, 6, 4), (2, 6, 4), (1, 5, 8)])
+@pytest.mark.parametrize("path,n,ckpt", [(1, 6, 4), (2, 6, 4), (1, 5, 8), (1, 6, 1), (2, 5, 1)])
 def test_backward_linear_loss_matches_fd(path, n, ckpt):
     torch = torch_mod()
     w = _world()
