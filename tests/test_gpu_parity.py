@@ -256,6 +256,38 @@ def test_rollout_10_steps_global_genes(name, path):
         lenia.lenia_destroy(ctx)
 
 
+@pytest.mark.parametrize("name,path", [("c2s", 1), ("c2s", 2), ("c2w", 2)])
+def test_rollout_30_steps_localized_statistics(name, path):
+    """Localized genes over 30 steps: alpha decisions near a threshold may go
+    either way in FP32 and FP64, so trajectories drift apart; compared are the
+    per-channel mass and circular-mean centre (the statistics the rollout
+    reports), whose gap is printed against the step and bounded."""
+    torch = torch_mod()
+    w = WORLDS[name]()
+    n = 30
+    _, _, st_ref = oracle.rollout(w, n)
+    cfg, ks = lenia.config_from_world(w, path)
+    ctx = lenia.lenia_init(cfg, ks)
+    try:
+        A, P = to_dev(w.A), to_dev(w.P)
+        st = torch.zeros((n, w.n_channels, 3), dtype=torch.float32, device="cuda")
+        lenia.lenia_rollout(ctx, A, P, n, st)
+        lenia.lenia_check(ctx)
+        g = st.cpu().numpy().astype(np.float64)
+    finally:
+        lenia.lenia_destroy(ctx)
+    mass_ref = np.maximum(st_ref[:, :, 0], 1.0)
+    rel_mass = np.abs(g[:, :, 0] - st_ref[:, :, 0]) / mass_ref
+    H, W = w.height, w.width
+    dy = np.abs((g[:, :, 1] - st_ref[:, :, 1] + H / 2) % H - H / 2)
+    dx = np.abs((g[:, :, 2] - st_ref[:, :, 2] + W / 2) % W - W / 2)
+    for t in (0, 4, 9, 19, 29):
+        print(f"{name} step {t + 1}: mass rel gap {rel_mass[t].max():.2e}, centre gap "
+              f"{max(dy[t].max(), dx[t].max()):.2e} px")
+    assert rel_mass[:10].max() <= 1e-4 and rel_mass.max() <= 1e-2, rel_mass.max(axis=1)
+    assert max(dy[:10].max(), dx[:10].max()) <= 1e-2 and max(dy.max(), dx.max()) <= 0.5
+
+
 def test_rollout_equals_repeated_steps_and_is_deterministic():
     torch = torch_mod()
     w = w_c3_small()
