@@ -17,7 +17,8 @@
  *
  * Conventions for every entry point:
  *   - Layout: A is float32 [C][H][W]; P is float32 [n_p][K][H][W] with the
- *     gene planes in the order mu, sigma, h (only the localized ones);
+ *     gene planes in the order mu, sigma, h (only the localized ones), then
+ *     the kernel genes r1, w1, b1, r2, w2, b2 with LENIA_LOC_KERNEL;
  *     U is float32 [K][H][W].  All contiguous, row-major, x fastest.
  *   - Pointers named *_in / *_out / A / P / U / stats_out are DEVICE pointers
  *     unless the entry point's name ends in _host.  The caller owns them.
@@ -26,8 +27,9 @@
  *     stream is synchronised.  A context is not thread-safe.
  *   - The library owns the context and all scratch memory (kernel spectra,
  *     FFT intermediates, potentials, stats partials), allocated in lenia_init
- *     and freed in lenia_destroy.  No entry point allocates device memory
- *     after lenia_init.
+ *     and freed in lenia_destroy.  After lenia_init only lenia_set_walls and
+ *     the first lenia_step_evolve allocate device memory (as documented
+ *     there); lenia_stats_noalloc allocates nothing at all.
  *   - Errors: every entry point returns a status; nothing aborts and nothing
  *     is thrown.  Arguments are validated before any launch; a CUDA error
  *     seen after a launch returns LENIA_ECUDA.  lenia_last_error() gives a
