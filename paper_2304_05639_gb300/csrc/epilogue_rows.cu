@@ -358,9 +358,7 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
 }
 
 // ------------------------------------------------------------ tensor maps
-namespace {
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -374,6 +372,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     });
     return fn;
 }
+
+namespace {
 
 struct MapKey {
     const void* base;
@@ -399,7 +399,7 @@ bool plane_map(CUtensorMap* out, const float* base, int W, int H, int planes, in
             *out = cache[i].second;
             return true;
         }
-    auto fn = encode_fn();
+    auto fn = tensor_map_encoder();
     if (!fn) return false;
     CUtensorMap m;
     const cuuint64_t dims[3] = {(cuuint64_t)W / 2, (cuuint64_t)H, (cuuint64_t)planes};

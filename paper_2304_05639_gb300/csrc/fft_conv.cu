@@ -14,9 +14,14 @@
 //               [kernel][kx][y].  Column 0 holds the packed DC and Nyquist
 //               columns (both real along y), which are separated, multiplied
 //               by their own spectra and re-packed in one step.
-//   rows_c2r  : inverse real row FFT of every kernel row -> U_k, NB rows per block.
+//   rows_c2r  : inverse real row FFT of every kernel row -> U_k, NB rows per
+//               block, staged from the column-major spectra by tiled TMA loads.
 // Forward and inverse transforms are unnormalised; 1/(H W) is folded into
 // the stored kernel spectra.
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "fft_core.cuh"
 #include "lenia_internal.cuh"
 #include "ptx_util.cuh"
@@ -98,57 +103,94 @@ __global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
     }
 }
 
-// ---------------------------------------------------------------- rows C2R
-template <int M, int T, int NB>
-__global__ void __launch_bounds__(T) k_rows_c2r(FftParams p)
+// Tensor map of a column-major spectrum stack [planes][M][H] of float2,
+// viewed as (H, M, planes) 8-byte elements, with boxes of box_y x box_x x 1.
+// Encoded maps are cached by argument (most recent first).
+static bool spectrum_map(CUtensorMap* out, const float2* base, int H, int M, int planes, int box_y, int box_x)
 {
-    extern __shared__ float2 sm[];
+    struct Key {
+        const void* base;
+        int H, M, planes, by, bx;
+        bool operator==(const Key& o) const
+        {
+            return base == o.base && H == o.H && M == o.M && planes == o.planes && by == o.by && bx == o.bx;
+        }
+    };
+    static std::mutex mu;
+    static std::vector<std::pair<Key, CUtensorMap>> cache;
+    const Key key{base, H, M, planes, box_y, box_x};
+    std::lock_guard<std::mutex> lock(mu);
+    for (size_t i = 0; i < cache.size(); i++)
+        if (cache[i].first == key) {
+            *out = cache[i].second;
+            return true;
+        }
+    auto fn = tensor_map_encoder();
+    if (!fn || ((uintptr_t)base & 15) != 0) return false;
+    CUtensorMap m;
+    const cuuint64_t dims[3] = {(cuuint64_t)H, (cuuint64_t)M, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)H * 8, (cuuint64_t)M * H * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)box_y, (cuuint32_t)box_x, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(base), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    cache.insert(cache.begin(), {key, m});
+    if (cache.size() > 64) cache.pop_back();
+    *out = m;
+    return true;
+}
+
+// ---------------------------------------------------------------- rows C2R
+// Tiled TMA loads stage the block's NB rows of a kernel's column-major
+// spectrum: boxes of NB rows x C2R_BOX columns, landing as [kx][b] in the
+// work buffer (128-byte aligned).  The first radix-32 pass reads X[q] and
+// X[M - q] from there, forms
+//   Z'[q] = (X[q] + conj X[M-q]) + i w_W^{-q} (X[q] - conj X[M-q])   (= 2 Z[q]),
+// and, after its barrier, writes the swizzled work layout over the staged
+// data.  Lanes take consecutive rows first, so each warp's staged reads
+// cover 256 contiguous bytes.
+constexpr int C2R_BOX = 256;                   // spectrum columns per TMA box (the box limit)
+
+template <int M, int T, int NB>
+__global__ void __launch_bounds__(T, (512 / T) < 8 ? (512 / T) : 8)
+    k_rows_c2r(FftParams p, const __grid_constant__ CUtensorMap tm_uhat)
+{
+    constexpr int R = fft_radix(M, ROW_RMAX);
+    static_assert(R == 32 || R == M, "first inverse row pass is radix 32");
+    constexpr int BX = M < C2R_BOX ? M : C2R_BOX;
+    extern __shared__ float4 sm4[];
+    __shared__ uint64_t bar;
+    float2* sm = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(sm4) +
+                                           ((128 - (smem_addr(sm4) & 127)) & 127));
     constexpr int SZ = row_pitch(M);
     const int k = blockIdx.y;
     const int y0 = blockIdx.x * NB;
     const int W = 2 * M;
-    const float2* in = p.Uhat + (size_t)k * M * p.H + y0;     // column-major [k][kx][y]
 
-    // Z'[k] = (X[k] + conj X[M-k]) + i w_W^{-k} (X[k] - conj X[M-k])  (= 2 Z[k])
-    // All of a thread's input pairs are loaded before any is combined.
-    constexpr int PAIRS = NB * (M / 2 + 1);
-    constexpr int PER = (PAIRS + T - 1) / T;
-    float2 xk[PER], xm[PER];
-#pragma unroll
-    for (int it = 0; it < PER; it++) {
-        const int u = threadIdx.x + it * T;
-        if (u < PAIRS) {
-            const int b = u % NB, q = u / NB;
-            xk[it] = __ldg(&in[(size_t)q * p.H + b]);
-            xm[it] = __ldg(&in[(size_t)(q == 0 ? 0 : M - q) * p.H + b]);
-        }
-    }
-#pragma unroll
-    for (int it = 0; it < PER; it++) {
-        const int u = threadIdx.x + it * T;
-        if (u >= PAIRS) break;
-        const int b = u % NB, q = u / NB;
-        if (q == 0) {
-            const float2 x = xk[it];                          // (DC, Nyquist)
-            sm[b * SZ + swz32(0)] = make_float2(x.x + x.y, x.x - x.y);
-            continue;
-        }
-        {
-            float2 s = cadd(xk[it], cconj(xm[it]));
-            float2 d = cmulc(csub(xk[it], cconj(xm[it])), __ldg(&p.tw_W[q]));
-            sm[b * SZ + swz32(q)] = make_float2(s.x - d.y, s.y + d.x);   // s + i d
-        }
-        if (q != M - q) {
-            float2 s = cadd(xm[it], cconj(xk[it]));
-            float2 d = cmulc(csub(xm[it], cconj(xk[it])), __ldg(&p.tw_W[M - q]));
-            sm[b * SZ + swz32(M - q)] = make_float2(s.x - d.y, s.y + d.x);
-        }
+    constexpr uint32_t bytes = (uint32_t)NB * M * sizeof(float2);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, bytes);
+#pragma unroll
+        for (int i = 0; i < M / BX; i++) tma_load_3d(sm + (size_t)i * BX * NB, &tm_uhat, y0, i * BX, k, &bar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0));
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            if (p.status) atomicExch(p.status, kStatusWaitTimeout);
+            mbar_wait_bounded(&bar, 0);
+        }
+        return;
+    }
+
     float2* out = reinterpret_cast<float2*>(p.U + ((size_t)k * p.H + y0) * W);
     const float2* addp = p.add ? reinterpret_cast<const float2*>(p.add + ((size_t)k * p.H + y0) * W) : nullptr;
-    auto sld = [&](int b, int i) { return sm[b * SZ + swz32(i)]; };
-    auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz32(i)] = v; };
     auto st_g = [&](int b, int i, float2 v) {
         if (addp) {
             const float2 a = __ldg(&addp[(size_t)b * M + i]);
@@ -156,10 +198,58 @@ __global__ void __launch_bounds__(T) k_rows_c2r(FftParams p)
         }
         out[(size_t)b * M + i] = v;
     };
-    fft_run<M, NB, T, true, false, ROW_RMAX>(p.tw_M, sld, sld, sst, st_g);
+    auto sld = [&](int b, int i) { return sm[b * SZ + swz32(i)]; };
+    auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz32(i)] = v; };
+    auto stg = [&](int b, int q) { return sm[q * NB + b]; };      // staged element (row b, column q)
+
+    constexpr int JB = M / R;                        // butterflies per row
+    constexpr int NBF = NB * JB;
+    constexpr int PER = (NBF + T - 1) / T;
+    float2 v[PER][R];
+#pragma unroll
+    for (int it = 0; it < PER; it++) {
+        const int u = threadIdx.x + it * T;
+        if (NBF % T == 0 || u < NBF) {
+            const int b = u % NB, j = u / NB;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int q = j + r * JB;
+                const float2 xk = stg(b, q);
+                if (q == 0) {                                  // (DC, Nyquist)
+                    v[it][r] = make_float2(xk.x + xk.y, xk.x - xk.y);
+                } else {
+                    const float2 xm = stg(b, M - q);
+                    const float2 sp = cadd(xk, cconj(xm));
+                    const float2 d = cmulc(csub(xk, cconj(xm)), __ldg(&p.tw_W[q]));
+                    v[it][r] = make_float2(sp.x - d.y, sp.y + d.x);   // s + i d
+                }
+            }
+            DFT<R, true>::run(v[it]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < PER; it++) {
+        const int u = threadIdx.x + it * T;
+        if (NBF % T == 0 || u < NBF) {
+            const int b = u % NB, j = u / NB;
+#pragma unroll
+            for (int q = 0; q < R; q++) {
+                if constexpr (R == M) st_g(b, j * R + q, v[it][q]);
+                else sst(b, j * R + q, v[it][q]);
+            }
+        }
+    }
+    if constexpr (R < M) {
+        __syncthreads();
+        fft_run<M, NB, T, true, false, ROW_RMAX, R>(p.tw_M, sld, sld, sst, st_g);
+    }
 }
 
 // ------------------------------------------------------- columns: fwd, x K^, inv
+// The column transforms use packed FP32-pair butterflies (PK = true; 7%
+// faster on a 2048^2 world); the row transforms, whose radix-32 butterflies
+// are register-bound, run faster with scalar ones.
 // PERK: one block per (column, channel, kernel of that channel), grid z = the
 // longest kernel list: shorter serial chains for small grids, at the cost of
 // repeating the forward column transform for every kernel of a channel.
@@ -181,7 +271,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
     auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
     auto sldF = [&](int, int i) { return F[swz(i)]; };
     auto sstF = [&](int, int i, float2 v) { F[swz(i)] = v; };
-    fft_run<H, 1, T, false, false>(p.tw_H, ld_g, sldF, sstF, sstF);
+    fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
 
     const int t0 = PERK ? (int)blockIdx.z : 0;
     const int nk = PERK ? t0 + 1 : p.kcount[c];
@@ -207,7 +297,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
         auto sldW = [&](int, int i) { return Wk[swz(i)]; };
         auto sstW = [&](int, int i, float2 v) { Wk[swz(i)] = v; };
         auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
-        fft_run<H, 1, T, true, false>(p.tw_H, ld_mul, sldW, sstW, st_g);
+        fft_run<H, 1, T, true, false, 16, 1, true>(p.tw_H, ld_mul, sldW, sstW, st_g);
     }
 }
 
@@ -236,7 +326,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_adj(Fft
         const int k = p.klist[c][t];
         const float2* src = p.Ahat + ((size_t)k * M + kx) * H;
         auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
-        fft_run<H, 1, T, false, false>(p.tw_H, ld_g, sldF, sstF, sstF);
+        fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
         const float* Sk = p.S + (size_t)k * (M + 1) * HS;
         // each thread updates its own entries of Acc (no barrier needed between
         // the zeroing and the updates); F is complete after fft_run's barrier
@@ -260,7 +350,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_adj(Fft
     float2* dst = p.Uhat + ((size_t)c * M + kx) * H;
     auto ld_acc = [&](int, int i) { return Acc[swz(i)]; };
     auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
-    fft_run<H, 1, T, true, false>(p.tw_H, ld_acc, sldF, sstF, st_g);
+    fft_run<H, 1, T, true, false, 16, 1, true>(p.tw_H, ld_acc, sldF, sstF, st_g);
 }
 
 // ------------------------------------------------------------ dispatch
@@ -285,9 +375,13 @@ static cudaError_t rows_launch_nb(const FftParams& p, cudaStream_t s, bool inver
             k_rows_r2c<M, T1, NB, false><<<dim3(p.H / NB, p.C), T1, smem, s>>>(p);
         }
     } else {
-        cudaError_t e = smem_limit<k_rows_c2r<M, TI, NB>>(smem);
+        // column-major spectrum [plane][kx][y] as (y, kx, plane) of 8-byte elements
+        CUtensorMap tm;
+        constexpr int BX = M < C2R_BOX ? M : C2R_BOX;
+        if (!spectrum_map(&tm, p.Uhat, p.H, M, p.K, NB, BX)) return cudaErrorInvalidValue;
+        cudaError_t e = smem_limit<k_rows_c2r<M, TI, NB>>(smem + 128);
         if (e != cudaSuccess) return e;
-        k_rows_c2r<M, TI, NB><<<dim3(p.H / NB, p.K), TI, smem, s>>>(p);
+        k_rows_c2r<M, TI, NB><<<dim3(p.H / NB, p.K), TI, smem + 128, s>>>(p, tm);
     }
     return cudaGetLastError();
 }

@@ -27,6 +27,7 @@ namespace lenia {
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -36,8 +37,22 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)
 {
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
+// The same sums on packed FP32 pairs (sm_100 family f32x2 instructions, one
+// instruction per complex add; round-to-nearest like the scalar forms, so
+// the results are identical).  PK selects them in the butterflies below.
+template <bool PK>
+__device__ __forceinline__ float2 cadd_(float2 a, float2 b)
+{
+    if constexpr (PK) return __fadd2_rn(a, b);
+    else return cadd(a, b);
+}
+template <bool PK>
+__device__ __forceinline__ float2 csub_(float2 a, float2 b)
+{
+    if constexpr (PK) return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+    else return csub(a, b);
+}
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // multiply by -i (forward) or +i (inverse)
 template <bool INV>
 __device__ __forceinline__ float2 mul_mi(float2 a)
@@ -64,7 +79,7 @@ struct C32 {
 };
 
 // w_R^q = exp(-+2 pi i q / R) applied to a, for q < R/2 (compile-time).
-template <int R, int Q, bool INV>
+template <int R, int Q, bool INV, bool PK = false>
 __device__ __forceinline__ float2 rot(float2 a)
 {
     static_assert(R == 2 || R == 4 || R == 8 || R == 16 || R == 32, "radix");
@@ -75,21 +90,25 @@ __device__ __forceinline__ float2 rot(float2 a)
         constexpr float c = C32::cosq(q32);
         constexpr float s = C32::sinq(q32);
         // forward: multiply by (c - i s); inverse by (c + i s)
-        return INV ? make_float2(a.x * c - a.y * s, a.x * s + a.y * c)
-                   : make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
+        if constexpr (PK)
+            return INV ? __ffma2_rn(make_float2(a.y, a.x), make_float2(-s, s), __fmul2_rn(a, make_float2(c, c)))
+                       : __ffma2_rn(make_float2(a.y, a.x), make_float2(s, -s), __fmul2_rn(a, make_float2(c, c)));
+        else
+            return INV ? make_float2(a.x * c - a.y * s, a.x * s + a.y * c)
+                       : make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
     }
 }
 
 // In-register R-point DFT, natural-order input and output (radix-2 split).
-template <int R, bool INV>
+template <int R, bool INV, bool PK = false>
 struct DFT {
     template <int Q>
     __device__ __forceinline__ static void combine(float2* v, const float2* e, const float2* o)
     {
         if constexpr (Q < R / 2) {
-            float2 t = rot<R, Q, INV>(o[Q]);
-            v[Q] = cadd(e[Q], t);
-            v[Q + R / 2] = csub(e[Q], t);
+            float2 t = rot<R, Q, INV, PK>(o[Q]);
+            v[Q] = cadd_<PK>(e[Q], t);
+            v[Q + R / 2] = csub_<PK>(e[Q], t);
             combine<Q + 1>(v, e, o);
         }
     }
@@ -101,22 +120,22 @@ struct DFT {
             e[i] = v[2 * i];
             o[i] = v[2 * i + 1];
         }
-        DFT<R / 2, INV>::run(e);
-        DFT<R / 2, INV>::run(o);
+        DFT<R / 2, INV, PK>::run(e);
+        DFT<R / 2, INV, PK>::run(o);
         combine<0>(v, e, o);
     }
 };
-template <bool INV>
-struct DFT<2, INV> {
+template <bool INV, bool PK>
+struct DFT<2, INV, PK> {
     __device__ __forceinline__ static void run(float2* v)
     {
         float2 a = v[0], b = v[1];
-        v[0] = cadd(a, b);
-        v[1] = csub(a, b);
+        v[0] = cadd_<PK>(a, b);
+        v[1] = csub_<PK>(a, b);
     }
 };
-template <bool INV>
-struct DFT<1, INV> {
+template <bool INV, bool PK>
+struct DFT<1, INV, PK> {
     __device__ __forceinline__ static void run(float2*) {}
 };
 
@@ -141,7 +160,7 @@ __host__ __device__ constexpr int fft_tw_offset(int N, int NS, int rmax = 16)
 // T threads.  Element i of transform b is read with ld(b, i) and written with
 // st(b, i, v).  BFAST: consecutive threads take consecutive transforms b
 // (interleaved layouts), else consecutive butterflies j.
-template <int N, int R, int NB, int T, bool INV, bool BFAST, class LD, class ST>
+template <int N, int R, int NB, int T, bool INV, bool BFAST, bool PK = false, class LD, class ST>
 __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp, LD ld, ST st)
 {
     constexpr int NBF = NB * (N / R);
@@ -164,7 +183,7 @@ __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp,
                     v[p][r] = INV ? cmulc(v[p][r], w) : cmul(v[p][r], w);
                 }
             }
-            DFT<R, INV>::run(v[p]);
+            DFT<R, INV, PK>::run(v[p]);
         }
     }
     __syncthreads();
@@ -186,8 +205,8 @@ __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp,
 // Full transform: pass 1 reads with ld_first, middle passes use the shared
 // accessors sld/sst, the last pass writes with st_last.  With a single pass
 // the first reader and the last writer are used together.
-template <int N, int NB, int T, bool INV, bool BFAST, int RMAX = 16, int NS = 1, class LF, class SL, class SS,
-          class STL>
+template <int N, int NB, int T, bool INV, bool BFAST, int RMAX = 16, int NS = 1, bool PK = false, class LF,
+          class SL, class SS, class STL>
 __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_first, SL sld, SS sst, STL st_last)
 {
     constexpr int R = fft_radix(N / NS, RMAX);
@@ -195,15 +214,15 @@ __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_fir
     constexpr bool last = (NS * R == N);
     const float2* twp = tw + fft_tw_offset(N, NS, RMAX);
     if constexpr (first && last) {
-        fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, ld_first, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK>(NS, twp, ld_first, st_last);
     } else if constexpr (first) {
-        fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, ld_first, sst);
-        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R>(tw, ld_first, sld, sst, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK>(NS, twp, ld_first, sst);
+        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK>(tw, ld_first, sld, sst, st_last);
     } else if constexpr (last) {
-        fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, sld, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK>(NS, twp, sld, st_last);
     } else {
-        fft_pass<N, R, NB, T, INV, BFAST>(NS, twp, sld, sst);
-        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R>(tw, ld_first, sld, sst, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK>(NS, twp, sld, sst);
+        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK>(tw, ld_first, sld, sst, st_last);
     }
 }
 

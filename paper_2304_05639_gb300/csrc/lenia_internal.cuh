@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of liblenia.
 #pragma once
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -176,6 +177,9 @@ cudaError_t launch_adjoint_epilogue(const AdjParams& p, cudaStream_t s);
 cudaError_t launch_adjoint_gather(const AdjParams& p, cudaStream_t s);
 cudaError_t launch_adjoint_gene_out(const double* gene_acc, int nv, float* out, cudaStream_t s);
 bool epilogue_rows_supported(const EpiParams& p);
+// cuTensorMapEncodeTiled through the runtime's driver entry point (null if
+// the driver does not provide it).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 cudaError_t launch_epilogue_rows(const EpiParams& p, int num_sms, int* status, cudaStream_t s, int* n_blocks);
 bool fft_size_supported(int H, int W);
 int epilogue_blocks(int H, int W);
