@@ -253,51 +253,97 @@ __global__ void __launch_bounds__(T, (512 / T) < 8 ? (512 / T) : 8)
 // PERK: one block per (column, channel, kernel of that channel), grid z = the
 // longest kernel list: shorter serial chains for small grids, at the cost of
 // repeating the forward column transform for every kernel of a channel.
+// Shared memory of the column passes: two H-element work buffers (XOR
+// swizzle, no padding) and, for k_cols_conv, one kernel-spectrum column.
+__host__ __device__ constexpr int cols_spec_floats(int H) { return (H / 2 + 1 + 3) / 4 * 4; }
+__host__ __device__ constexpr size_t cols_smem_bytes(int H) { return 2 * (size_t)H * 8 + (size_t)cols_spec_floats(H) * 4; }
+
+// Column 0 of the packed spectrum holds the DC and Nyquist columns (both
+// real along y): out = f a + conj(f(-ky)) b with a, b from the two kernel
+// spectra.  Kept out of line so that its registers do not weigh on the other
+// columns' code.
+template <int H, int T>
+__device__ __noinline__ void cols_conv_dc(const FftParams& p, float2* F, float2* Wk, int plane, int c, int w, int t0,
+                                          int nk, const float* Sw)
+{
+    const int M = p.W / 2;
+    const int HS = H / 2 + 1;
+    const float2* src = p.Ahat + (size_t)plane * M * H;
+    auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
+    auto sldF = [&](int, int i) { return F[swx(i)]; };
+    auto sstF = [&](int, int i, float2 v) { F[swx(i)] = v; };
+    auto sldW = [&](int, int i) { return Wk[swx(i)]; };
+    auto sstW = [&](int, int i, float2 v) { Wk[swx(i)] = v; };
+    fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
+    for (int t = t0; t < nk; t++) {
+        const int k = p.klist[c][t];
+        const float* Sk = Sw + (size_t)k * (M + 1) * HS;
+        auto ld_mul = [&](int, int i) {
+            const int kyr = i <= H / 2 ? i : H - i;
+            const float2 f = F[swx(i)];
+            const float s0 = __ldg(&Sk[kyr]);
+            const float sn = __ldg(&Sk[(size_t)M * HS + kyr]);
+            const float2 fm = cconj(F[swx((H - i) & (H - 1))]);
+            const float a = 0.5f * (s0 + sn), bb = 0.5f * (s0 - sn);
+            return make_float2(f.x * a + fm.x * bb, f.y * a + fm.y * bb);
+        };
+        float2* dst = p.Uhat + ((size_t)(w * p.kpw + k - p.k_base) * M) * H;
+        auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
+        fft_run<H, 1, T, true, false, 16, 1, true>(p.tw_H, ld_mul, sldW, sstW, st_g);
+    }
+}
+
 template <int H, int T, bool PERK>
 __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(FftParams p)
 {
     extern __shared__ float2 sm[];
-    constexpr int SZ = swz_size(H);
     float2* F = sm;
-    float2* Wk = sm + SZ;
+    float2* Wk = sm + H;
+    float* Sb = reinterpret_cast<float*>(sm + 2 * H);      // the current kernel's spectrum column
     const int plane = blockIdx.y;              // Ahat plane: channel c of world w
     const int c = plane % p.cw, w = plane / p.cw;
     const int kx = blockIdx.x;
     const int M = p.W / 2;
     const int HS = H / 2 + 1;
     if (PERK && (int)blockIdx.z >= p.kcount[c]) return;     // uniform over the block
+    const int t0 = PERK ? (int)blockIdx.z : 0;
+    const int nk = PERK ? t0 + 1 : p.kcount[c];
+    const float* Sw = p.S_list ? p.S_list[w] : p.S;
 
     const float2* src = p.Ahat + ((size_t)plane * M + kx) * H;
     auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
-    auto sldF = [&](int, int i) { return F[swz(i)]; };
-    auto sstF = [&](int, int i, float2 v) { F[swz(i)] = v; };
-    fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
+    auto sldF = [&](int, int i) { return F[swx(i)]; };
+    auto sstF = [&](int, int i, float2 v) { F[swx(i)] = v; };
+    auto sldW = [&](int, int i) { return Wk[swx(i)]; };
+    auto sstW = [&](int, int i, float2 v) { Wk[swx(i)] = v; };
 
-    const int t0 = PERK ? (int)blockIdx.z : 0;
-    const int nk = PERK ? t0 + 1 : p.kcount[c];
+    if (kx == 0) {
+        cols_conv_dc<H, T>(p, F, Wk, plane, c, w, t0, nk, Sw);
+        return;
+    }
+
+    // Other columns: each kernel's spectrum column is copied asynchronously
+    // into Sb while the previous transform runs (the first one during the
+    // forward transform); the product with it is the first inverse pass's load.
+    auto fetch_s = [&](int t) {
+        const float* Sc = Sw + (size_t)p.klist[c][t] * (M + 1) * HS + (size_t)kx * HS;
+        for (int i = threadIdx.x; i < HS; i += T) cp_async4(&Sb[i], &Sc[i]);
+        cp_async_commit();
+    };
+    if (t0 < nk) fetch_s(t0);
+    fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
+    auto ld_mul = [&](int, int i) { return cscale(F[swx(i)], Sb[i <= H / 2 ? i : H - i]); };
     for (int t = t0; t < nk; t++) {
         const int k = p.klist[c][t];
-        const float* Sk = (p.S_list ? p.S_list[w] : p.S) + (size_t)k * (M + 1) * HS;
-        auto ld_mul = [&](int, int i) {
-            const int ky = i;
-            const int kyr = ky <= H / 2 ? ky : H - ky;
-            const float2 f = F[swz(i)];
-            if (kx == 0) {
-                // packed (DC, Nyquist) column: out = f a + conj(f(-ky)) b
-                const float s0 = __ldg(&Sk[kyr]);
-                const float sn = __ldg(&Sk[(size_t)M * HS + kyr]);
-                const float2 fm = cconj(F[swz((H - ky) & (H - 1))]);
-                const float a = 0.5f * (s0 + sn), bb = 0.5f * (s0 - sn);
-                return make_float2(f.x * a + fm.x * bb, f.y * a + fm.y * bb);
-            }
-            const float s = __ldg(&Sk[(size_t)kx * HS + kyr]);
-            return cscale(f, s);
-        };
+        cp_async_wait_all();
+        __syncthreads();
         float2* dst = p.Uhat + ((size_t)(w * p.kpw + k - p.k_base) * M + kx) * H;
-        auto sldW = [&](int, int i) { return Wk[swz(i)]; };
-        auto sstW = [&](int, int i, float2 v) { Wk[swz(i)] = v; };
         auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
-        fft_run<H, 1, T, true, false, 16, 1, true>(p.tw_H, ld_mul, sldW, sstW, st_g);
+        constexpr int R1 = fft_radix(H, 16);
+        // first pass (reads Sb, then a barrier), then the next column's copy
+        fft_pass<H, R1, 1, T, true, false, true>(1, p.tw_H, ld_mul, sstW);
+        if (t + 1 < nk) fetch_s(t + 1);
+        fft_run<H, 1, T, true, false, 16, R1, true>(p.tw_H, sldW, sldW, sstW, st_g);
     }
 }
 
@@ -311,16 +357,15 @@ template <int H, int T>
 __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_adj(FftParams p)
 {
     extern __shared__ float2 sm[];
-    constexpr int SZ = swz_size(H);
     float2* F = sm;
-    float2* Acc = sm + SZ;
+    float2* Acc = sm + H;
     const int c = blockIdx.y;
     const int kx = blockIdx.x;
     const int M = p.W / 2;
     const int HS = H / 2 + 1;
-    for (int i = threadIdx.x; i < H; i += T) Acc[swz(i)] = make_float2(0.f, 0.f);
-    auto sldF = [&](int, int i) { return F[swz(i)]; };
-    auto sstF = [&](int, int i, float2 v) { F[swz(i)] = v; };
+    for (int i = threadIdx.x; i < H; i += T) Acc[swx(i)] = make_float2(0.f, 0.f);
+    auto sldF = [&](int, int i) { return F[swx(i)]; };
+    auto sstF = [&](int, int i, float2 v) { F[swx(i)] = v; };
     const int nk = p.kcount[c];
     for (int t = 0; t < nk; t++) {
         const int k = p.klist[c][t];
@@ -332,23 +377,23 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_adj(Fft
         // the zeroing and the updates); F is complete after fft_run's barrier
         for (int i = threadIdx.x; i < H; i += T) {
             const int kyr = i <= H / 2 ? i : H - i;
-            const float2 f = F[swz(i)];
+            const float2 f = F[swx(i)];
             float2 v;
             if (kx == 0) {
                 const float s0 = __ldg(&Sk[kyr]);
                 const float sn = __ldg(&Sk[(size_t)M * HS + kyr]);
-                const float2 fm = cconj(F[swz((H - i) & (H - 1))]);
+                const float2 fm = cconj(F[swx((H - i) & (H - 1))]);
                 const float a = 0.5f * (s0 + sn), bb = 0.5f * (s0 - sn);
                 v = make_float2(f.x * a + fm.x * bb, f.y * a + fm.y * bb);
             } else {
                 v = cscale(f, __ldg(&Sk[(size_t)kx * HS + kyr]));
             }
-            Acc[swz(i)] = cadd(Acc[swz(i)], v);
+            Acc[swx(i)] = cadd(Acc[swx(i)], v);
         }
     }
     __syncthreads();
     float2* dst = p.Uhat + ((size_t)c * M + kx) * H;
-    auto ld_acc = [&](int, int i) { return Acc[swz(i)]; };
+    auto ld_acc = [&](int, int i) { return Acc[swx(i)]; };
     auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
     fft_run<H, 1, T, true, false, 16, 1, true>(p.tw_H, ld_acc, sldF, sstF, st_g);
 }
@@ -404,7 +449,7 @@ template <int H>
 static cudaError_t cols_launch(const FftParams& p, cudaStream_t s, bool transposed = false)
 {
     constexpr int T = H / 16 >= 64 ? H / 16 : 64;
-    const size_t smem = 2 * (size_t)swz_size(H) * sizeof(float2);
+    const size_t smem = cols_smem_bytes(H);
     const int M = p.W / 2;
     if (transposed) {
         cudaError_t e = smem_limit<k_cols_adj<H, T>>(smem);

@@ -230,6 +230,10 @@ __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_fir
 // radix-32 row transforms, whose first pass writes with stride 32) keeps the
 // power-of-two strides of the first passes off a single bank.
 __device__ __forceinline__ int swz(int i) { return i + (i >> 4); }
+// XOR form without padding (column transforms): element i of each aligned
+// group of 16 moves to slot (i mod 16) xor (i / 16 mod 16), which spreads the
+// stride-16 stores of the first two radix-16 passes over all 16 bank pairs.
+__device__ __forceinline__ int swx(int i) { return i ^ ((i >> 4) & 15); }
 __host__ __device__ constexpr int swz_size(int n) { return n + (n >> 4) + 1; }
 __device__ __forceinline__ int swz32(int i) { return i + (i >> 5); }
 __host__ __device__ constexpr int swz32_size(int n) { return n + (n >> 5) + 1; }

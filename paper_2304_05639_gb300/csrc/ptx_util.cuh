@@ -84,6 +84,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
         : "memory");
 }
 
+// 4-byte asynchronous global->shared copy (no alignment beyond 4 bytes);
+// cp_async_wait_all waits for this thread's committed copies.
+__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src_gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Tiled TMA load of a 3-D box at coordinates (x, y, z) of the tensor map
 // (x counts elements of the map's data type), completing on `bar`.
 __device__ __forceinline__ void tma_load_3d(void* dst_smem, const CUtensorMap* map, int x, int y, int z,
