@@ -253,53 +253,63 @@ __global__ void __launch_bounds__(T, (512 / T) < 8 ? (512 / T) : 8)
 // PERK: one block per (column, channel, kernel of that channel), grid z = the
 // longest kernel list: shorter serial chains for small grids, at the cost of
 // repeating the forward column transform for every kernel of a channel.
-// Shared memory of the column passes: two H-element work buffers (XOR
-// swizzle, no padding) and, for k_cols_conv, one kernel-spectrum column.
+// Column passes of H >= 2048 keep each thread's share of the forward column
+// spectrum in tensor memory (TMEM) instead of a second shared-memory buffer:
+// one H-element work buffer and one kernel-spectrum column per block, so that
+// eight blocks fit on an SM.
+template <int H>
+__host__ __device__ constexpr bool cols_tmem() { return H >= 2048; }
 __host__ __device__ constexpr int cols_spec_floats(int H) { return (H / 2 + 1 + 3) / 4 * 4; }
-__host__ __device__ constexpr size_t cols_smem_bytes(int H) { return 2 * (size_t)H * 8 + (size_t)cols_spec_floats(H) * 4; }
+template <int H>
+__host__ __device__ constexpr size_t cols_smem_bytes()
+{
+    return (cols_tmem<H>() ? 1 : 2) * (size_t)H * 8 + (size_t)cols_spec_floats(H) * 4;
+}
 
 // Column 0 of the packed spectrum holds the DC and Nyquist columns (both
 // real along y): out = f a + conj(f(-ky)) b with a, b from the two kernel
-// spectra.  Kept out of line so that its registers do not weigh on the other
-// columns' code.
+// spectra.  It runs in one H-element buffer, repeating the forward
+// transform for each kernel (one block in M), and out of line so that its
+// registers do not weigh on the other columns' code.
 template <int H, int T>
-__device__ __noinline__ void cols_conv_dc(const FftParams& p, float2* F, float2* Wk, int plane, int c, int w, int t0,
-                                          int nk, const float* Sw)
+__device__ __noinline__ void cols_conv_dc(const FftParams& p, float2* Bf, int plane, int c, int w, int t0, int nk,
+                                          const float* Sw)
 {
     const int M = p.W / 2;
     const int HS = H / 2 + 1;
     const float2* src = p.Ahat + (size_t)plane * M * H;
     auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
-    auto sldF = [&](int, int i) { return F[swx(i)]; };
-    auto sstF = [&](int, int i, float2 v) { F[swx(i)] = v; };
-    auto sldW = [&](int, int i) { return Wk[swx(i)]; };
-    auto sstW = [&](int, int i, float2 v) { Wk[swx(i)] = v; };
-    fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
+    auto sld = [&](int, int i) { return Bf[swx(i)]; };
+    auto sst = [&](int, int i, float2 v) { Bf[swx(i)] = v; };
     for (int t = t0; t < nk; t++) {
+        fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sld, sst, sst);
         const int k = p.klist[c][t];
         const float* Sk = Sw + (size_t)k * (M + 1) * HS;
+        // the first inverse pass reads every input before its barrier, so it
+        // may write the same buffer
         auto ld_mul = [&](int, int i) {
             const int kyr = i <= H / 2 ? i : H - i;
-            const float2 f = F[swx(i)];
+            const float2 f = Bf[swx(i)];
             const float s0 = __ldg(&Sk[kyr]);
             const float sn = __ldg(&Sk[(size_t)M * HS + kyr]);
-            const float2 fm = cconj(F[swx((H - i) & (H - 1))]);
+            const float2 fm = cconj(Bf[swx((H - i) & (H - 1))]);
             const float a = 0.5f * (s0 + sn), bb = 0.5f * (s0 - sn);
             return make_float2(f.x * a + fm.x * bb, f.y * a + fm.y * bb);
         };
         float2* dst = p.Uhat + ((size_t)(w * p.kpw + k - p.k_base) * M) * H;
         auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
-        fft_run<H, 1, T, true, false, 16, 1, true>(p.tw_H, ld_mul, sldW, sstW, st_g);
+        fft_run<H, 1, T, true, false, 16, 1, true>(p.tw_H, ld_mul, sld, sst, st_g);
     }
 }
 
 template <int H, int T, bool PERK>
 __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(FftParams p)
 {
+    constexpr bool TM = cols_tmem<H>();
     extern __shared__ float2 sm[];
-    float2* F = sm;
-    float2* Wk = sm + H;
-    float* Sb = reinterpret_cast<float*>(sm + 2 * H);      // the current kernel's spectrum column
+    float2* F = sm;                                         // forward spectrum (smem variant)
+    float2* Wk = TM ? sm : sm + H;                          // inverse work buffer
+    float* Sb = reinterpret_cast<float*>(sm + (TM ? H : 2 * H));   // the current kernel's spectrum column
     const int plane = blockIdx.y;              // Ahat plane: channel c of world w
     const int c = plane % p.cw, w = plane / p.cw;
     const int kx = blockIdx.x;
@@ -309,6 +319,10 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
     const int t0 = PERK ? (int)blockIdx.z : 0;
     const int nk = PERK ? t0 + 1 : p.kcount[c];
     const float* Sw = p.S_list ? p.S_list[w] : p.S;
+    if (kx == 0) {
+        cols_conv_dc<H, T>(p, sm, plane, c, w, t0, nk, Sw);
+        return;
+    }
 
     const float2* src = p.Ahat + ((size_t)plane * M + kx) * H;
     auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
@@ -317,33 +331,87 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
     auto sldW = [&](int, int i) { return Wk[swx(i)]; };
     auto sstW = [&](int, int i, float2 v) { Wk[swx(i)] = v; };
 
-    if (kx == 0) {
-        cols_conv_dc<H, T>(p, F, Wk, plane, c, w, t0, nk, Sw);
-        return;
-    }
-
-    // Other columns: each kernel's spectrum column is copied asynchronously
-    // into Sb while the previous transform runs (the first one during the
-    // forward transform); the product with it is the first inverse pass's load.
+    // Each kernel's spectrum column is copied asynchronously into Sb while
+    // the previous transform runs (the first one during the forward
+    // transform); the product with it is the first inverse pass's load.
     auto fetch_s = [&](int t) {
         const float* Sc = Sw + (size_t)p.klist[c][t] * (M + 1) * HS + (size_t)kx * HS;
         for (int i = threadIdx.x; i < HS; i += T) cp_async4(&Sb[i], &Sc[i]);
         cp_async_commit();
     };
-    if (t0 < nk) fetch_s(t0);
-    fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
-    auto ld_mul = [&](int, int i) { return cscale(F[swx(i)], Sb[i <= H / 2 ? i : H - i]); };
-    for (int t = t0; t < nk; t++) {
-        const int k = p.klist[c][t];
-        cp_async_wait_all();
+    constexpr int R1 = fft_radix(H, 16);
+    if constexpr (!TM) {
+        if (t0 < nk) fetch_s(t0);
+        fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
+        auto ld_mul = [&](int, int i) { return cscale(F[swx(i)], Sb[i <= H / 2 ? i : H - i]); };
+        for (int t = t0; t < nk; t++) {
+            const int k = p.klist[c][t];
+            cp_async_wait_all();
+            __syncthreads();
+            float2* dst = p.Uhat + ((size_t)(w * p.kpw + k - p.k_base) * M + kx) * H;
+            auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
+            // first pass (reads Sb, then a barrier), then the next column's copy
+            fft_pass<H, R1, 1, T, true, false, true>(1, p.tw_H, ld_mul, sstW);
+            if (t + 1 < nk) fetch_s(t + 1);
+            fft_run<H, 1, T, true, false, 16, R1, true>(p.tw_H, sldW, sldW, sstW, st_g);
+        }
+    } else {
+        // The first inverse pass (radix 16, one butterfly per thread) takes
+        // elements j + r H/16 of the forward spectrum, the same for every
+        // kernel: thread j keeps those 16 values in its TMEM lane.
+        constexpr int TS = H / R1;
+        static_assert(R1 == 16 && TS == T && T % 128 == 0, "one first-pass butterfly per thread");
+        constexpr int NCOLS = 32 * (T / 128);
+        __shared__ uint32_t tmem_base;
+        const int warp = threadIdx.x >> 5, j = threadIdx.x;
+        if (warp == 0) {
+            tmem_alloc<NCOLS>(&tmem_base);
+            tmem_fence_before_sync();
+        }
+        if (t0 < nk) fetch_s(t0);
+        fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);   // ends with a barrier
+        tmem_fence_after_sync();
+        const uint32_t taddr = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
+        {
+            float fv[32];
+#pragma unroll
+            for (int r = 0; r < 16; r++) {
+                const float2 f = F[swx(j + r * TS)];
+                fv[2 * r] = f.x;
+                fv[2 * r + 1] = f.y;
+            }
+            tmem_st16(taddr, fv);
+            tmem_st16(taddr + 16, fv + 16);
+            tmem_wait_st();
+        }
+        for (int t = t0; t < nk; t++) {
+            const int k = p.klist[c][t];
+            cp_async_wait_all();
+            __syncthreads();          // Sb landed; every read of the work buffer is done
+            float fv[32];
+            tmem_ld16(taddr, fv);
+            tmem_ld16(taddr + 16, fv + 16);
+            float2 v[16];
+#pragma unroll
+            for (int r = 0; r < 16; r++) {
+                const int ky = j + r * TS;
+                v[r] = cscale(make_float2(fv[2 * r], fv[2 * r + 1]), Sb[ky <= H / 2 ? ky : H - ky]);
+            }
+            DFT<16, true, true>::run(v);
+#pragma unroll
+            for (int q = 0; q < 16; q++) Wk[swx(j * 16 + q)] = v[q];
+            __syncthreads();
+            if (t + 1 < nk) fetch_s(t + 1);
+            float2* dst = p.Uhat + ((size_t)(w * p.kpw + k - p.k_base) * M + kx) * H;
+            auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
+            fft_run<H, 1, T, true, false, 16, R1, true>(p.tw_H, sldW, sldW, sstW, st_g);
+        }
+        tmem_fence_before_sync();
         __syncthreads();
-        float2* dst = p.Uhat + ((size_t)(w * p.kpw + k - p.k_base) * M + kx) * H;
-        auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
-        constexpr int R1 = fft_radix(H, 16);
-        // first pass (reads Sb, then a barrier), then the next column's copy
-        fft_pass<H, R1, 1, T, true, false, true>(1, p.tw_H, ld_mul, sstW);
-        if (t + 1 < nk) fetch_s(t + 1);
-        fft_run<H, 1, T, true, false, 16, R1, true>(p.tw_H, sldW, sldW, sstW, st_g);
+        if (warp == 0) {
+            tmem_fence_after_sync();
+            tmem_dealloc<NCOLS>(tmem_base);
+        }
     }
 }
 
@@ -449,9 +517,10 @@ template <int H>
 static cudaError_t cols_launch(const FftParams& p, cudaStream_t s, bool transposed = false)
 {
     constexpr int T = H / 16 >= 64 ? H / 16 : 64;
-    const size_t smem = cols_smem_bytes(H);
+    const size_t smem = cols_smem_bytes<H>();
     const int M = p.W / 2;
     if (transposed) {
+        const size_t smem = 2 * (size_t)H * 8;
         cudaError_t e = smem_limit<k_cols_adj<H, T>>(smem);
         if (e != cudaSuccess) return e;
         k_cols_adj<H, T><<<dim3(M, p.C), T, smem, s>>>(p);
