@@ -27,9 +27,10 @@
  *     stream is synchronised.  A context is not thread-safe.
  *   - The library owns the context and all scratch memory (kernel spectra,
  *     FFT intermediates, potentials, stats partials), allocated in lenia_init
- *     and freed in lenia_destroy.  After lenia_init only lenia_set_walls and
- *     the first lenia_step_evolve allocate device memory (as documented
- *     there); lenia_stats_noalloc allocates nothing at all.
+ *     and freed in lenia_destroy.  After lenia_init only lenia_set_walls,
+ *     the first lenia_step_evolve and the first host-buffer step allocate
+ *     device memory (as documented there); lenia_stats_noalloc allocates
+ *     nothing at all.
  *   - Errors: every entry point returns a status; nothing aborts and nothing
  *     is thrown.  Arguments are validated before any launch; a CUDA error
  *     seen after a launch returns LENIA_ECUDA.  lenia_last_error() gives a
@@ -252,12 +253,15 @@ LENIA_API lenia_status lenia_step_host(lenia_ctx* ctx, const float* A_in, const 
                              float* A_out, float* P_out, float* stats_out, void* stream);
 
 /* The same step enqueued without waiting, for independent host worlds in a
- * row (a serving loop): the phenospace upload and the convolution run on
- * `stream` while the genes upload on a library stream; the downloads run on
- * another library stream and overlap the next call's uploads.  Host buffers
- * must stay valid and unmodified (inputs) / unread (outputs) until
- * lenia_host_wait returns.  Each call's inputs must not be a previous call's
- * pending outputs. */
+ * row (a serving loop).  Alternate calls use two sets of device staging
+ * buffers: a call's uploads (on a library stream) wait only until the call
+ * before last has finished reading its set, so they run under the previous
+ * call's step and downloads; the step runs on `stream`; the downloads run on
+ * another library stream.  The first host-buffer step (this or
+ * lenia_step_host) allocates the second set, (2 C + 2 n_p K) floats per site
+ * (synchronously).  Host buffers must stay valid and unmodified (inputs) /
+ * unread (outputs) until lenia_host_wait returns.  Each call's inputs must
+ * not be a previous call's pending outputs. */
 LENIA_API lenia_status lenia_step_host_async(lenia_ctx* ctx, const float* A_in, const float* P_in,
                                              float* A_out, float* P_out, float* stats_out, void* stream);
 /* Waits for every enqueued host step (downloads included), then lenia_check. */

@@ -77,8 +77,14 @@ struct lenia_ctx {
     uint16_t* d_cnt = nullptr;             // [H][W] empty sites per K_oxy disk
     // host-buffer steps (lenia_step_host[_async]): a stream for gene uploads and
     // one for downloads, and the events that order them against the compute
+    // host-buffer pipeline (lenia_step_host_async): two staging sets used by
+    // alternate steps; set 0 is d_A2/d_P2 (in) and d_A3/d_P3 (out), set 1 is
+    // allocated on first use
     cudaStream_t up_stream = nullptr, down_stream = nullptr;
-    cudaEvent_t ev_up = nullptr, ev_done = nullptr, ev_down = nullptr;
+    cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_down[2] = {nullptr, nullptr};
+    float *d_hA_in1 = nullptr, *d_hP_in1 = nullptr, *d_hA_out1 = nullptr, *d_hP_out1 = nullptr;
+    float* d_hstats = nullptr;             // [2][C][3]
+    int host_set = 0;                      // staging set of the next host step
     bool host_pending = false;             // a download has been enqueued since the last wait
     // optional per-launch timing (lenia_profile_start / lenia_profile_stop)
     bool prof = false;
@@ -496,12 +502,14 @@ void lenia_destroy(lenia_ctx* c)
                     c->d_A3, c->d_P3, c->d_stats, c->d_status, c->d_ckpt, c->d_seg, c->d_gA[0],
                     c->d_gA[1], c->d_gpre, c->d_gU, c->d_V, c->d_gene_part, c->d_gene_acc,
                     c->d_Ahat_t, c->d_Uhat_t, c->d_ticket, c->d_walls, c->d_alpha_e, c->d_empty,
-                    c->d_cnt, c->d_Useg, c->d_adj_ticket};
+                    c->d_cnt, c->d_Useg, c->d_adj_ticket, c->d_hA_in1, c->d_hP_in1, c->d_hA_out1,
+                    c->d_hP_out1, c->d_hstats};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-    for (cudaEvent_t e : {c->ev_up, c->ev_done, c->ev_down})
-        if (e) cudaEventDestroy(e);
+    for (int b = 0; b < 2; b++)
+        for (cudaEvent_t e : {c->ev_up[b], c->ev_done[b], c->ev_down[b]})
+            if (e) cudaEventDestroy(e);
     for (cudaStream_t t : {c->up_stream, c->down_stream})
         if (t) cudaStreamDestroy(t);
     delete c;
@@ -1114,45 +1122,58 @@ lenia_status lenia_step_host_async(lenia_ctx* c, const float* A_in, const float*
     if (!c) return LENIA_EINVAL;
     if (!A_in || !A_out || (c->n_p && (!P_in || !P_out)))
         return fail(c, LENIA_EINVAL, "host A (and P with localized genes) must be non-null");
+    const int C = c->cfg.n_channels;
+    const size_t nA = c->N * C, nP = c->N * c->n_p * c->cfg.n_kernels;
     if (!c->up_stream) {
+        lenia_status a = dalloc(c, &c->d_hA_in1, nA);
+        if (a == LENIA_OK) a = dalloc(c, &c->d_hA_out1, nA);
+        if (a == LENIA_OK && nP) a = dalloc(c, &c->d_hP_in1, nP);
+        if (a == LENIA_OK && nP) a = dalloc(c, &c->d_hP_out1, nP);
+        if (a == LENIA_OK) a = dalloc(c, &c->d_hstats, (size_t)2 * C * 3);
+        if (a != LENIA_OK) return a;
         CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking));
         CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->down_stream, cudaStreamNonBlocking));
-        CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming));
-        CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming));
-        CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_down, cudaEventDisableTiming));
-        // nothing recorded yet: record once so that the first waits are no-ops
-        CUDA_OR_FAIL(c, cudaEventRecord(c->ev_done, (cudaStream_t)stream));
-        CUDA_OR_FAIL(c, cudaEventRecord(c->ev_down, (cudaStream_t)stream));
+        for (int b = 0; b < 2; b++) {
+            CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_up[b], cudaEventDisableTiming));
+            CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming));
+            CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_down[b], cudaEventDisableTiming));
+            // nothing recorded yet: record once so that the first waits are no-ops
+            CUDA_OR_FAIL(c, cudaEventRecord(c->ev_done[b], (cudaStream_t)stream));
+            CUDA_OR_FAIL(c, cudaEventRecord(c->ev_down[b], (cudaStream_t)stream));
+        }
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t ab = c->N * c->cfg.n_channels * sizeof(float);
-    const size_t pb = c->N * c->n_p * c->cfg.n_kernels * sizeof(float);
-    // genes upload on their own stream once the previous step no longer reads
-    // the staging buffer; the phenospace upload and the convolution (which
-    // reads A only) proceed meanwhile on the compute stream
-    if (pb) {
-        CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->up_stream, c->ev_done, 0));
-        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_P2, P_in, pb, cudaMemcpyHostToDevice, c->up_stream));
-        CUDA_OR_FAIL(c, cudaEventRecord(c->ev_up, c->up_stream));
-    }
-    CUDA_OR_FAIL(c, cudaStreamWaitEvent(s, c->ev_done, 0));      // (a caller may change streams)
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_A2, A_in, ab, cudaMemcpyHostToDevice, s));
-    lenia_status st = potentials(c, c->d_A2, c->d_U, s);
+    const int b = c->host_set;
+    float* dA_in = b ? c->d_hA_in1 : c->d_A2;
+    float* dP_in = b ? c->d_hP_in1 : c->d_P2;
+    float* dA_out = b ? c->d_hA_out1 : c->d_A3;
+    float* dP_out = b ? c->d_hP_out1 : c->d_P3;
+    float* dstats = c->d_hstats + (size_t)b * C * 3;
+    const size_t ab = nA * sizeof(float), pb = nP * sizeof(float);
+    // uploads on their own stream, into the set the step before last has
+    // finished reading: they run ahead, under the previous step's compute
+    // and downloads
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->up_stream, c->ev_done[b], 0));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(dA_in, A_in, ab, cudaMemcpyHostToDevice, c->up_stream));
+    if (pb) CUDA_OR_FAIL(c, cudaMemcpyAsync(dP_in, P_in, pb, cudaMemcpyHostToDevice, c->up_stream));
+    CUDA_OR_FAIL(c, cudaEventRecord(c->ev_up[b], c->up_stream));
+    // the step, once its inputs landed and the download of the step before
+    // last is done with this set's outputs
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(s, c->ev_up[b], 0));
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(s, c->ev_down[b], 0));
+    lenia_status st = step_impl(c, dA_in, c->n_p ? dP_in : nullptr, dA_out, c->n_p ? dP_out : nullptr,
+                                stats_out ? dstats : nullptr, nullptr, nullptr, s);
     if (st != LENIA_OK) return st;
-    if (pb) CUDA_OR_FAIL(c, cudaStreamWaitEvent(s, c->ev_up, 0));
-    CUDA_OR_FAIL(c, cudaStreamWaitEvent(s, c->ev_down, 0));      // the previous download is done with d_A3/d_P3
-    st = step_impl(c, c->d_A2, c->n_p ? c->d_P2 : nullptr, c->d_A3, c->n_p ? c->d_P3 : nullptr,
-                   stats_out ? c->d_stats : nullptr, nullptr, c->d_U, s);
-    if (st != LENIA_OK) return st;
-    CUDA_OR_FAIL(c, cudaEventRecord(c->ev_done, s));
-    // downloads on their own stream, overlapping the next step's uploads
-    CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->down_stream, c->ev_done, 0));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(A_out, c->d_A3, ab, cudaMemcpyDeviceToHost, c->down_stream));
-    if (pb) CUDA_OR_FAIL(c, cudaMemcpyAsync(P_out, c->d_P3, pb, cudaMemcpyDeviceToHost, c->down_stream));
+    CUDA_OR_FAIL(c, cudaEventRecord(c->ev_done[b], s));
+    // downloads on their own stream, overlapping the next steps' uploads
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->down_stream, c->ev_done[b], 0));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(A_out, dA_out, ab, cudaMemcpyDeviceToHost, c->down_stream));
+    if (pb) CUDA_OR_FAIL(c, cudaMemcpyAsync(P_out, dP_out, pb, cudaMemcpyDeviceToHost, c->down_stream));
     if (stats_out)
-        CUDA_OR_FAIL(c, cudaMemcpyAsync(stats_out, c->d_stats, c->cfg.n_channels * 3 * sizeof(float),
-                                        cudaMemcpyDeviceToHost, c->down_stream));
-    CUDA_OR_FAIL(c, cudaEventRecord(c->ev_down, c->down_stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(stats_out, dstats, C * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                                        c->down_stream));
+    CUDA_OR_FAIL(c, cudaEventRecord(c->ev_down[b], c->down_stream));
+    c->host_set = b ^ 1;
     c->host_pending = true;
     return LENIA_OK;
 }
