@@ -9,8 +9,8 @@
 //   dL/dmu_k    = sum gpre dt h_k F' g (U - mu) / sigma^2
 //   dL/dsigma_k = sum gpre dt h_k F' g (U - mu)^2 / sigma^3
 //   dL/dh_k     = sum gpre dt F(g)
-// as block partials reduced in FP64 in a fixed order by the block that
-// finishes last.  The transposed convolution (gA_src += K~_k (x) gU_k; K~ is
+// as FP64 block partials, reduced in a fixed order by a second small kernel
+// (one block per value).  The transposed convolution (gA_src += K~_k (x) gU_k; K~ is
 // point symmetric, so it is the same convolution) runs on the forward
 // machinery; its inverse row pass adds gpre (FFT path) or k_adjoint_gather
 // adds it (direct path).
@@ -79,30 +79,41 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint_epilogue(AdjParams p)
         }
     }
     __syncthreads();
+    // value-major partials [K * 3][blocks]: the reduction kernel reads them coalesced
     for (int v = threadIdx.x; v < K * 3; v += ADJ_THREADS) {
         double s = 0.0;
         for (int w = 0; w < ADJ_THREADS / 32; w++) s += (double)red[w][v];
-        p.gene_partials[(size_t)blockIdx.x * K * 3 + v] = s;
+        p.gene_partials[(size_t)v * gridDim.x + blockIdx.x] = s;
     }
-    // the block that finishes last adds every block's partials to gene_acc,
-    // blocks in order (deterministic), and re-arms the ticket
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(p.ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // one warp per value: lane l sums blocks l, l + 32, ... in order, then a
-    // fixed shuffle tree (the same order every launch)
-    for (int v = warp; v < K * 3; v += ADJ_THREADS / 32) {
-        double s = 0.0;
-        for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(&p.gene_partials[(size_t)b * K * 3 + v]);
+}
+
+// gene_acc[v] += sum over the nb block partials of value v (block v): thread t
+// sums blocks t, t + 256, ... in order, then a fixed shuffle / shared tree,
+// so every launch adds in the same order.
+constexpr int ADJ_RED_THREADS = 256;
+__global__ void __launch_bounds__(ADJ_RED_THREADS) k_adjoint_gene_reduce(const double* partials, int nb,
+                                                                      double* gene_acc)
+{
+    __shared__ double wsum[ADJ_RED_THREADS / 32];
+    const int v = blockIdx.x;
+    const double* src = partials + (size_t)v * nb;
+    double s0 = 0.0, s1 = 0.0;
+    int b = threadIdx.x;
+    for (; b + ADJ_RED_THREADS < nb; b += 2 * ADJ_RED_THREADS) {
+        s0 += src[b];
+        s1 += src[b + ADJ_RED_THREADS];
+    }
+    if (b < nb) s0 += src[b];
+    double s = s0 + s1;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (lane == 0) p.gene_acc[v] += s;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < ADJ_RED_THREADS / 32; w++) t += wsum[w];
+        gene_acc[v] += t;
     }
-    if (threadIdx.x == 0) *p.ticket = 0u;
 }
 
 // gA_c = gpre_c + sum_{k: src(k) = c} V_k  (V_k = K~_k (x) gU_k, in kernel order),
@@ -134,7 +145,11 @@ int adjoint_blocks(int H, int W) { return (int)(((size_t)H * W + ADJ_THREADS - 1
 
 cudaError_t launch_adjoint_epilogue(const AdjParams& p, cudaStream_t s)
 {
-    k_adjoint_epilogue<<<adjoint_blocks(p.H, p.W), ADJ_THREADS, 0, s>>>(p);
+    const int nb = adjoint_blocks(p.H, p.W);
+    k_adjoint_epilogue<<<nb, ADJ_THREADS, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_adjoint_gene_reduce<<<p.kt.K * 3, ADJ_RED_THREADS, 0, s>>>(p.gene_partials, nb, p.gene_acc);
     return cudaGetLastError();
 }
 

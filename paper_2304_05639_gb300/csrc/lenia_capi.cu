@@ -60,7 +60,6 @@ struct lenia_ctx {
     float* d_ckpt = nullptr;               // [n_ckpt][C][H][W]
     float* d_seg = nullptr;                // [max(ckpt, 2)][C][H][W]
     float* d_Useg = nullptr;               // [ckpt][K][H][W] potentials of the segment's states
-    unsigned int* d_adj_ticket = nullptr;  // last-block ticket of the gene-gradient reduction
     float* d_gA[2] = {nullptr, nullptr};
     float* d_gpre = nullptr;
     float* d_gU = nullptr;
@@ -502,7 +501,7 @@ void lenia_destroy(lenia_ctx* c)
                     c->d_A3, c->d_P3, c->d_stats, c->d_status, c->d_ckpt, c->d_seg, c->d_gA[0],
                     c->d_gA[1], c->d_gpre, c->d_gU, c->d_V, c->d_gene_part, c->d_gene_acc,
                     c->d_Ahat_t, c->d_Uhat_t, c->d_ticket, c->d_walls, c->d_alpha_e, c->d_empty,
-                    c->d_cnt, c->d_Useg, c->d_adj_ticket, c->d_hA_in1, c->d_hP_in1, c->d_hA_out1,
+                    c->d_cnt, c->d_Useg, c->d_hA_in1, c->d_hP_in1, c->d_hA_out1,
                     c->d_hP_out1, c->d_hstats};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -772,8 +771,6 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         // every state kept (ckpt_every = 1): the forward pass also keeps every
         // step's potentials, so the reverse pass recomputes nothing
         ALLOC(c->d_Useg, (size_t)(c->ckpt == 1 ? c->max_steps : c->ckpt) * K * c->N);
-        ALLOC(c->d_adj_ticket, 1);
-        CK_INIT(cudaMemset(c->d_adj_ticket, 0, sizeof(unsigned int)));
         ALLOC(c->d_gA[0], nA1);
         ALLOC(c->d_gA[1], nA1);
         ALLOC(c->d_gpre, nA1);
@@ -872,7 +869,6 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
             ap.gA_out = c->d_gA[cur ^ 1];
             ap.gene_partials = c->d_gene_part;
             ap.gene_acc = c->d_gene_acc;
-            ap.ticket = c->d_adj_ticket;
             ap.H = c->cfg.height;
             ap.W = c->cfg.width;
             ap.growth_form = c->cfg.growth_form;
@@ -925,7 +921,6 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
             ap.gA_out = c->d_gA[cur ^ 1];
             ap.gene_partials = c->d_gene_part;
             ap.gene_acc = c->d_gene_acc;
-            ap.ticket = c->d_adj_ticket;
             ap.H = c->cfg.height;
             ap.W = c->cfg.width;
             ap.growth_form = c->cfg.growth_form;

@@ -148,9 +148,8 @@ struct AdjParams {
     const float* V;            // K~_k (x) gU_k [K][H][W], or summed per source channel [C][H][W]
     int v_per_channel;         // 1: V holds sum_{src(k) = c} K~_k (x) gU_k per channel c
     float* gA_out;             // dL/dA_t [C][H][W]
-    double* gene_partials;     // [blocks][K][3]
+    double* gene_partials;     // [K][3][blocks]
     double* gene_acc;          // [K][3]: d/dmu, d/dsigma, d/dh
-    unsigned int* ticket;      // completion counter of the gene reduction (0 between launches)
     int H, W, growth_form;
     float dt;
     KernelTable kt;

@@ -477,3 +477,28 @@ def test_full_size_localized_1024_sampled():
 def test_max_fft_size_4096_sampled():
     w = inputs.localized_single_channel(H=4096, W=4096, R=12, patch=256, n_geno=8)
     _sampled_compare(w, 1, n=200)
+
+
+@pytest.mark.slow
+def test_tall_multichannel_4096_columns_sampled():
+    """4096 x 256, 3 channels, 15 kernels: 4096-point column transforms with five
+    kernels per channel (eight warps per column block, two TMEM column ranges),
+    checked at sampled sites, plus a 4-step rollout equal to repeated steps."""
+    torch = torch_mod()
+    w = inputs.multi_channel(H=4096, W=256, R=18, patch=96, n_geno=4, seed_index=14, live=True, name="tall")
+    _sampled_compare(w, 1, n=300)
+    cfg, ks = lenia.config_from_world(w, lenia.CONV_FFT)
+    ctx = lenia.lenia_init(cfg, ks)
+    try:
+        A, P = to_dev(w.A), to_dev(w.P)
+        a, p = A.clone(), P.clone()
+        lenia.lenia_rollout(ctx, a, p, 4)
+        for _ in range(4):
+            A2, P2 = torch.empty_like(A), torch.empty_like(P)
+            lenia.lenia_step(ctx, A, P, A2, P2)
+            A, P = A2, P2
+        torch.cuda.synchronize()
+        assert torch.equal(a, A) and torch.equal(p, P)
+    finally:
+        lenia.lenia_destroy(ctx)
+
