@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(256, 5) k_epilogue_rings(EpiParams p)
     const size_t rd = (size_t)(yc == H - 1 ? 0 : yc + 1) * W;
     const size_t i = rc + xc;
     bool alpha = true;
+    bool wrote_nz = false;         // a non-zero gene value was stored before alpha was known
     float tsum = 0.f;
     float acc[CT];
 #pragma unroll
@@ -416,6 +417,17 @@ __global__ void __launch_bounds__(256, 5) k_epilogue_rings(EpiParams p)
                                              : __ldg(p.P + (size_t)(pp * KT + k) * N + i);
                 alpha = alpha && (!p.maintain || val > eps_p);
                 g[pp] = val;
+            }
+            // the kernel's maintained genes go out now, while they are in
+            // registers (zeros once alpha is known false); a site that ends
+            // without alpha rewrites its planes with zeros below
+            if (in && p.P_out) {
+#pragma unroll
+                for (int pp = 0; pp < NP; pp++) {
+                    const float val = alpha ? g[pp] : 0.f;
+                    wrote_nz = wrote_nz || val != 0.f;
+                    p.P_out[(size_t)(pp * KT + k) * N + i] = val;
+                }
             }
             // ring weights and the potential
             const float w1 = g[PK + 1], w2 = g[PK + 4];
@@ -458,15 +470,10 @@ __global__ void __launch_bounds__(256, 5) k_epilogue_rings(EpiParams p)
 #pragma unroll
     for (int v = 0; v < CT * 5; v++) st[v] = 0.f;
     if (in) {
-        if (p.P_out) {
+        // a later store from this thread to the same address wins
+        if (p.P_out && !alpha && wrote_nz) {
 #pragma unroll 1
-            for (int pk = 0; pk < NP * KT; pk++) {
-                float val = 0.f;
-                if (alpha)
-                    val = p.maintain ? diffuse5<NP, KT>(p.P, pk, N, ru, rc, rd, xm, xc, xp, eps_p)
-                                     : __ldg(p.P + (size_t)pk * N + i);
-                p.P_out[(size_t)pk * N + i] = val;
-            }
+            for (int pk = 0; pk < NP * KT; pk++) p.P_out[(size_t)pk * N + i] = 0.f;
         }
 #pragma unroll
         for (int c = 0; c < CT; c++) {
