@@ -351,30 +351,24 @@ __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
 
 // Ring decomposition fast path (Section 2.4): diffusion radius 1, compile-time
 // kernel and channel counts, ring count and gene layout; one site per thread
-// (32 x 8 sites per block).  The ring potentials of one source channel sit in
-// registers while every kernel reading that channel diffuses its own NP genes,
-// forms its ring weights and its potential.  Once alpha is known the genes
-// are diffused again (their lines are still in L1/L2) and written once:
-// the diffused values where alpha = 1, zeros elsewhere.  Ring weights use the
-// hardware base-2 exponential: k_r = sum_i b_i 2^(-(r/n - r_i)^2 log2(e) / (2 w_i^2)).
+// (32 x 8 sites per block).  Kernels are taken in order of their source
+// channel; each kernel's NP gene planes over the block's tile with a one-site
+// halo (RG_TILE_H x RG_TILE_W) are copied into shared memory with cp.async
+// while the previous kernel is computed (double buffer), and the 5-point
+// diffusion reads them there.  The kernel's ring weights come from its
+// diffused kernel genes with the hardware base-2 exponential,
+// k_r = sum_i b_i 2^(-(r/n - r_i)^2 log2(e) / (2 w_i^2)), and its potential
+// from the channel's ring potentials (L1 hits after the channel's first
+// kernel).  The maintained genes are written as soon as they are diffused;
+// a site that ends without alpha rewrites them with zeros.  Needs
+// W >= RG_TILE_W and H >= RG_TILE_H (one wrap per halo coordinate).
 constexpr int RG_TY = 8;     // rows per block of the ring epilogue (one site per thread)
+constexpr int RG_TILE_W = EP_TX + 2, RG_TILE_H = RG_TY + 2;
 
-template <int NP, int KT>
-__device__ __forceinline__ float diffuse5(const float* P, int pk, size_t N, size_t ru, size_t rc, size_t rd,
-                                          int xm, int xc, int xp, float eps_p)
-{
-    const float* pl = P + (size_t)pk * N;
-    // disk |d| <= 1 in the order (-1,0), (0,-1), (0,0), (0,1), (1,0)
-    const float v0 = __ldg(pl + ru + xc), v1 = __ldg(pl + rc + xm), v2 = __ldg(pl + rc + xc);
-    const float v3 = __ldg(pl + rc + xp), v4 = __ldg(pl + rd + xc);
-    const float sm = (((v0 + v1) + v2) + v3) + v4;
-    const float n = (float)(v0 > eps_p) + (float)(v1 > eps_p) + (float)(v2 > eps_p) + (float)(v3 > eps_p) +
-                    (float)(v4 > eps_p);
-    return n > 0.f ? __saturatef(sm * rcp_approx(n)) : 0.f;
-}
-
+// Four blocks per SM (64 registers): at five the kernel spills (0.43 ms on the
+// paper's configuration against 0.36), at three it loses latency hiding (0.375).
 template <int KT, int CT, int NR, int LOC>
-__global__ void __launch_bounds__(256, 5) k_epilogue_rings(EpiParams p)
+__global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
 {
     constexpr int NG = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
     constexpr int NP = NG + 6;
@@ -383,87 +377,132 @@ __global__ void __launch_bounds__(256, 5) k_epilogue_rings(EpiParams p)
     constexpr int PH = (LOC & 4) ? NG - 1 : -1;
     constexpr int PK = NG;
     constexpr float LOG2E = 1.4426950408889634f;
+    constexpr int TP = RG_TILE_H * RG_TILE_W;           // floats per staged plane
+    __shared__ float tile[2][NP * TP];
+    __shared__ int ord[KT];
     const int H = p.H, W = p.W;
     const size_t N = (size_t)H * W;
-    const int x = blockIdx.x * EP_TX + threadIdx.x;
-    const int y = blockIdx.y * RG_TY + threadIdx.y;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * EP_TX, y0 = blockIdx.y * RG_TY;
+    const int x = x0 + tx;
+    const int y = y0 + ty;
     const bool in = x < W && y < H;
     const int xc = x < W ? x : W - 1, yc = y < H ? y : H - 1;
-    const int xm = xc == 0 ? W - 1 : xc - 1;
-    const int xp = xc == W - 1 ? 0 : xc + 1;
     const float eps_p = p.eps_p, eps_u = p.eps_u;
-    const size_t rc = (size_t)yc * W;
-    const size_t ru = (size_t)(yc == 0 ? H - 1 : yc - 1) * W;
-    const size_t rd = (size_t)(yc == H - 1 ? 0 : yc + 1) * W;
-    const size_t i = rc + xc;
+    const size_t i = (size_t)yc * W + xc;
+    // this thread's staged elements: tile rows ty (and 8 + ty for ty < 2),
+    // tile columns tx (and 32 + tx for tx < 2), as wrapped global offsets
+    auto wrapx = [&](int v) { return v < 0 ? v + W : (v >= W ? v - W : v); };
+    auto wrapy = [&](int v) { return v < 0 ? v + H : (v >= H ? v - H : v); };
+    const size_t g_r0 = (size_t)wrapy(y0 - 1 + ty) * W;
+    const size_t g_r1 = (size_t)wrapy(y0 + RG_TY - 1 + ty) * W;
+    const int g_c0 = wrapx(x0 - 1 + tx), g_c1 = wrapx(x0 + EP_TX - 1 + tx);
+    const bool hr = ty < RG_TILE_H - RG_TY, hc = tx < RG_TILE_W - EP_TX;
+    auto stage = [&](int k, float* buf) {
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++) {
+            const float* base = p.P + (size_t)(pp * KT + k) * N;
+            float* t = buf + pp * TP;
+            cp_async4(&t[ty * RG_TILE_W + tx], base + g_r0 + g_c0);
+            if (hc) cp_async4(&t[ty * RG_TILE_W + EP_TX + tx], base + g_r0 + g_c1);
+            if (hr) {
+                cp_async4(&t[(RG_TY + ty) * RG_TILE_W + tx], base + g_r1 + g_c0);
+                if (hc) cp_async4(&t[(RG_TY + ty) * RG_TILE_W + EP_TX + tx], base + g_r1 + g_c1);
+            }
+        }
+        cp_async_commit();
+    };
+    // kernels in order of their source channel (the order of the sums below)
+    if (tx == 0 && ty == 0) {
+        int n = 0;
+        for (int c = 0; c < CT; c++)
+            for (int k = 0; k < KT; k++)
+                if (p.kt.src[k] == c) ord[n++] = k;
+    }
+    __syncthreads();
+    stage(ord[0], tile[0]);
+
     bool alpha = true;
     bool wrote_nz = false;         // a non-zero gene value was stored before alpha was known
     float tsum = 0.f;
     float acc[CT];
 #pragma unroll
     for (int c = 0; c < CT; c++) acc[c] = 0.f;
+    const int o = (ty + 1) * RG_TILE_W + tx + 1;        // the site in the tile
 #pragma unroll 1
-    for (int c = 0; c < CT; c++) {
+    for (int j = 0; j < KT; j++) {
+        const int k = ord[j];
+        const int c = p.kt.src[k];
+        cp_async_wait_all();
+        __syncthreads();            // kernel j staged; every thread is done with kernel j - 1's buffer
+        if (j + 1 < KT) stage(ord[j + 1], tile[(j + 1) & 1]);
+        const float* T = tile[j & 1];
         // the channel's ring potentials: read again by each kernel of the
         // channel (L1 hits after the first)
         const float* V0 = p.U + (size_t)c * NR * N + i;
-#pragma unroll 1
-        for (int k = 0; k < KT; k++) {
-            if (p.kt.src[k] != c) continue;
-            float g[NP];
+        float g[NP];
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++) {
+            const float* t = T + pp * TP;
+            float val;
+            if (p.maintain) {
+                // disk |d| <= 1 in the order (-1,0), (0,-1), (0,0), (0,1), (1,0)
+                const float v0 = t[o - RG_TILE_W], v1 = t[o - 1], v2 = t[o], v3 = t[o + 1], v4 = t[o + RG_TILE_W];
+                const float sm = (((v0 + v1) + v2) + v3) + v4;
+                const float n = (float)(v0 > eps_p) + (float)(v1 > eps_p) + (float)(v2 > eps_p) +
+                                (float)(v3 > eps_p) + (float)(v4 > eps_p);
+                val = n > 0.f ? __saturatef(sm * rcp_approx(n)) : 0.f;
+            } else {
+                val = t[o];
+            }
+            alpha = alpha && (!p.maintain || val > eps_p);
+            g[pp] = val;
+        }
+        // the kernel's maintained genes go out now, while they are in
+        // registers (zeros once alpha is known false); a site that ends
+        // without alpha rewrites its planes with zeros below
+        if (in && p.P_out) {
 #pragma unroll
             for (int pp = 0; pp < NP; pp++) {
-                const float val = p.maintain ? diffuse5<NP, KT>(p.P, pp * KT + k, N, ru, rc, rd, xm, xc, xp, eps_p)
-                                             : __ldg(p.P + (size_t)(pp * KT + k) * N + i);
-                alpha = alpha && (!p.maintain || val > eps_p);
-                g[pp] = val;
+                const float val = alpha ? g[pp] : 0.f;
+                wrote_nz = wrote_nz || val != 0.f;
+                p.P_out[(size_t)(pp * KT + k) * N + i] = val;
             }
-            // the kernel's maintained genes go out now, while they are in
-            // registers (zeros once alpha is known false); a site that ends
-            // without alpha rewrites its planes with zeros below
-            if (in && p.P_out) {
-#pragma unroll
-                for (int pp = 0; pp < NP; pp++) {
-                    const float val = alpha ? g[pp] : 0.f;
-                    wrote_nz = wrote_nz || val != 0.f;
-                    p.P_out[(size_t)(pp * KT + k) * N + i] = val;
-                }
-            }
-            // ring weights and the potential
-            const float w1 = g[PK + 1], w2 = g[PK + 4];
-            const float b1 = w1 > 0.f ? g[PK + 2] : 0.f, b2 = w2 > 0.f ? g[PK + 5] : 0.f;
-            const float a1 = w1 > 0.f ? -0.5f * LOG2E / (w1 * w1) : 0.f;
-            const float a2 = w2 > 0.f ? -0.5f * LOG2E / (w2 * w2) : 0.f;
-            const float c1 = g[PK + 0], c2 = g[PK + 3];
-            float num = 0.f, den = 0.f;
-            const float* V = V0;
-#pragma unroll 4
-            for (int r = 0; r < NR; r++, V += N) {
-                const float xr = p.ring_x[r];
-                const float d1 = xr - c1, d2 = xr - c2;
-                const float kr = b1 * ex2_approx((d1 * d1) * a1) + b2 * ex2_approx((d2 * d2) * a2);
-                num = fmaf(kr, __ldg(V), num);
-                den = fmaf(kr, p.ring_cnt[r], den);
-            }
-            const float u = den > 0.f ? num / den : 0.f;
-            // growth (as in the other epilogues)
-            const float m = PMU >= 0 ? g[PMU >= 0 ? PMU : 0] : p.kt.mu[k];
-            const float sg = PSG >= 0 ? g[PSG >= 0 ? PSG : 0] : p.kt.sigma[k];
-            const float hh = PH >= 0 ? g[PH >= 0 ? PH : 0] : p.kt.h[k];
-            float gk = 0.f;
-            if (sg > 0.f) {
-                const float z = (u - m) / sg;
-                gk = expf(-0.5f * z * z);
-            }
-            const float t = p.alpha_on ? u : hh * gk;
-            tsum += t;
-            if (p.maintain) alpha = alpha && (t > eps_u);
-            const float G = p.growth_form == 0 ? hh * (2.f * gk - 1.f) : hh * gk;
-            const int d = p.kt.dst[k];
-#pragma unroll
-            for (int cc = 0; cc < CT; cc++)
-                if (cc == d) acc[cc] += G;
         }
+        // ring weights and the potential
+        const float w1 = g[PK + 1], w2 = g[PK + 4];
+        const float b1 = w1 > 0.f ? g[PK + 2] : 0.f, b2 = w2 > 0.f ? g[PK + 5] : 0.f;
+        const float a1 = w1 > 0.f ? -0.5f * LOG2E / (w1 * w1) : 0.f;
+        const float a2 = w2 > 0.f ? -0.5f * LOG2E / (w2 * w2) : 0.f;
+        const float c1 = g[PK + 0], c2 = g[PK + 3];
+        float num = 0.f, den = 0.f;
+        const float* V = V0;
+#pragma unroll 4
+        for (int r = 0; r < NR; r++, V += N) {
+            const float xr = p.ring_x[r];
+            const float d1 = xr - c1, d2 = xr - c2;
+            const float kr = b1 * ex2_approx((d1 * d1) * a1) + b2 * ex2_approx((d2 * d2) * a2);
+            num = fmaf(kr, __ldg(V), num);
+            den = fmaf(kr, p.ring_cnt[r], den);
+        }
+        const float u = den > 0.f ? num / den : 0.f;
+        // growth (as in the other epilogues)
+        const float m = PMU >= 0 ? g[PMU >= 0 ? PMU : 0] : p.kt.mu[k];
+        const float sg = PSG >= 0 ? g[PSG >= 0 ? PSG : 0] : p.kt.sigma[k];
+        const float hh = PH >= 0 ? g[PH >= 0 ? PH : 0] : p.kt.h[k];
+        float gk = 0.f;
+        if (sg > 0.f) {
+            const float z = (u - m) / sg;
+            gk = expf(-0.5f * z * z);
+        }
+        const float t = p.alpha_on ? u : hh * gk;
+        tsum += t;
+        if (p.maintain) alpha = alpha && (t > eps_u);
+        const float G = p.growth_form == 0 ? hh * (2.f * gk - 1.f) : hh * gk;
+        const int d = p.kt.dst[k];
+#pragma unroll
+        for (int cc = 0; cc < CT; cc++)
+            if (cc == d) acc[cc] += G;
     }
     if (!p.maintain) alpha = true;
     float st[CT * 5];
@@ -641,7 +680,7 @@ cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks)
     const bool rd1 = p.r_diff == 1 || !p.maintain;
     const bool r1 = rd1 && p.n_rings == 0;
     const int locr = loc | (p.p_kern >= 0 ? 8 : 0);
-    if (rd1 && p.n_rings > 0 && locr == 15 &&
+    if (rd1 && p.n_rings > 0 && locr == 15 && p.W >= RG_TILE_W && p.H >= RG_TILE_H &&
         ((p.n_rings == 24 && K == 15 && C == 3) || (p.n_rings == 24 && K == 1 && C == 1) ||
          (p.n_rings == 12 && K == 15 && C == 3))) {
         const dim3 rgrid((p.W + EP_TX - 1) / EP_TX, (p.H + RG_TY - 1) / RG_TY);
