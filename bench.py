@@ -106,13 +106,14 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload_config(ws, conv_path, size=2048):
-    """The benchmark workload, named by what it is (both arms print the same;
-    other sizes are profiling runs of the same recipe)."""
+def workload_config(ws, size=2048):
+    """The benchmark workload, named by what it is (both arms print the same
+    object; other sizes are profiling runs of the same recipe).  How an arm
+    computes it (its convolution path) goes beside the config, not in it."""
     return {"workload": WORKLOAD if size == 2048 else WORKLOAD.replace("2048x2048", f"{size}x{size}"),
             "height": size, "width": size, "channels": 3, "kernels": 15, "radius": 18,
             "gene_planes": 30, "worlds": ws, "parallelism": "replicas" if ws > 1 else "single",
-            "conv_path": conv_path, "l2": "inputs larger than L2 (A + P = 551 MB per world)"}
+            "l2": "inputs larger than L2 (A + P = 551 MB per world)"}
 
 
 def adjoint_leg(torch, lenia, inputs, stream):
@@ -389,7 +390,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 2048 * 2048 / v * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": workload_config(ws, "direct FP64 sums (CPU oracle)"),
+            "config": workload_config(ws), "conv_path": "direct FP64 sums (CPU oracle)",
             "cpu_baseline": {**cb, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -503,7 +504,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(ws, "fft" if path == lenia.CONV_FFT else "direct", args.size),
+        "config": workload_config(ws, args.size), "conv_path": "fft" if path == lenia.CONV_FFT else "direct",
         "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic,
