@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -32,6 +33,17 @@ WORKLOAD = "lenia 2048x2048, 3 channels, 15 shell kernels R=18, localized mu/sig
 # Algorithmic bytes per site-step: A read + write (3 channels x 4 B x 2) and
 # the 30 gene planes read + write (30 x 4 B x 2).
 ALG_BYTES_PER_SITE = 3 * 4 * 2 + 30 * 4 * 2
+
+
+def fft_flops(H, W, C, K):
+    """Flops of the FFT route per step, counted the standard way (a complex
+    FFT of n points 5 n log2 n, a real one half that): C forward real 2D
+    transforms; per kernel the spectral product (a real factor on W/2 + 1
+    columns) and one inverse real 2D transform."""
+    lw, lh = math.log2(W), math.log2(H)
+    rows = H * 2.5 * W * lw                     # real row transforms of one plane
+    cols = (W // 2 + 1) * 5.0 * H * lh          # complex column transforms of one half spectrum
+    return C * (rows + cols) + K * ((W // 2 + 1) * H * 2.0 + cols + rows)
 
 
 def _traffic(kernel: str):
@@ -104,6 +116,20 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(mx)) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fp32_line(prof, H, W, scalar_tflops, pair_tflops):
+    """FP32-pipe fraction of the FFT passes (arithmetic- and latency-bound,
+    not DRAM-bound) against the measured FMA peak."""
+    names = ("rows_r2c", "cols_conv", "rows_c2r")
+    ms = sum(prof[k][0] / max(1, prof[k][1]) for k in names if k in prof)
+    flops = fft_flops(H, W, 3, 15)
+    peak = max(scalar_tflops, pair_tflops)
+    achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    return {"peak_tflops": peak, "peak_kind": "measured (FMA chains on every SM)",
+            "peak_scalar_tflops": scalar_tflops, "peak_pair_tflops": pair_tflops,
+            "fft_passes": {"kernels": list(names), "flop_per_site": flops / (H * W), "ms": ms,
+                           "achieved_tflops": achieved, "frac": achieved / peak if peak > 0 else None}}
 
 
 def workload_config(ws, size=2048):
@@ -439,6 +465,9 @@ def run_ours(args):
         step(i)
     torch.cuda.synchronize()
     launches_per_step = lenia.lenia_launches_per_step(ctx)
+    # FP32 FMA throughput of this GPU, measured (the denominator of the FFT
+    # passes' FP32 fraction), before the timed region
+    fp32_scalar, fp32_pair = lenia.lenia_measure_fp32_peak(stream)
 
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
     lenia.lenia_profile_start(ctx, launches_per_step * args.steps + 8)
@@ -511,6 +540,7 @@ def run_ours(args):
                      "traffic_gbs": (traffic / (dom_ms / 1e3) / 1e9) if traffic else None,
                      "alg_bytes_per_site": ALG_BYTES_PER_SITE,
                      "step_frac": (ALG_BYTES_PER_SITE * sites * args.steps / (t_max / 1e3) / 1e9) / hbm},
+        "fp32": fp32_line(prof, H, W, fp32_scalar, fp32_pair),
         "kernels_ms": {k: {"avg_ms": v[0] / max(1, v[1]), "launches": v[1],
                            "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
                        for k, v in prof.items()},

@@ -29,8 +29,8 @@
  *     FFT intermediates, potentials, stats partials), allocated in lenia_init
  *     and freed in lenia_destroy.  After lenia_init only lenia_set_walls,
  *     the first lenia_step_evolve and the first host-buffer step allocate
- *     device memory (as documented there); lenia_stats_noalloc allocates
- *     nothing at all.
+ *     device memory (as documented there), and lenia_measure_fp32_peak
+ *     its own small buffer; lenia_stats_noalloc allocates nothing at all.
  *   - Errors: every entry point returns a status; nothing aborts and nothing
  *     is thrown.  Arguments are validated before any launch; a CUDA error
  *     seen after a launch returns LENIA_ECUDA.  lenia_last_error() gives a
@@ -243,6 +243,16 @@ LENIA_API lenia_status lenia_check(lenia_ctx* ctx, void* stream);
  * a streaming kernel would, so the next lenia_check returns LENIA_ETIMEOUT.
  * Nothing faults or traps; the context stays usable. */
 LENIA_API lenia_status lenia_selftest_wait_timeout(lenia_ctx* ctx, int32_t limit_mcycles, void* stream);
+
+/* Measurement helper (no counterpart in the paper): the FP32 throughput of
+ * the current device's CUDA cores in TFLOP/s, as the best of five timed
+ * launches of independent fused multiply-add chains on every SM, scalar
+ * (scalar_tflops) and on packed FP32 pairs (pair_tflops; one packed FMA
+ * counts four flops).  It is the denominator of the FP32-pipe fractions the
+ * benchmark reports beside the HBM roofline.  Synchronous: it allocates and
+ * frees a small device buffer and waits for `stream`.  Both outputs are host
+ * pointers and must be non-null (LENIA_EINVAL otherwise). */
+LENIA_API lenia_status lenia_measure_fp32_peak(double* scalar_tflops, double* pair_tflops, void* stream);
 
 /* lenia_step with HOST buffers: copies A_in/P_in host->device into library
  * buffers, steps, and copies A_out/P_out (and stats_out, C*3 floats, nullable)

@@ -173,6 +173,7 @@ cudaError_t launch_spectra(const double* Kd, int R, int H, int W, const double* 
 cudaError_t launch_selftest_wait(long long limit_cycles, int* status, cudaStream_t s);
 int adjoint_blocks(int H, int W);
 cudaError_t launch_adjoint_epilogue(const AdjParams& p, cudaStream_t s);
+cudaError_t measure_fp32_peak(cudaStream_t s, double* scalar_tflops, double* pair_tflops);
 cudaError_t launch_adjoint_gather(const AdjParams& p, cudaStream_t s);
 cudaError_t launch_adjoint_gene_out(const double* gene_acc, int nv, float* out, cudaStream_t s);
 bool epilogue_rows_supported(const EpiParams& p);

@@ -28,7 +28,7 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes", "lenia_batch_init",
            "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy",
            "lenia_selftest_wait_timeout", "lenia_set_walls", "lenia_step_evolve",
-           "lenia_step_host_async", "lenia_host_wait", "lenia_batch_group_of")
+           "lenia_step_host_async", "lenia_host_wait", "lenia_batch_group_of", "lenia_measure_fp32_peak")
 PROFILE_KINDS = 10
 
 
@@ -132,6 +132,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_profile_kind_name.restype = ctypes.c_char_p
     lib.lenia_stats_noalloc.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp]
     lib.lenia_stats_noalloc.restype = st
+    lib.lenia_measure_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+    lib.lenia_measure_fp32_peak.restype = st
     lib.lenia_batch_init.argtypes = [ctypes.c_int32, ctypes.POINTER(LeniaConfig), ctypes.POINTER(LeniaKernelDesc),
                                      ctypes.c_int32, vp, ctypes.POINTER(vp)]
     lib.lenia_batch_init.restype = st
@@ -230,6 +232,15 @@ def lenia_stats_noalloc(A, n_channels, height, width, out, stream=None):
                                     _stream(stream))
     if st != LENIA_OK:
         raise LeniaError(st, f"lenia_stats_noalloc: {load().lenia_status_string(st).decode()}")
+
+
+def lenia_measure_fp32_peak(stream=None):
+    """(scalar, packed-pair) FP32 FMA throughput of the current device, TFLOP/s."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = load().lenia_measure_fp32_peak(ctypes.byref(a), ctypes.byref(b), _stream(stream))
+    if st != LENIA_OK:
+        raise LeniaError(st, f"lenia_measure_fp32_peak: {load().lenia_status_string(st).decode()}")
+    return a.value, b.value
 
 
 def lenia_batch_init(worlds, autotune: bool = True, conv_path: int = CONV_AUTO, stream=None):
