@@ -237,6 +237,47 @@ def batched_leg(torch, lenia, inputs, stream, steps=200):
             "batched_over_plain": v / pv}
 
 
+def small_legs(torch, lenia, inputs, stream, fp32_peak=None):
+    """The two small configurations as rollouts through lenia_rollout: the
+    64^2 one-kernel world with global genes (100 steps; launch- and
+    latency-bound, reported in us per step) and the 1024^2 one-channel world
+    with localized mu/sigma (1000 steps; reported against the HBM and FP32
+    peaks; its state, ~12 MB, stays in L2)."""
+    out = {}
+    for name, w, steps in (("c1", inputs.single_kernel_global(), 100),
+                           ("c2", inputs.localized_single_channel(), 1000)):
+        cfg, ks = lenia.config_from_world(w)
+        ctx = lenia.lenia_init(cfg, ks, stream)
+        try:
+            a = torch.from_numpy(w.A).cuda()
+            p = torch.from_numpy(w.P).cuda() if w.P is not None else None
+            lenia.lenia_rollout(ctx, a, p, 10, None, stream)          # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lenia.lenia_rollout(ctx, a, p, steps, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lenia.lenia_check(ctx)
+            ms = e0.elapsed_time(e1)
+            path = lenia.lenia_conv_path(ctx)
+            lps = lenia.lenia_launches_per_step(ctx)
+        finally:
+            lenia.lenia_destroy(ctx)
+        v = w.sites * steps / (ms / 1e3)
+        alg = 8 + (16 if w.P is not None else 0)          # A in/out, plus mu and sigma in/out
+        r = {"workload": f"{w.height}x{w.width}, {w.n_channels} channel, {w.n_kernels} kernel R={w.kernels[0].radius}, "
+                         + ("localized mu/sigma, gene maintenance" if w.P is not None else "global genes"),
+             "steps": steps, "us_per_step": ms * 1e3 / steps, "value": v, "unit": UNIT,
+             "conv_path": "fft" if path == lenia.CONV_FFT else "direct", "launches_per_step": lps,
+             "alg_bytes_per_site": alg, "frac_of_hbm": v * alg / 1e9 / _peaks()[0]}
+        if fp32_peak and path == lenia.CONV_FFT:
+            fl = fft_flops(w.height, w.width, w.n_channels, w.n_kernels)
+            r["fp32_fft_frac_of_step"] = fl * steps / (ms / 1e3) / 1e12 / fp32_peak
+        out[name] = r
+    return out
+
+
 def evolve_leg(torch, lenia, inputs, stream, plain_ms, steps=100):
     """The headline world with Algorithm 2's evolutionary lines switched on:
     an 8-column wall, one mutation and one penalisation per step (seeded
@@ -558,6 +599,7 @@ def run_ours(args):
         line["batched"] = batched_leg(torch, lenia, inputs, stream)
         line["evolve"] = evolve_leg(torch, lenia, inputs, stream, t_max / args.steps)
         line["rings"] = rings_leg(torch, lenia, inputs, stream)
+        line["small"] = small_legs(torch, lenia, inputs, stream, max(fp32_scalar, fp32_pair))
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -574,10 +616,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched-world, evolution and ring legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched-world, evolution, ring and small-world legs")
     ap.add_argument("--size", type=int, default=2048, help="torus side (2048 = the benchmark workload)")
     ap.add_argument("--conv-path", type=int, default=0, help="0 auto, 1 fft, 2 direct")
-    ap.add_argument("--leg", default=None, choices=["adjoint", "batched", "evolve", "rings"],
+    ap.add_argument("--leg", default=None, choices=["adjoint", "batched", "evolve", "rings", "small"],
                     help="run only this extra leg (N = 1) and print its JSON object (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -601,6 +643,8 @@ def run_leg(args):
         out = batched_leg(torch, lenia, inputs, stream, steps=args.steps)
     elif args.leg == "evolve":
         out = evolve_leg(torch, lenia, inputs, stream, None, steps=args.steps)
+    elif args.leg == "small":
+        out = small_legs(torch, lenia, inputs, stream, max(lenia.lenia_measure_fp32_peak(stream)))
     else:
         out = rings_leg(torch, lenia, inputs, stream, steps=args.steps)
     print(json.dumps({"leg": args.leg, **out}), flush=True)
