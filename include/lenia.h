@@ -150,7 +150,10 @@ LENIA_API lenia_status lenia_step(lenia_ctx* ctx, const float* A_in, const float
 
 /* n_steps steps in place on A (and P): the state ping-pongs through
  * library-owned buffers and ends in the caller's.  stats_out (nullable,
- * device) receives n_steps * C * 3 floats, step s at offset s*C*3. */
+ * device) receives n_steps * C * 3 floats, step s at offset s*C*3.
+ * Without stats_out and with n_steps >= 4, pairs of steps replay a CUDA
+ * graph that the context captures for its (A, P) pointers and genes (the
+ * first such call captures it; calls with other buffers capture again). */
 LENIA_API lenia_status lenia_rollout(lenia_ctx* ctx, float* A, float* P, int32_t n_steps,
                            float* stats_out, void* stream);
 
@@ -164,14 +167,16 @@ LENIA_API lenia_status lenia_rollout(lenia_ctx* ctx, float* A, float* P, int32_t
  * clip subgradient 1 iff 0 < pre-clip < 1, growth derivative, and the
  * transposed convolution, which for the point-symmetric K~ is the same
  * convolution.  P0 must be NULL.  Returns LENIA_ENOTSUP when the context has
- * no adjoint buffers or has gene maps. */
+ * no adjoint buffers or has gene maps.  A0 and gA_T are copied into library
+ * buffers first and the results copied out last; the pass between runs as a
+ * CUDA graph captured once per (n_steps, genes) and replayed afterwards. */
 LENIA_API lenia_status lenia_backward(lenia_ctx* ctx, const float* A0, const float* P0, int32_t n_steps,
                             const float* gA_T, float* gA0, float* g_genes, void* stream);
 
 /* Replace the global growth genes: genes is a HOST array [K][3] of
  * (mu, sigma, h) per kernel (sigma > 0 unless sigma is localized).  The
  * kernels' shapes and spectra are unchanged.  Takes effect for work
- * enqueued after the call. */
+ * enqueued after the call (graphs captured with the old genes are redone). */
 LENIA_API lenia_status lenia_set_genes(lenia_ctx* ctx, const float* genes);
 
 /* Mass, circular-mean centre y, centre x of each channel of A: out is a

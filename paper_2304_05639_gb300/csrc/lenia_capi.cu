@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <array>
 #include <string>
 #include <vector>
 
@@ -87,6 +88,16 @@ struct lenia_ctx {
     bool host_pending = false;             // a download has been enqueued since the last wait
     // optional per-launch timing (lenia_profile_start / lenia_profile_stop)
     bool prof = false;
+    // rollouts and backward passes as CUDA graphs, captured on a private
+    // stream and replayed while the call's arguments and the genes are
+    // unchanged (kernel parameters carry the genes and the pointers)
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        std::array<uintptr_t, 7> key{};
+    };
+    cudaStream_t cap_stream = nullptr;
+    GraphSlot g_rollout, g_backward;
+    uint64_t genes_version = 0;            // bumped by lenia_set_genes
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kind;
     size_t ev_used = 0;
@@ -509,7 +520,9 @@ void lenia_destroy(lenia_ctx* c)
     for (int b = 0; b < 2; b++)
         for (cudaEvent_t e : {c->ev_up[b], c->ev_done[b], c->ev_down[b]})
             if (e) cudaEventDestroy(e);
-    for (cudaStream_t t : {c->up_stream, c->down_stream})
+    for (cudaGraphExec_t g : {c->g_rollout.exec, c->g_backward.exec})
+        if (g) cudaGraphExecDestroy(g);
+    for (cudaStream_t t : {c->up_stream, c->down_stream, c->cap_stream})
         if (t) cudaStreamDestroy(t);
     delete c;
 }
@@ -799,12 +812,45 @@ lenia_status lenia_step(lenia_ctx* c, const float* A_in, const float* P_in, floa
     return step_impl(c, A_in, P_in, A_out, P_out, stats_out, nullptr, nullptr, (cudaStream_t)stream);
 }
 
-lenia_status lenia_rollout(lenia_ctx* c, float* A, float* P, int32_t n_steps, float* stats_out, void* stream)
+// Runs body(stream) as a CUDA graph: captured once on the private stream for
+// a key (the call's arguments and the genes version), then launched on s.
+// Capturing enqueues nothing.  While per-launch profiling is on, or if a
+// capture fails, body runs directly on s.
+extern "C++" {
+template <class Body>
+static lenia_status run_graph(lenia_ctx* c, lenia_ctx::GraphSlot& slot, const std::array<uintptr_t, 7>& key,
+                              cudaStream_t s, Body body)
 {
-    if (!c) return LENIA_EINVAL;
-    if (n_steps < 0) return fail(c, LENIA_EINVAL, "n_steps must be >= 0");
-    if (!A || (c->n_p && !P)) return fail(c, LENIA_EINVAL, "A (and P with localized genes) must be non-null");
-    cudaStream_t s = (cudaStream_t)stream;
+    if (c->prof) return body(s);
+    if (!(slot.exec && slot.key == key)) {
+        if (slot.exec) {
+            cudaGraphExecDestroy(slot.exec);
+            slot.exec = nullptr;
+        }
+        if (!c->cap_stream) CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const lenia_status st = body(c->cap_stream);
+            ok = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess && st == LENIA_OK && g;
+            if (ok) ok = cudaGraphInstantiate(&slot.exec, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+        }
+        if (!ok) {
+            slot.exec = nullptr;
+            (void)cudaGetLastError();
+            c->err.clear();
+            return body(s);
+        }
+        slot.key = key;
+    }
+    CUDA_OR_FAIL(c, cudaGraphLaunch(slot.exec, s));
+    return LENIA_OK;
+}
+}  // extern "C++"
+
+static lenia_status rollout_body(lenia_ctx* c, float* A, float* P, int32_t n_steps, float* stats_out, cudaStream_t s)
+{
     const size_t stride = (size_t)c->cfg.n_channels * 3;
     for (int t = 0; t < n_steps; t++) {
         const bool even = (t % 2) == 0;
@@ -826,24 +872,40 @@ lenia_status lenia_rollout(lenia_ctx* c, float* A, float* P, int32_t n_steps, fl
     return LENIA_OK;
 }
 
-lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int32_t n_steps, const float* gA_T,
-                            float* gA0, float* g_genes, void* stream)
+lenia_status lenia_rollout(lenia_ctx* c, float* A, float* P, int32_t n_steps, float* stats_out, void* stream)
 {
     if (!c) return LENIA_EINVAL;
-    if (!c->adj)
-        return fail(c, LENIA_ENOTSUP,
-                    "lenia_backward needs global genes and a context made with max_rollout_steps > 0");
-    if (!A0 || !gA_T) return fail(c, LENIA_EINVAL, "A0 and gA_T must be non-null");
-    if (P0) return fail(c, LENIA_EINVAL, "P0 must be NULL: the adjoint covers global genes only");
-    if (n_steps < 1 || n_steps > c->max_steps) return fail(c, LENIA_EINVAL, "n_steps must be 1..max_rollout_steps");
+    if (n_steps < 0) return fail(c, LENIA_EINVAL, "n_steps must be >= 0");
+    if (!A || (c->n_p && !P)) return fail(c, LENIA_EINVAL, "A (and P with localized genes) must be non-null");
+    if (n_steps == 0) return LENIA_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    // per-step statistics go to per-step addresses, and short rollouts do not
+    // repay a capture: launch directly
+    if (stats_out || n_steps < 4) return rollout_body(c, A, P, n_steps, stats_out, s);
+    // otherwise pairs of steps replay one cached two-step graph (the state is
+    // back in A, P after each pair); an odd last step runs directly
+    const std::array<uintptr_t, 7> key{(uintptr_t)A, (uintptr_t)P, (uintptr_t)c->genes_version, 2, 0, 0, 0};
+    for (int i = 0; i < n_steps / 2; i++) {
+        const lenia_status st =
+            run_graph(c, c->g_rollout, key, s, [&](cudaStream_t t) { return rollout_body(c, A, P, 2, nullptr, t); });
+        if (st != LENIA_OK) return st;
+    }
+    return (n_steps % 2) ? rollout_body(c, A, P, 1, nullptr, s) : LENIA_OK;
+}
+
+// The backward's work, enqueued on s (a fixed sequence of launches and
+// copies for given arguments: no host decision depends on device data).
+// Reads A_0 from the first checkpoint slot and dL/dA_T from d_gA[0]; leaves
+// dL/dA_0 in d_gA[n_steps % 2] (one buffer swap per reversed step) and the
+// FP64 gene gradients in d_gene_acc, so that it touches library buffers only.
+static lenia_status backward_body(lenia_ctx* c, int32_t n_steps, cudaStream_t s)
+{
     const int C = c->cfg.n_channels, K = c->cfg.n_kernels, L = c->ckpt;
     const size_t nA = c->N * C;
     auto ckpt = [&](int j) { return c->d_ckpt + (size_t)j * nA; };
     auto seg = [&](int j) { return c->d_seg + (size_t)j * nA; };
 
     // forward pass, keeping the states at multiples of the checkpoint interval
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(ckpt(0), A0, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
     const float* prev = ckpt(0);
     if (L == 1) {
         // every state and every step's potentials kept: reverse directly
@@ -855,7 +917,6 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
             if (st != LENIA_OK) return st;
         }
         CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_gene_acc, 0, (size_t)K * 3 * sizeof(double), s));
-        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_gA[0], gA_T, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
         int cur = 0;
         for (int t = n_steps - 1; t >= 0; t--) {
             AdjParams ap;
@@ -881,8 +942,6 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
             if (!per_channel) CUDA_OR_FAIL(c, launch_adjoint_gather(ap, s));
             cur ^= 1;
         }
-        if (gA0) CUDA_OR_FAIL(c, cudaMemcpyAsync(gA0, c->d_gA[cur], nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
-        if (g_genes) CUDA_OR_FAIL(c, launch_adjoint_gene_out(c->d_gene_acc, K * 3, g_genes, s));
         return LENIA_OK;
     }
     for (int t = 0; t + 1 < n_steps; t++) {
@@ -895,7 +954,6 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
     // states and their potentials from its checkpoint, then apply the step
     // adjoint in reverse
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_gene_acc, 0, (size_t)K * 3 * sizeof(double), s));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_gA[0], gA_T, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
     auto useg = [&](int j) { return c->d_Useg + (size_t)j * K * c->N; };
     int cur = 0;
     const int n_seg = (n_steps + L - 1) / L;
@@ -934,6 +992,31 @@ lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int3
             cur ^= 1;
         }
     }
+    return LENIA_OK;
+}
+
+lenia_status lenia_backward(lenia_ctx* c, const float* A0, const float* P0, int32_t n_steps, const float* gA_T,
+                            float* gA0, float* g_genes, void* stream)
+{
+    if (!c) return LENIA_EINVAL;
+    if (!c->adj)
+        return fail(c, LENIA_ENOTSUP,
+                    "lenia_backward needs global genes and a context made with max_rollout_steps > 0");
+    if (!A0 || !gA_T) return fail(c, LENIA_EINVAL, "A0 and gA_T must be non-null");
+    if (P0) return fail(c, LENIA_EINVAL, "P0 must be NULL: the adjoint covers global genes only");
+    if (n_steps < 1 || n_steps > c->max_steps) return fail(c, LENIA_EINVAL, "n_steps must be 1..max_rollout_steps");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = c->cfg.n_kernels;
+    const size_t nA = c->N * c->cfg.n_channels;
+    // the arguments go in and out by copies on s, so that the graph of the
+    // pass itself depends only on n_steps and the genes
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_ckpt, A0, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->d_gA[0], gA_T, nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    const std::array<uintptr_t, 7> key{(uintptr_t)n_steps, (uintptr_t)c->genes_version, 1, 0, 0, 0, 0};
+    const lenia_status st =
+        run_graph(c, c->g_backward, key, s, [&](cudaStream_t t) { return backward_body(c, n_steps, t); });
+    if (st != LENIA_OK) return st;
+    const int cur = n_steps & 1;
     if (gA0) CUDA_OR_FAIL(c, cudaMemcpyAsync(gA0, c->d_gA[cur], nA * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (g_genes) CUDA_OR_FAIL(c, launch_adjoint_gene_out(c->d_gene_acc, K * 3, g_genes, s));
     return LENIA_OK;
@@ -953,6 +1036,7 @@ lenia_status lenia_set_genes(lenia_ctx* c, const float* genes)
         c->kd[k].sigma = c->kt.sigma[k] = genes[3 * k + 1];
         c->kd[k].h = c->kt.h[k] = genes[3 * k + 2];
     }
+    c->genes_version++;                    // kernels captured with the old genes are stale
     return LENIA_OK;
 }
 
