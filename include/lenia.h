@@ -30,7 +30,9 @@
  *     and freed in lenia_destroy.  After lenia_init only lenia_set_walls,
  *     the first lenia_step_evolve and the first host-buffer step allocate
  *     device memory (as documented there), and lenia_measure_fp32_peak
- *     its own small buffer; lenia_stats_noalloc allocates nothing at all.
+ *     its own small buffer; instantiating the CUDA graphs of lenia_rollout
+ *     and lenia_backward lets the driver reserve memory for them;
+ *     lenia_stats_noalloc allocates nothing at all.
  *   - Errors: every entry point returns a status; nothing aborts and nothing
  *     is thrown.  Arguments are validated before any launch; a CUDA error
  *     seen after a launch returns LENIA_ECUDA.  lenia_last_error() gives a
