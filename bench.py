@@ -8,8 +8,13 @@ diffusion + growth + alpha mask + clipped update, and per-channel stats.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-on the host cores over a bounded sample of the same workload.
+Prints one JSON line (rank 0): the step's throughput, the dominant kernel's
+HBM roofline (with its ncu DRAM traffic), the FFT passes against the
+measured FP32 peak, an end-to-end serving loop through host buffers, clocks
+sampled during the timed region, the CPU oracle baseline, and (N = 1) the
+adjoint, batched-world, evolution, ring and small-world legs (--leg NAME
+runs one alone).  --impl reference times the FP64 CPU oracle on the host
+cores over a bounded sample of the same workload.
 """
 from __future__ import annotations
 
