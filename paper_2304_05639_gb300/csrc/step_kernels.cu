@@ -358,8 +358,9 @@ __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
 // diffusion reads them there.  The kernel's ring weights come from its
 // diffused kernel genes with the hardware base-2 exponential,
 // k_r = sum_i b_i 2^(-(r/n - r_i)^2 log2(e) / (2 w_i^2)), and its potential
-// from the channel's ring potentials (L1 hits after the channel's first
-// kernel).  The maintained genes are written as soon as they are diffused;
+// from the channel's ring potentials, which each thread copies for its own
+// site with cp.async into dynamic shared memory (n_rings x 256 floats) once
+// per channel, right after the previous channel's last use.  The maintained genes are written as soon as they are diffused;
 // a site that ends without alpha rewrites them with zeros.  Needs
 // W >= RG_TILE_W and H >= RG_TILE_H (one wrap per halo coordinate).
 constexpr int RG_TY = 8;     // rows per block of the ring epilogue (one site per thread)
@@ -380,6 +381,7 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
     constexpr int TP = RG_TILE_H * RG_TILE_W;           // floats per staged plane
     __shared__ float tile[2][NP * TP];
     __shared__ int ord[KT];
+    extern __shared__ float vst[];                      // [NR][256]: each thread's own ring potentials
     const int H = p.H, W = p.W;
     const size_t N = (size_t)H * W;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -420,6 +422,16 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
                 if (p.kt.src[k] == c) ord[n++] = k;
     }
     __syncthreads();
+    const int tid = ty * EP_TX + tx;
+    // the thread's own ring potentials of one channel (no block barrier needed:
+    // the thread that copies them is the one that reads them)
+    auto stage_v = [&](int c) {
+        const float* Vc = p.U + (size_t)c * NR * N + i;
+#pragma unroll
+        for (int r = 0; r < NR; r++) cp_async4(&vst[r * 256 + tid], Vc + (size_t)r * N);
+        cp_async_commit();
+    };
+    stage_v(p.kt.src[ord[0]]);
     stage(ord[0], tile[0]);
 
     bool alpha = true;
@@ -437,9 +449,6 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
         __syncthreads();            // kernel j staged; every thread is done with kernel j - 1's buffer
         if (j + 1 < KT) stage(ord[j + 1], tile[(j + 1) & 1]);
         const float* T = tile[j & 1];
-        // the channel's ring potentials: read again by each kernel of the
-        // channel (L1 hits after the first)
-        const float* V0 = p.U + (size_t)c * NR * N + i;
         float g[NP];
 #pragma unroll
         for (int pp = 0; pp < NP; pp++) {
@@ -475,16 +484,18 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
         const float a1 = w1 > 0.f ? -0.5f * LOG2E / (w1 * w1) : 0.f;
         const float a2 = w2 > 0.f ? -0.5f * LOG2E / (w2 * w2) : 0.f;
         const float c1 = g[PK + 0], c2 = g[PK + 3];
+        // the channel's ring potentials, staged in shared memory for its kernels
         float num = 0.f, den = 0.f;
-        const float* V = V0;
 #pragma unroll 4
-        for (int r = 0; r < NR; r++, V += N) {
+        for (int r = 0; r < NR; r++) {
             const float xr = p.ring_x[r];
             const float d1 = xr - c1, d2 = xr - c2;
             const float kr = b1 * ex2_approx((d1 * d1) * a1) + b2 * ex2_approx((d2 * d2) * a2);
-            num = fmaf(kr, __ldg(V), num);
+            num = fmaf(kr, vst[r * 256 + tid], num);
             den = fmaf(kr, p.ring_cnt[r], den);
         }
+        // the channel's last kernel: fetch the next channel's potentials now
+        if (j + 1 < KT && p.kt.src[ord[j + 1]] != c) stage_v(p.kt.src[ord[j + 1]]);
         const float u = den > 0.f ? num / den : 0.f;
         // growth (as in the other epilogues)
         const float m = PMU >= 0 ? g[PMU >= 0 ? PMU : 0] : p.kt.mu[k];
@@ -686,9 +697,19 @@ cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks)
         const dim3 rgrid((p.W + EP_TX - 1) / EP_TX, (p.H + RG_TY - 1) / RG_TY);
         if (n_blocks) *n_blocks = rgrid.x * rgrid.y;
         const dim3 rblock(EP_TX, RG_TY);
-        if (p.n_rings == 24 && K == 15) k_epilogue_rings<15, 3, 24, 15><<<rgrid, rblock, 0, s>>>(p);
-        else if (p.n_rings == 24) k_epilogue_rings<1, 1, 24, 15><<<rgrid, rblock, 0, s>>>(p);
-        else k_epilogue_rings<15, 3, 12, 15><<<rgrid, rblock, 0, s>>>(p);
+        const size_t vb = (size_t)p.n_rings * 256 * sizeof(float);
+        cudaError_t e = cudaSuccess;
+        if (p.n_rings == 24 && K == 15) {
+            e = smem_limit<k_epilogue_rings<15, 3, 24, 15>>(vb);
+            if (e == cudaSuccess) k_epilogue_rings<15, 3, 24, 15><<<rgrid, rblock, vb, s>>>(p);
+        } else if (p.n_rings == 24) {
+            e = smem_limit<k_epilogue_rings<1, 1, 24, 15>>(vb);
+            if (e == cudaSuccess) k_epilogue_rings<1, 1, 24, 15><<<rgrid, rblock, vb, s>>>(p);
+        } else {
+            e = smem_limit<k_epilogue_rings<15, 3, 12, 15>>(vb);
+            if (e == cudaSuccess) k_epilogue_rings<15, 3, 12, 15><<<rgrid, rblock, vb, s>>>(p);
+        }
+        if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
     if (r1 && K == 15 && C == 3 && loc == 3) k_epilogue_r1<15, 3, 3><<<grid, block, 0, s>>>(p);
