@@ -78,6 +78,9 @@ __global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
     // X[k] = E[k] + w_W^k O[k], E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i
     // Output column kx holds rows y0 .. y0 + NB - 1 contiguously (b fastest).
     float2* outc = p.Ahat + (size_t)c * M * p.H + y0;
+    // four pairs per thread in flight (their twiddle loads overlap): 0.035 ->
+    // 0.033 ms at 2048^2, although the registers rise from 80 to 90
+#pragma unroll 4
     for (int u = threadIdx.x; u < NB * (M / 2 + 1); u += T) {
         const int b = u % NB;
         const int k = u / NB;
