@@ -95,6 +95,16 @@ def test_status_strings(lib):
     lib.lenia_destroy(None)               # no-op
 
 
+def test_context_free_entry_points_validate_on_the_host(lib):
+    """Null outputs and null contexts are rejected before any CUDA call."""
+    d = ctypes.c_double(0.0)
+    assert lib.lenia_measure_fp32_peak(None, ctypes.byref(d), None) == lenia.LENIA_EINVAL
+    assert lib.lenia_measure_fp32_peak(ctypes.byref(d), None, None) == lenia.LENIA_EINVAL
+    assert lib.lenia_rollout(None, None, None, 1, None, None) == lenia.LENIA_EINVAL
+    assert lib.lenia_backward(None, None, None, 1, None, None, None, None) == lenia.LENIA_EINVAL
+    assert lib.lenia_step_host_async(None, None, None, None, None, None, None) == lenia.LENIA_EINVAL
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """The ctypes mirrors of lenia_config, lenia_kernel_desc and lenia_events
     have the C compiler's sizes and field offsets."""
