@@ -2,11 +2,17 @@
 
 Workload: the 2048 x 2048, 3-channel, 15-kernel (R = 18) world with
 localized mu/sigma gene maps and gene maintenance on (seeded synthetic
-input shaped like the paper's runs).  One step = one pass of the whole hot
-path: row FFTs, column FFT x kernel spectra x inverse, inverse row FFTs,
-diffusion + growth + alpha mask + clipped update, and per-channel stats.
+input shaped like the paper's runs: 16 genotype patches whose genes are
+matched to their noise, so the patch interiors pass every kernel's growth
+test).  One step = one pass of the whole hot path: row FFTs, column FFT x
+kernel spectra x inverse, inverse row FFTs, diffusion + growth + alpha mask
++ clipped update, and per-channel stats.  Every timed step advances the same
+live state by one step (inputs 551 MB, larger than L2).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 and no torchrun environment the script starts N ranks
+itself (torch.distributed.run on 127.0.0.1), one replica world per GPU.
 
 Prints one JSON line (rank 0): the step's throughput, the dominant kernel's
 HBM roofline (with its ncu DRAM traffic), the FFT passes against the
@@ -34,7 +40,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s at 2048^2 FP32 (% HBM roofline); batched & adjoint vs plain step"
 UNIT = "cell-updates/s"
-WORKLOAD = "lenia 2048x2048, 3 channels, 15 shell kernels R=18, localized mu/sigma maps, gene maintenance"
+WORKLOAD = ("lenia 2048x2048, 3 channels, 15 shell kernels R=18, localized mu/sigma maps (16 genotype "
+            "patches matched to their noise), gene maintenance")
 # Algorithmic bytes per site-step: A read + write (3 channels x 4 B x 2) and
 # the 30 gene planes read + write (30 x 4 B x 2).
 ALG_BYTES_PER_SITE = 3 * 4 * 2 + 30 * 4 * 2
@@ -144,7 +151,8 @@ def workload_config(ws, size=2048):
     return {"workload": WORKLOAD if size == 2048 else WORKLOAD.replace("2048x2048", f"{size}x{size}"),
             "height": size, "width": size, "channels": 3, "kernels": 15, "radius": 18,
             "gene_planes": 30, "worlds": ws, "parallelism": "replicas" if ws > 1 else "single",
-            "l2": "inputs larger than L2 (A + P = 551 MB per world)"}
+            "l2": "inputs larger than L2 (A + P = 551 MB per world)",
+            "state": "each timed step advances the same live state (A0, P0) by one step"}
 
 
 def adjoint_leg(torch, lenia, inputs, stream):
@@ -287,7 +295,7 @@ def evolve_leg(torch, lenia, inputs, stream, plain_ms, steps=100):
     """The headline world with Algorithm 2's evolutionary lines switched on:
     an 8-column wall, one mutation and one penalisation per step (seeded
     events, r_oxy = 4, square half-size 16), against the plain step."""
-    w = inputs.multi_channel()
+    w = inputs.multi_channel(matched=True)
     H, W = w.height, w.width
     cfg, ks = lenia.config_from_world(w)
     ctx = lenia.lenia_init(cfg, ks, stream)
@@ -415,7 +423,7 @@ class OracleSample:
         from paper_2304_05639_gb300 import inputs
         oracle.build()
         self.oracle, self.inputs = oracle, inputs
-        self.world = inputs.multi_channel()
+        self.world = inputs.multi_channel(matched=True)
         self.rng = inputs.Rng(99)
         self.rate = None
 
@@ -444,6 +452,11 @@ def cpu_baseline(seconds_target: float = 15.0):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, each timed step a
+    bounded random sample of the workload's sites (one step each).  value is
+    sites per second over the timed samples; ms_per_step is the measured time
+    of one sampled step, and the time a full 2048^2 step would take at that
+    rate is given beside it, labelled as extrapolated."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -459,10 +472,13 @@ def run_reference(args):
     v = len(vals) * n / tot
     cb = s.describe(n * len(vals), tot)
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 2048 * 2048 / v * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": tot / len(vals) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": workload_config(ws), "conv_path": "direct FP64 sums (CPU oracle)",
+            "sites_per_step": n,
+            "step_sample": f"each timed step is {n} random sites of the 2048^2 workload (not the whole torus)",
+            "ms_per_full_step_extrapolated": 2048 * 2048 / v * 1e3,
             "cpu_baseline": {**cb, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -487,9 +503,9 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     if args.size == 2048:
-        world = inputs.multi_channel()
+        world = inputs.multi_channel(matched=True)
     else:   # same recipe on a smaller torus (profiling captures)
-        world = inputs.multi_channel(H=args.size, W=args.size, patch=max(16, args.size // 8))
+        world = inputs.multi_channel(H=args.size, W=args.size, patch=max(16, args.size // 8), matched=True)
     cfg, ks = lenia.config_from_world(world, args.conv_path)
     stream = torch.cuda.current_stream(dev)
     ctx = lenia.lenia_init(cfg, ks, stream)
@@ -500,23 +516,23 @@ def run_ours(args):
     A2, P2 = torch.empty_like(A), torch.empty_like(P)
     stats = torch.zeros((args.steps + args.warmup, world.n_channels, 3), dtype=torch.float32, device=dev)
 
-    bufs = [(A, P), (A2, P2)]
-
+    # every step advances the same live state (A, P) into (A2, P2): the
+    # inputs (551 MB) are larger than L2, so no step reads them from cache
     def step(i):
-        a_in, p_in = bufs[i % 2]
-        a_out, p_out = bufs[(i + 1) % 2]
-        lenia.lenia_step(ctx, a_in, p_in, a_out, p_out, stats[i], stream)
+        lenia.lenia_step(ctx, A, P, A2, P2, stats[i], stream)
 
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
     launches_per_step = lenia.lenia_launches_per_step(ctx)
+    # sites whose genes survive the step (alpha = 1)
+    alpha1 = int((P2 != 0).all(dim=0).all(dim=0).sum()) if P2.numel() else 0
     # FP32 FMA throughput of this GPU, measured (the denominator of the FFT
     # passes' FP32 fraction), before the timed region
     fp32_scalar, fp32_pair = lenia.lenia_measure_fp32_peak(stream)
 
+    # the timed region: plain steps, no per-launch events
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
-    lenia.lenia_profile_start(ctx, launches_per_step * args.steps + 8)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -529,8 +545,16 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
-    prof = lenia.lenia_profile_stop(ctx)
     clk = clocks.stop() if clocks else None
+
+    # a second, separate region times each launch (CUDA events around every
+    # launch on the launching stream) for the per-kernel figures
+    prof_steps = min(args.steps, 200)
+    lenia.lenia_profile_start(ctx, launches_per_step * prof_steps + 8)
+    for i in range(prof_steps):
+        step(i)
+    torch.cuda.synchronize()
+    prof = lenia.lenia_profile_stop(ctx)
 
     # end to end through the public host-buffer entry points: a serving loop of
     # independent host worlds (pinned buffers), each step uploading its
@@ -598,6 +622,8 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "stats_finite": ok_stats,
+        "alpha1_sites": alpha1,
+        "kernel_profile": f"per-launch CUDA events over {prof_steps} steps after the timed region",
     }
     if not args.no_extras and ws == 1 and args.size == 2048:
         line["adjoint"] = adjoint_leg(torch, lenia, inputs, stream)
@@ -613,9 +639,45 @@ def run_ours(args):
     return 0
 
 
+def spawn_ranks(argv, gpus):
+    """--gpus N > 1 outside a torchrun environment: start N ranks of this
+    script with torch.distributed.run on 127.0.0.1 and return their exit
+    status (None when nothing needs spawning)."""
+    if gpus <= 1 or "WORLD_SIZE" in os.environ:
+        return None
+    import socket
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
+
+
+def run_rank_check(args):
+    """CPU check of the rank plumbing (gloo, no GPU): every rank reports a
+    made-up time (10 + rank ms), rank 0 prints the max over ranks, the world
+    size and the job value the GPU path would compute from them."""
+    import torch
+    import torch.distributed as dist
+    ws, rank, _ = _dist()
+    if ws > 1:
+        dist.init_process_group("gloo")
+    t_max = max_over_ranks([10.0 + rank], torch)[0]
+    if rank == 0:
+        print(json.dumps({"n_gpus": ws, "ms_max": t_max, "value": job_value(ws, 1000, 1, t_max)}), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--rank-check", action="store_true",
+                    help="check the multi-rank plumbing on CPU (gloo) and exit")
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -629,6 +691,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    rc = spawn_ranks(sys.argv[1:], args.gpus)
+    if rc is not None:
+        return rc
+    if args.rank_check:
+        return run_rank_check(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.leg:

@@ -309,16 +309,23 @@ LENIA_API const char* lenia_profile_kind_name(int32_t kind);
  * Scratch: a file-scope static __device__ array of 2.75 MB inside
  * liblenia.so, held on every GPU that loads the library until the process
  * exits.  Limits: 1 <= C <= 8, 1 <= H, W <= 8192 and
- * ceil(W/32) * ceil(H/8) * C <= 65536 (for example 2048 x 2048 with 3
- * channels); larger requests return LENIA_EINVAL with a message on stderr
- * before any launch.
- * The first call on each device (with that device current) looks up the
- * array's device address with cudaGetSymbolAddress; make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * last call's contents; every value a call reads is written earlier in the
- * same call, so nothing needs clearing.  Calls whose work overlaps on the
- * GPU (different streams, or different host threads) race on the array:
- * serialise them.  Returns LENIA_ECUDA if a launch fails. */
+ * ceil(W/32) * ceil(H/32) * C <= 65536 (blocks of 32 x 32 sites times
+ * channels; for example 2048 x 2048 with 3 channels, or 8192 x 8192 with
+ * one); larger requests return LENIA_EINVAL with a message on stderr before
+ * any launch.
+ * Each call made outside stream capture looks the array's device address up
+ * in the current context (cudaGetSymbolAddress, with that device current; a
+ * lookup, no allocation), so a context that was reset (cudaDeviceReset) or
+ * replaced since the previous call is handled.  A call whose stream is
+ * capturing reuses the address of the device's last lookup: make the first
+ * call on each device before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents; every value a call reads is
+ * written earlier in the same call, so nothing needs clearing.  Calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race on the array: serialise them.  The result equals lenia_stats to
+ * rounding, not bit for bit (its sine/cosine tables are computed on the
+ * device here and on the host there).  Returns LENIA_ECUDA if a launch
+ * fails. */
 LENIA_API lenia_status lenia_stats_noalloc(const float* A, int32_t n_channels, int32_t height,
                                            int32_t width, float* out, void* stream);
 

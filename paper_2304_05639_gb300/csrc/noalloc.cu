@@ -29,19 +29,29 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the array on the current device (set up once per device).
-cudaError_t scratch_address(void** out)
+// Device address of the array in the current device's current context.  The
+// address is looked up again (cudaGetSymbolAddress: a lookup, no allocation)
+// on every call whose stream is not capturing, so a context that was reset
+// (cudaDeviceReset) or replaced since the last call gets its own address; a
+// capturing stream reuses the address of the device's last such lookup, which
+// is why the first call on a device must come before any capture.
+cudaError_t scratch_address(cudaStream_t s, void** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = p;
+    } else if (!g_scratch_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
@@ -85,17 +95,17 @@ extern "C" lenia_status lenia_stats_noalloc(const float* A, int32_t n_channels, 
     if (records > kNoAllocMaxRecords) {
         fprintf(stderr,
                 "lenia_stats_noalloc: world too large for the static scratch "
-                "(ceil(W/32) * ceil(H/8) * channels = %lld > %d)\n",
+                "(ceil(W/32) * ceil(H/32) * channels = %lld > %d)\n",
                 records, kNoAllocMaxRecords);
         return LENIA_EINVAL;
     }
+    cudaStream_t s = (cudaStream_t)stream;
     void* base = nullptr;
-    cudaError_t e = scratch_address(&base);
+    cudaError_t e = scratch_address(s, &base);
     if (e != cudaSuccess) {
-        fprintf(stderr, "lenia_stats_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+        fprintf(stderr, "lenia_stats_noalloc: scratch address lookup: %s\n", cudaGetErrorString(e));
         return LENIA_ECUDA;
     }
-    cudaStream_t s = (cudaStream_t)stream;
     double* partials = (double*)base;
     float* trig = (float*)(partials + kPartialDoubles);
     const int H = height, W = width, C = n_channels;

@@ -31,6 +31,7 @@ GROWTH_PAPER = 1       # h*exp(-(u-m)^2/(2 s^2))   (Section 2.4 form)
 LOC_MU, LOC_SIGMA, LOC_H = 1, 2, 4
 LOC_KERNEL = 8         # ring-wise kernel genes r1, w1, b1, r2, w2, b2 (six planes)
 KERNEL_SHELLS, KERNEL_BUMPS = 0, 1
+HALF_HEIGHT = 1.1774100225154747   # sqrt(2 ln 2): where exp(-z^2 / 2) = 1/2
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -189,11 +190,21 @@ def localized_single_channel(H=1024, W=1024, R=12, patch=128, n_geno=16,
 def multi_channel(H=2048, W=2048, R=18, patch=256, n_geno=16, seed_index=2,
                   dt=0.2, n_channels=3, localized=LOC_MU | LOC_SIGMA,
                   maintain=1, name="c3", mu_range=(0.10, 0.40),
-                  sigma_range=(0.01, 0.06), live=False) -> World:
+                  sigma_range=(0.01, 0.06), live=False, matched=False) -> World:
     """Multi-channel world with the paper's kernel topology (15 kernels for 3
     channels).  Shells B ~ U{1,2,3}, beta ~ U[0,1), h ~ U[0.1,1).  n_geno
     genotypes, each with per-kernel (mu, sigma), fill square patches; A is
-    U[0,1) noise on each patch (U[0, 2 mu) per channel when live=True)."""
+    U[0,1) noise on each patch (U[0, 2 mu) per channel when live=True).
+
+    matched=True (implies live) draws genotypes whose kernels agree with the
+    patch they sit on, so that the patch interiors pass every kernel's growth
+    test at once: per genotype and channel c a level L ~ U[mu_range); every
+    kernel reading c gets sigma ~ U[0.03, 0.06) and mu = L - 1.1774 sigma +
+    U[-0.01, 0.01); channel c's noise is U[0, 2 L), whose local mean (the
+    potential) is L.  1.1774 = sqrt(2 ln 2) places L near the half-height point
+    of each kernel's bump on its upper side, so the patches start close to
+    an equilibrium (a larger potential lowers the growth) and stay alive for
+    a number of steps.""" 
     rng = Rng(BASE_SEED + seed_index)
     topo = paper_topology(n_channels)
     K = len(topo)
@@ -203,8 +214,16 @@ def multi_channel(H=2048, W=2048, R=18, patch=256, n_geno=16, seed_index=2,
         beta = tuple(float(b) for b in rng.uniform(B))
         h = float(rng.uniform(1, 0.1, 1.0)[0])
         kernels.append(KernelDesc(s, d, R, KERNEL_SHELLS, beta, h=h))
-    mus = rng.uniform(n_geno * K, *mu_range).reshape(n_geno, K)
-    sigmas = rng.uniform(n_geno * K, *sigma_range).reshape(n_geno, K)
+    if matched:
+        live = True
+        level = rng.uniform(n_geno * n_channels, *mu_range).reshape(n_geno, n_channels)
+        jitter = rng.uniform(n_geno * K, -0.01, 0.01).reshape(n_geno, K)
+        src = np.array([s for (s, _) in topo])
+        sigmas = rng.uniform(n_geno * K, 0.03, 0.06).reshape(n_geno, K)
+        mus = (level[:, src] + jitter - np.float32(HALF_HEIGHT) * sigmas).astype(np.float32)
+    else:
+        mus = rng.uniform(n_geno * K, *mu_range).reshape(n_geno, K)
+        sigmas = rng.uniform(n_geno * K, *sigma_range).reshape(n_geno, K)
     for k in range(K):
         kernels[k].mu = float(np.mean(mus[:, k]))
         kernels[k].sigma = float(np.mean(sigmas[:, k]))
@@ -225,7 +244,9 @@ def multi_channel(H=2048, W=2048, R=18, patch=256, n_geno=16, seed_index=2,
                     P[p, k][np.ix_(my, mx)] = vals[k]
         for c in range(n_channels):
             noise = rng.uniform(len(ry) * len(rx)).reshape(len(ry), len(rx))
-            if live:
+            if matched:
+                noise = (noise * np.float32(2.0 * level[g, c])).astype(np.float32)
+            elif live:
                 m = float(np.mean([mus[g][k] for k, (s, d) in enumerate(topo) if s == c]))
                 noise = (noise * np.float32(2.0 * m)).astype(np.float32)
             A[c][np.ix_(ry, rx)] = noise
@@ -288,7 +309,8 @@ def workload(name: str) -> World:
 
 
 def ring_world(H=512, W=1024, R=12, n_rings=24, n_channels=3, patch=96, n_geno=8, seed_index=6,
-               dt=0.2, localized=LOC_MU | LOC_SIGMA | LOC_H | LOC_KERNEL, live=True, name="rings") -> World:
+               dt=0.2, localized=LOC_MU | LOC_SIGMA | LOC_H | LOC_KERNEL, live=True, name="rings",
+               matched=False) -> World:
     """The paper's configuration (Section 2.1): a 512 x 1024 torus, 3 channels,
     15 kernels in the paper's topology, each kernel two Gaussian bumps cut into
     n_rings rings of a radius-R disk (Section 2.4), every gene localized:
@@ -296,13 +318,23 @@ def ring_world(H=512, W=1024, R=12, n_rings=24, n_channels=3, patch=96, n_geno=8
     n_geno genotypes fill square patches (as in the other worlds); per kernel
     r1 ~ U[0.1, 0.5), w1 ~ U[0.05, 0.15), b1 ~ U[0.5, 1), r2 ~ U[0.5, 0.9),
     w2 ~ U[0.05, 0.15), b2 ~ U[0.1, 0.6), m ~ U[0.1, 0.4), s ~ U[0.01, 0.06),
-    h ~ U[0.1, 1).  A is U[0, 1) noise on each patch (U[0, 2 m) with live)."""
+    h ~ U[0.1, 1).  A is U[0, 1) noise on each patch (U[0, 2 m) with live).
+    matched=True redraws m and s as multi_channel(matched=True) does (a level
+    L per genotype and channel, s ~ U[0.03, 0.06), m = L - 1.1774 s + U[-0.01,
+    0.01)) and makes channel c's noise U[0, 2 L)."""
     rng = Rng(BASE_SEED + seed_index)
     topo = paper_topology(n_channels)
     K = len(topo)
     ranges = {"mu": (0.10, 0.40), "sigma": (0.01, 0.06), "h": (0.1, 1.0), "r1": (0.1, 0.5), "w1": (0.05, 0.15),
               "b1": (0.5, 1.0), "r2": (0.5, 0.9), "w2": (0.05, 0.15), "b2": (0.1, 0.6)}
     geno = {g: rng.uniform(n_geno * K, *ranges[g]).reshape(n_geno, K) for g in ranges}
+    level = None
+    if matched:
+        level = rng.uniform(n_geno * n_channels, *ranges["mu"]).reshape(n_geno, n_channels)
+        jitter = rng.uniform(n_geno * K, -0.01, 0.01).reshape(n_geno, K)
+        src = np.array([s_ for (s_, _) in topo])
+        geno["sigma"] = rng.uniform(n_geno * K, 0.03, 0.06).reshape(n_geno, K)
+        geno["mu"] = (level[:, src] + jitter - np.float32(HALF_HEIGHT) * geno["sigma"]).astype(np.float32)
     kernels = []
     for k, (src, dst) in enumerate(topo):
         bump = tuple(float(np.mean(geno[g][:, k])) for g in ("r1", "w1", "b1", "r2", "w2", "b2"))
@@ -319,7 +351,9 @@ def ring_world(H=512, W=1024, R=12, n_rings=24, n_channels=3, patch=96, n_geno=8
                 P[p, k][np.ix_(my, mx)] = geno[name_][g, k]
         for c in range(n_channels):
             noise = rng.uniform(len(ry) * len(rx)).reshape(len(ry), len(rx))
-            if live:
+            if level is not None:
+                noise = (noise * np.float32(2.0 * level[g, c])).astype(np.float32)
+            elif live:
                 m = float(np.mean([geno["mu"][g, k] for k, (s_, d_) in enumerate(topo) if s_ == c]))
                 noise = (noise * np.float32(2.0 * m)).astype(np.float32)
             A[c][np.ix_(ry, rx)] = noise

@@ -52,3 +52,21 @@ def test_max_over_ranks_and_job_value_two_ranks():
 def test_single_rank_is_identity():
     assert bench.max_over_ranks([1.5, 2.5], torch) == [1.5, 2.5]
     assert bench.job_value(1, 4096, 10, 2.0) == pytest.approx(4096 * 10 / 0.002)
+
+
+def test_gpus_flag_spawns_ranks():
+    """`bench.py --gpus 2` outside torchrun starts two ranks itself (gloo on
+    CPU here): rank 0 reports n_gpus = 2 and the slower rank's time."""
+    import json
+    import subprocess
+    import sys
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"),
+                          "--gpus", "2", "--rank-check"], capture_output=True, text=True, timeout=300, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["ms_max"] == 11.0
+    assert d["value"] == pytest.approx(2 * 1000 / 0.011)

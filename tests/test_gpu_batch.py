@@ -78,11 +78,14 @@ def test_batch_step_matches_oracle():
         P = [to_dev(w.P) if w.P is not None else None for w in ws]
         lenia.lenia_batch_rollout(batch, A, P, 1)
         lenia.lenia_batch_check(batch)
+        alive = 0
         for i, w in enumerate(ws):
             A1, P1, U, al = oracle.step(w, return_u=True, return_alpha=True)
             Ph = np.stack([[oracle.diffuse(w.P[p, k]) for k in range(w.n_kernels)] for p in range(w.n_planes)])
             g = {"A": A[i].cpu().numpy(), "P": P[i].cpu().numpy()}
-            compare_step(w, g, A1, P1, al, alpha_margin(w, U, Ph))
+            alive += compare_step(w, g, A1, P1, al, alpha_margin(w, U, Ph), min_alpha1=0)["alpha1"]
+        print("alpha = 1 sites over the batch:", alive)
+        assert alive >= 1000
     finally:
         lenia.lenia_batch_destroy(batch)
 
@@ -102,10 +105,14 @@ def test_grouped_worlds_match_oracle_and_single_worlds():
         P = [to_dev(w.P) for w in ws]
         lenia.lenia_batch_rollout(batch, A, P, 1)
         lenia.lenia_batch_check(batch)
+        alive = 0
         for i, w in enumerate(ws):
             A1, P1, U, al = oracle.step(w, return_u=True, return_alpha=True)
             Ph = np.stack([[oracle.diffuse(w.P[p, k]) for k in range(w.n_kernels)] for p in range(w.n_planes)])
-            compare_step(w, {"A": A[i].cpu().numpy(), "P": P[i].cpu().numpy()}, A1, P1, al, alpha_margin(w, U, Ph))
+            alive += compare_step(w, {"A": A[i].cpu().numpy(), "P": P[i].cpu().numpy()}, A1, P1, al,
+                                  alpha_margin(w, U, Ph), min_alpha1=0)["alpha1"]
+        print("alpha = 1 sites over the batch:", alive)
+        assert alive >= 1000
         lenia.lenia_batch_rollout(batch, A, P, 2)          # three steps in all
         lenia.lenia_batch_check(batch)
         for i, w in enumerate(ws):
@@ -121,5 +128,41 @@ def test_grouped_worlds_match_oracle_and_single_worlds():
                     assert torch.equal(a, A[i]) and torch.equal(p, P[i]), w.name
             finally:
                 lenia.lenia_destroy(ctx)
+    finally:
+        lenia.lenia_batch_destroy(batch)
+
+
+def test_full_batched_workload_sampled_worlds_match_oracle():
+    """The benchmark's batched workload in its launch configuration: 256
+    single-channel localized worlds, sides drawn from {64, 128, 256, 512}, radii
+    8..16, autotuned paths, grouped launches.  After one batch step, a sample
+    of worlds of every side - four of side 512, whose group carries most of the
+    sites and runs the 512-wide grouped kernels - is compared with the oracle
+    element by element."""
+    ws = inputs.batched_worlds(live=True)
+    batch = lenia.lenia_batch_init(ws, autotune=True)
+    try:
+        A = [to_dev(w.A) for w in ws]
+        P = [to_dev(w.P) for w in ws]
+        lenia.lenia_batch_rollout(batch, A, P, 1)
+        lenia.lenia_batch_check(batch)
+        by_side = {}
+        for i, w in enumerate(ws):
+            by_side.setdefault(w.height, []).append(i)
+        assert sorted(by_side) == [64, 128, 256, 512]
+        groups512 = {lenia.lenia_batch_group_of(batch, i) for i in by_side[512]}
+        assert len(groups512) == 1 and -1 not in groups512, groups512      # one group of 512-side worlds
+        pick = by_side[512][:4] + by_side[256][:3] + by_side[128][:2] + by_side[64][:2]
+        alive = 0
+        for i in pick:
+            w = ws[i]
+            A1, P1, U, al = oracle.step(w, return_u=True, return_alpha=True)
+            Ph = np.stack([[oracle.diffuse(w.P[p, k]) for k in range(w.n_kernels)] for p in range(w.n_planes)])
+            res = compare_step(w, {"A": A[i].cpu().numpy(), "P": P[i].cpu().numpy()}, A1, P1, al,
+                               alpha_margin(w, U, Ph), min_alpha1=0)
+            alive += res["alpha1"]
+            print(w.name, w.height, "R", w.kernels[0].radius, "path", lenia.lenia_batch_conv_path(batch, i),
+                  "group", lenia.lenia_batch_group_of(batch, i), res)
+        assert alive >= 1000
     finally:
         lenia.lenia_batch_destroy(batch)

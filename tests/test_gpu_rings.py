@@ -27,8 +27,11 @@ def _built():
     torch_mod()
 
 
+# Under the default alpha reading (alpha_on = 0) the genotypes are matched to
+# their patches, so that every kernel's growth test passes in the interiors.
 def w_small(alpha_on=1):
-    w = inputs.ring_world(H=64, W=128, R=6, n_rings=12, patch=24, n_geno=3)
+    w = inputs.ring_world(H=64, W=128, R=6, n_rings=12, patch=24 if alpha_on else 32, n_geno=3,
+                          matched=not alpha_on)
     w.alpha_on = alpha_on
     return w
 
@@ -40,14 +43,16 @@ def w_single(alpha_on=1):
 
 
 def w_ragged(alpha_on=1):
-    w = inputs.ring_world(H=72, W=100, R=5, n_rings=10, patch=24, n_geno=3, seed_index=8)
+    w = inputs.ring_world(H=72, W=100, R=5, n_rings=10, patch=24 if alpha_on else 32, n_geno=3, seed_index=8,
+                          matched=not alpha_on)
     w.alpha_on = alpha_on
     return w
 
 
 def w_coarse(alpha_on=1):
     # fewer rings than pixels of radius: wide rings
-    w = inputs.ring_world(H=64, W=64, R=9, n_rings=4, patch=24, n_geno=2, seed_index=9)
+    w = inputs.ring_world(H=64, W=64, R=9, n_rings=4, patch=24 if alpha_on else 32, n_geno=2, seed_index=9,
+                          matched=not alpha_on)
     w.alpha_on = alpha_on
     return w
 

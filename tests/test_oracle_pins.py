@@ -334,6 +334,91 @@ def test_mask_on_potential_switch(oracle):
     assert np.array_equal(alpha.astype(bool), D > 0)
 
 
+def _uniform_gene_world(a, genes, localized=3, H=16, W=16, R=3, dt=0.1, dst=None, C=1, h=None):
+    """Uniform phenospace a (per channel) and uniform gene planes over the
+    whole torus: every normalised potential is exactly a (K~ * 1 = 1), the
+    diffusion of a constant plane returns it (five equal FP32 values sum
+    exactly in FP64), so each kernel's growth has a closed form.
+    genes[k] = (mu, sigma[, h]) of kernel k; kernel k reads and writes
+    channel dst[k] (default 0)."""
+    K = len(genes)
+    dst = dst or [0] * K
+    ks = [inputs.KernelDesc(dst[k], dst[k], R, 0, (1.0,), h=(h[k] if h else 1.0)) for k in range(K)]
+    av = [a] * C if np.isscalar(a) else list(a)
+    A = np.stack([np.full((H, W), v, np.float32) for v in av])
+    n_p = bin(localized).count("1")
+    P = np.zeros((n_p, K, H, W), np.float32)
+    for k, gk in enumerate(genes):
+        for p in range(n_p):
+            P[p, k] = np.float32(gk[p])
+    return inputs.World(H, W, C, ks, dt, localized=localized, maintain_genes=1, A=A, P=P)
+
+
+def _g(u, mu, s):
+    return math.exp(-(u - mu) ** 2 / (2.0 * s * s))
+
+
+def test_mask_is_and_over_kernels(oracle):
+    """Section 2.2: Delta_all(U) holds only where EVERY kernel's growth test
+    passes.  Three kernels on a uniform world: kernels 0 and 2 sit at their
+    growth peak (h g = 1 > eps), kernel 1 far from it (g = exp(-112.5)).  The
+    AND is false, so alpha = 0, every gene is zeroed, and each kernel's
+    masked growth is -h (reading R9): A' = a - 3 dt.  (An OR over kernels, or
+    a test of only the first or only the last kernel, would keep the genes.)"""
+    a = float(np.float32(0.3))
+    w = _uniform_gene_world(a, [(a, 0.02), (a + 0.3, 0.02), (a, 0.05)])
+    A1, P1, alpha = oracle.step(w, return_alpha=True)
+    assert alpha.sum() == 0 and np.all(P1 == 0)
+    assert np.max(np.abs(A1 - (a - 3 * 0.1))) < 1e-12
+    # every kernel passing: alpha = 1 everywhere, genes kept, the closed form
+    mus = [a, float(np.float32(a - 0.02)), float(np.float32(a + 0.03))]
+    sgs = [0.02, 0.03, 0.05]
+    w = _uniform_gene_world(a, list(zip(mus, sgs)))
+    A1, P1, alpha = oracle.step(w, return_alpha=True)
+    assert alpha.all()
+    np.testing.assert_array_equal(P1, w.P.astype(np.float64))
+    sgs32 = [float(np.float32(s)) for s in sgs]
+    inc = sum(2 * _g(a, m, s) - 1 for m, s in zip(mus, sgs32))
+    assert np.max(np.abs(A1 - (a + 0.1 * inc))) < 1e-12
+
+
+def test_mask_and_spans_channels(oracle):
+    """alpha is one decision per site over all kernels, whatever channel they
+    write: a failing kernel of channel 1 also masks channel 0's kernel, whose
+    growth then is -h (not +h)."""
+    a0, a1 = float(np.float32(0.2)), float(np.float32(0.6))
+    w = _uniform_gene_world([a0, a1], [(a0, 0.02), (a1 + 0.3, 0.02)], dst=[0, 1], C=2, h=[0.5, 0.25])
+    A1, P1, alpha = oracle.step(w, return_alpha=True)
+    assert alpha.sum() == 0 and np.all(P1 == 0)
+    assert np.max(np.abs(A1[0] - (a0 - 0.1 * 0.5))) < 1e-12
+    assert np.max(np.abs(A1[1] - (a1 - 0.1 * 0.25))) < 1e-12
+
+
+def test_localized_h_masked_where_alpha_is_zero(oracle):
+    """Reading R9 with a localized h: the update uses the masked genes, so
+    where alpha = 0 the gene h is 0 and the growth h (2 g - 1) is 0: A' = a
+    exactly (with a global h the same site would get -h).  Where alpha = 1
+    the site's own h scales the closed-form growth."""
+    a = float(np.float32(0.4))
+    hk = float(np.float32(0.7))
+    # genes die: mu far from U = a
+    w = _uniform_gene_world(a, [(a + 0.3, 0.02, hk)], localized=7)
+    A1, P1, alpha = oracle.step(w, return_alpha=True)
+    assert alpha.sum() == 0 and np.all(P1 == 0)
+    np.testing.assert_array_equal(A1, w.A.astype(np.float64))
+    # the same world with a global h = 0.7: A' = a - dt h
+    wg = _uniform_gene_world(a, [(a + 0.3, 0.02)], localized=3, h=[hk])
+    A1g, _ = oracle.step(wg)
+    assert np.max(np.abs(A1g - (a - 0.1 * hk))) < 1e-12
+    # genes alive: growth hk (2 g - 1) with the site's h
+    mu = float(np.float32(a - 0.01))
+    w = _uniform_gene_world(a, [(mu, 0.03, hk)], localized=7)
+    A1, P1, alpha = oracle.step(w, return_alpha=True)
+    assert alpha.all()
+    s32 = float(np.float32(0.03))
+    assert np.max(np.abs(A1 - (a + 0.1 * hk * (2 * _g(a, mu, s32) - 1)))) < 1e-12
+
+
 def test_step_translation_equivariant(oracle):
     """The whole step commutes with torus rolls (all operations are local and periodic)."""
     w = inputs.multi_channel(H=48, W=40, R=5, patch=12, n_geno=3, live=True)
