@@ -363,6 +363,55 @@ __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
 // per channel, right after the previous channel's last use.  The maintained genes are written as soon as they are diffused;
 // a site that ends without alpha rewrites them with zeros.  Needs
 // W >= RG_TILE_W and H >= RG_TILE_H (one wrap per halo coordinate).
+// One Gaussian bump's share of a ring-recombined potential (Section 2.4):
+// adds w_r V_r and w_r |K_r| over the NR rings to num and den, with
+// w_r = b exp(-(r/NR - c)^2 / (2 w^2)) (nothing where w <= 0).  With
+// x_r = r / NR equally spaced (D = 1/NR), the base-2 exponent
+// L(r) = a (x_r - c)^2, a = -log2(e) / (2 w^2) <= 0, steps by
+// L(r + 1) - L(r) = a D (D + 2 (x_r - c)), itself growing by 2 a D^2 per ring:
+//   w_{r+1} = w_r q_r,  q_{r+1} = q_r s,  s = 2^(2 a D^2)   (walking up),
+//   w_{r-1} = w_r q'_r, q'_{r-1} = q'_r s                   (walking down),
+// so four exponentials per bump replace one per ring.  The walks start at
+// the ring nearest c (w there is the bump's largest) and go outwards, where
+// every ratio is <= 1: no value overflows, an underflow only cuts off a
+// decaying tail, and the rounding of the products grows with the distance
+// from the peak, where the weights are small.  A walk stops once its weight
+// falls below 2^-40 of the peak's (its remaining terms are below FP32
+// resolution of the sums).  The four exponentials are the accurate exp2f,
+// since their rounding is carried along each walk.
+template <int NR>
+__device__ __forceinline__ void ring_bump(float c, float w, float b, const float* v, const float* cnt,
+                                          float& num, float& den)
+{
+    if (!(w > 0.f) || b == 0.f) return;
+    constexpr float LOG2E = 1.4426950408889634f;
+    constexpr float D = 1.f / (float)NR;
+    const float a = -0.5f * LOG2E / (w * w);
+    int rs = __float2int_rn(c * (float)NR);
+    rs = rs < 0 ? 0 : (rs > NR - 1 ? NR - 1 : rs);
+    const float d = (float)rs * D - c;
+    const float e0 = b * exp2f(a * (d * d));
+    const float aD = a * D;
+    const float s = exp2f(2.f * aD * D);
+    const float stop = e0 * 9.094947e-13f;             // 2^-40 of the peak weight
+    float e = e0, q = exp2f(aD * (D + 2.f * d));
+    for (int r = rs; r < NR && e >= stop; r++) {
+        num = fmaf(e, v[r * 256], num);
+        den = fmaf(e, cnt[r], den);
+        e *= q;
+        q *= s;
+    }
+    q = exp2f(aD * (D - 2.f * d));
+    e = e0 * q;
+    q *= s;
+    for (int r = rs - 1; r >= 0 && e >= stop; r--) {
+        num = fmaf(e, v[r * 256], num);
+        den = fmaf(e, cnt[r], den);
+        e *= q;
+        q *= s;
+    }
+}
+
 constexpr int RG_TY = 8;     // rows per block of the ring epilogue (one site per thread)
 constexpr int RG_TILE_W = EP_TX + 2, RG_TILE_H = RG_TY + 2;
 
@@ -381,6 +430,7 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
     constexpr int TP = RG_TILE_H * RG_TILE_W;           // floats per staged plane
     __shared__ float tile[2][NP * TP];
     __shared__ int ord[KT];
+    __shared__ float cnt_s[NR];
     extern __shared__ float vst[];                      // [NR][256]: each thread's own ring potentials
     const int H = p.H, W = p.W;
     const size_t N = (size_t)H * W;
@@ -415,6 +465,8 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
         cp_async_commit();
     };
     // kernels in order of their source channel (the order of the sums below)
+    if (ty == 0)
+        for (int r = tx; r < NR; r += EP_TX) cnt_s[r] = p.ring_cnt[r];
     if (tx == 0 && ty == 0) {
         int n = 0;
         for (int c = 0; c < CT; c++)
@@ -478,22 +530,12 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
                 p.P_out[(size_t)(pp * KT + k) * N + i] = val;
             }
         }
-        // ring weights and the potential
-        const float w1 = g[PK + 1], w2 = g[PK + 4];
-        const float b1 = w1 > 0.f ? g[PK + 2] : 0.f, b2 = w2 > 0.f ? g[PK + 5] : 0.f;
-        const float a1 = w1 > 0.f ? -0.5f * LOG2E / (w1 * w1) : 0.f;
-        const float a2 = w2 > 0.f ? -0.5f * LOG2E / (w2 * w2) : 0.f;
-        const float c1 = g[PK + 0], c2 = g[PK + 3];
-        // the channel's ring potentials, staged in shared memory for its kernels
+        // ring weights and the potential: each bump's weights over the rings,
+        // walked outwards from its peak ring (recurrence below), summed
+        // against the channel's ring potentials staged in shared memory
         float num = 0.f, den = 0.f;
-#pragma unroll 4
-        for (int r = 0; r < NR; r++) {
-            const float xr = p.ring_x[r];
-            const float d1 = xr - c1, d2 = xr - c2;
-            const float kr = b1 * ex2_approx((d1 * d1) * a1) + b2 * ex2_approx((d2 * d2) * a2);
-            num = fmaf(kr, vst[r * 256 + tid], num);
-            den = fmaf(kr, p.ring_cnt[r], den);
-        }
+        ring_bump<NR>(g[PK + 0], g[PK + 1], g[PK + 2], vst + tid, cnt_s, num, den);
+        ring_bump<NR>(g[PK + 3], g[PK + 4], g[PK + 5], vst + tid, cnt_s, num, den);
         // the channel's last kernel: fetch the next channel's potentials now
         if (j + 1 < KT && p.kt.src[ord[j + 1]] != c) stage_v(p.kt.src[ord[j + 1]]);
         const float u = den > 0.f ? num / den : 0.f;
