@@ -76,6 +76,15 @@ def _traffic(kernel: str):
         return None
 
 
+def _bf16_peak():
+    """Measured dense BF16 tensor peak in TFLOP/s (burst), or the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -390,6 +399,106 @@ def rings_leg(torch, lenia, inputs, stream, steps=100):
             "stats_finite": bool(torch.isfinite(st).all())}
 
 
+def _kernel_taps(lenia, ctx, world):
+    """Non-zero taps of each kernel and the Toeplitz K steps (16 input columns
+    each) that the tensor-core route issues per kernel and 256 x 32 tile."""
+    taps, ksteps = [], []
+    Rm = max(k.radius for k in world.kernels)
+    for k, kd in enumerate(world.kernels):
+        Kw = lenia.lenia_kernel_weights(ctx, k, kd.radius)
+        R = kd.radius
+        taps.append(int((Kw != 0).sum()))
+        n = 0
+        for dy in range(-R, R + 1):
+            nz = np.nonzero(Kw[dy + R])[0]
+            if len(nz):
+                dmin, dmax = int(nz[0]) - R, int(nz[-1]) - R
+                n += (dmax + Rm + 31) // 16 - (dmin + Rm) // 16 + 1
+        ksteps.append(n)
+    return taps, ksteps
+
+
+def _time_steps(torch, lenia, ctx, A, P, A2, P2, stream, n):
+    for _ in range(3):
+        lenia.lenia_step(ctx, A, P, A2, P2, None, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        lenia.lenia_step(ctx, A, P, A2, P2, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / n
+    lenia.lenia_profile_start(ctx, 8 * n)
+    for _ in range(n):
+        lenia.lenia_step(ctx, A, P, A2, P2, None, stream)
+    torch.cuda.synchronize()
+    prof = lenia.lenia_profile_stop(ctx)
+    lenia.lenia_check(ctx)
+    return step_ms, {k: v[0] / max(1, v[1]) for k, v in prof.items()}
+
+
+def direct_leg(torch, lenia, inputs, stream, fp32_peak=None, bf16_peak=None, steps=50):
+    """The direct convolution routes.  FP32 direct sums (TMA-staged tiles,
+    kernels over grid z): the 64^2 one-kernel world (R = 13) as a rollout, and
+    R = 5 worlds where the automatic choice is the direct path (1024^2 one
+    channel; 2048^2 three channels, 15 kernels).  Tensor cores (BF16 Toeplitz
+    products): the headline 2048^2 world (R = 18) with BF16 operands and with
+    the high/low split, against its FFT route; tensor work is counted as
+    issued (zero-padded band) and as useful (non-zero taps)."""
+    out = {}
+    w = inputs.single_kernel_global()
+    cfg, ks = lenia.config_from_world(w, lenia.CONV_DIRECT)
+    ctx = lenia.lenia_init(cfg, ks, stream)
+    try:
+        a = torch.from_numpy(w.A).cuda()
+        lenia.lenia_rollout(ctx, a, None, 10, None, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lenia.lenia_rollout(ctx, a, None, 100, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lenia.lenia_check(ctx)
+        out["c1_direct"] = {"workload": "64x64, 1 channel, 1 kernel R=13, global genes, 100-step rollout, direct path",
+                            "us_per_step": e0.elapsed_time(e1) * 1e3 / 100}
+    finally:
+        lenia.lenia_destroy(ctx)
+    cases = (("r5_1024", inputs.localized_single_channel(R=5), lenia.CONV_AUTO),
+             ("r5_2048_c3", inputs.multi_channel(R=5, matched=True), lenia.CONV_AUTO),
+             ("c3_fft", inputs.multi_channel(matched=True), lenia.CONV_FFT),
+             ("c3_bf16", inputs.multi_channel(matched=True), lenia.CONV_DIRECT_BF16),
+             ("c3_bf16x3", inputs.multi_channel(matched=True), lenia.CONV_DIRECT_BF16X3))
+    for name, w, path in cases:
+        cfg, ks = lenia.config_from_world(w, path)
+        ctx = lenia.lenia_init(cfg, ks, stream)
+        try:
+            A, P = torch.from_numpy(w.A).cuda(), torch.from_numpy(w.P).cuda()
+            A2, P2 = torch.empty_like(A), torch.empty_like(P)
+            step_ms, kern = _time_steps(torch, lenia, ctx, A, P, A2, P2, stream, steps)
+            used = lenia.lenia_conv_path(ctx)
+            taps, ksteps = _kernel_taps(lenia, ctx, w)
+        finally:
+            lenia.lenia_destroy(ctx)
+        conv_ms = sum(v for k, v in kern.items() if k in ("direct_conv", "rows_r2c", "cols_conv", "rows_c2r"))
+        useful = 2.0 * sum(taps) * w.sites
+        r = {"workload": f"{w.height}x{w.width}, {w.n_channels} channels, {w.n_kernels} kernels R={w.kernels[0].radius}",
+             "conv_path": {1: "fft", 2: "direct_fp32", 3: "direct_bf16", 4: "direct_bf16x3"}[used],
+             "ms_per_step": step_ms, "value": w.sites / (step_ms / 1e3), "unit": UNIT, "conv_ms": conv_ms,
+             "kernels_ms": kern, "useful_conv_tflops": useful / (conv_ms / 1e3) / 1e12 if conv_ms else None}
+        if used == lenia.CONV_DIRECT and fp32_peak:
+            r["fp32_frac"] = r["useful_conv_tflops"] / fp32_peak
+        if used in (lenia.CONV_DIRECT_BF16, lenia.CONV_DIRECT_BF16X3):
+            terms = 1 if used == lenia.CONV_DIRECT_BF16 else 3
+            issued = 2.0 * sum(ksteps) * 16 * 32 * 256 * terms * (w.sites / (32 * 256))
+            r["issued_tensor_tflops"] = issued / (conv_ms / 1e3) / 1e12
+            r["issued_over_useful"] = issued / useful
+            if bf16_peak:
+                r["tensor_frac_of_bf16_peak"] = r["issued_tensor_tflops"] / bf16_peak
+        out[name] = r
+    return out
+
+
 def max_over_ranks(values, torch, device=None):
     """Element-wise max of a list of floats over all ranks (identity at N = 1)."""
     import torch.distributed as dist
@@ -631,6 +740,7 @@ def run_ours(args):
         line["evolve"] = evolve_leg(torch, lenia, inputs, stream, t_max / args.steps)
         line["rings"] = rings_leg(torch, lenia, inputs, stream)
         line["small"] = small_legs(torch, lenia, inputs, stream, max(fp32_scalar, fp32_pair))
+        line["direct"] = direct_leg(torch, lenia, inputs, stream, max(fp32_scalar, fp32_pair), _bf16_peak())
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -686,7 +796,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched-world, evolution, ring and small-world legs")
     ap.add_argument("--size", type=int, default=2048, help="torus side (2048 = the benchmark workload)")
     ap.add_argument("--conv-path", type=int, default=0, help="0 auto, 1 fft, 2 direct")
-    ap.add_argument("--leg", default=None, choices=["adjoint", "batched", "evolve", "rings", "small"],
+    ap.add_argument("--leg", default=None, choices=["adjoint", "batched", "evolve", "rings", "small", "direct"],
                     help="run only this extra leg (N = 1) and print its JSON object (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -717,6 +827,8 @@ def run_leg(args):
         out = evolve_leg(torch, lenia, inputs, stream, None, steps=args.steps)
     elif args.leg == "small":
         out = small_legs(torch, lenia, inputs, stream, max(lenia.lenia_measure_fp32_peak(stream)))
+    elif args.leg == "direct":
+        out = direct_leg(torch, lenia, inputs, stream, max(lenia.lenia_measure_fp32_peak(stream)), _bf16_peak())
     else:
         out = rings_leg(torch, lenia, inputs, stream, steps=args.steps)
     print(json.dumps({"leg": args.leg, **out}), flush=True)

@@ -69,7 +69,16 @@ enum { LENIA_GROWTH_SIGNED = 0, LENIA_GROWTH_PAPER = 1 };
 /* LENIA_LOC_KERNEL: ring-wise kernel genes (Section 2.4), six planes r1, w1,
  * b1, r2, w2, b2 after the growth planes; needs n_rings > 0. */
 enum { LENIA_LOC_MU = 1, LENIA_LOC_SIGMA = 2, LENIA_LOC_H = 4, LENIA_LOC_KERNEL = 8 };
-enum { LENIA_CONV_AUTO = 0, LENIA_CONV_FFT = 1, LENIA_CONV_DIRECT = 2 };
+/* Convolution routes: AUTO picks FFT for power-of-two worlds with R > 6,
+ * else DIRECT (FP32 sums).  DIRECT_BF16 and DIRECT_BF16X3 run the direct
+ * convolution on the tensor cores as banded Toeplitz products (tcgen05,
+ * FP32 accumulation): BF16 operands (8 significant bits: a potential moves
+ * by at most (2^-7 + 2^-16) of its value), or both operands split into BF16
+ * high and low parts and three products summed (at most about 3 2^-16 of
+ * the value); both need H % 256 == 0, W % 32 == 0 and R <= 100, and are not
+ * available to lenia_backward. */
+enum { LENIA_CONV_AUTO = 0, LENIA_CONV_FFT = 1, LENIA_CONV_DIRECT = 2, LENIA_CONV_DIRECT_BF16 = 3,
+       LENIA_CONV_DIRECT_BF16X3 = 4 };
 
 /* One kernel k (Section 2.1: kernels with their growth mappings).
  *   src_channel, dst_channel: the channel convolved and the channel updated.
@@ -107,6 +116,8 @@ typedef struct {
  *   eps_p: gene threshold of Delta_same / Delta_all (strict '>').
  *   r_diff: radius of the diffusion disk |d|_2 <= r_diff, 0..8.
  *   conv_path: LENIA_CONV_* (AUTO picks FFT for power-of-two worlds).
+ *     The tensor-core routes (LENIA_CONV_DIRECT_BF16, _BF16X3) are chosen only
+ *     on request.
  *   max_rollout_steps, ckpt_every: adjoint buffers for lenia_backward (0 = none;
  *     global genes only); states kept every ckpt_every steps (0 -> 8); with
  *     ckpt_every = 1 every state and every step's potentials are kept
@@ -333,7 +344,7 @@ LENIA_API lenia_status lenia_stats_noalloc(const float* A, int32_t n_channels, i
  * -R..R, copied to the HOST buffer out. */
 LENIA_API lenia_status lenia_kernel_weights(const lenia_ctx* ctx, int32_t k, double* out);
 
-/* Convolution path in use: LENIA_CONV_FFT or LENIA_CONV_DIRECT. */
+/* Convolution path in use: LENIA_CONV_FFT, _DIRECT, _DIRECT_BF16 or _DIRECT_BF16X3. */
 LENIA_API int32_t lenia_conv_path(const lenia_ctx* ctx);
 
 /* Number of CUDA kernel launches one lenia_step enqueues (with stats). */

@@ -31,6 +31,14 @@ struct lenia_ctx {
     // device scratch (library-owned)
     float* d_w = nullptr;
     int* d_w_off = nullptr;
+    // tensor-core route (LENIA_CONV_DIRECT_BF16 / _BF16X3)
+    uint16_t* d_tc_hi = nullptr;
+    uint16_t* d_tc_lo = nullptr;
+    unsigned char* d_tc_B = nullptr;
+    int2* d_tc_ks = nullptr;
+    int* d_tc_grp = nullptr;
+    int* d_tc_has = nullptr;
+    TcConvParams tp;
     int* d_yr = nullptr;
     int* d_yr_off = nullptr;
     float* d_S = nullptr;
@@ -193,7 +201,10 @@ lenia_status validate(const lenia_config* c, const lenia_kernel_desc* ks, std::s
         return bad("r_diff must be 0..8 and 2 r_diff + 1 <= min(H, W)");
     if (!isfinite(c->eps_u) || !isfinite(c->eps_p)) return bad("eps must be finite");
     if (c->alpha_on != 0 && c->alpha_on != 1) return bad("alpha_on must be 0 or 1");
-    if (c->conv_path < LENIA_CONV_AUTO || c->conv_path > LENIA_CONV_DIRECT) return bad("unknown conv_path");
+    if (c->conv_path < LENIA_CONV_AUTO || c->conv_path > LENIA_CONV_DIRECT_BF16X3) return bad("unknown conv_path");
+    if ((c->conv_path == LENIA_CONV_DIRECT_BF16 || c->conv_path == LENIA_CONV_DIRECT_BF16X3) &&
+        c->max_rollout_steps > 0)
+        return bad("the adjoint needs the FFT or the FP32 direct path");
     if (c->conv_path == LENIA_CONV_FFT && !fft_size_supported(c->height, c->width))
         return bad("FFT path needs H and W powers of two in [64, 4096]");
     for (int k = 0; k < c->n_kernels; k++) {
@@ -226,6 +237,25 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb)
     const char* pa = (const char*)a;
     const char* pb = (const char*)b;
     return pa < pb + nb && pb < pa + na;
+}
+
+// BF16 bit pattern of x rounded to nearest, ties to even (the upper 16 bits
+// of the FP32 pattern after adding half an ulp of BF16; NaN kept quiet), and
+// the value of a BF16 bit pattern.
+uint16_t bf16_bits(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7FFFFFFFu) > 0x7F800000u) return (uint16_t)((u >> 16) | 0x40u);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+double bf16_value(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
 }
 
 template <class T>
@@ -310,6 +340,11 @@ lenia_status potentials(lenia_ctx* c, const float* A, float* U, cudaStream_t s)
             ProfScope ps(c, KIND_C2R, s);
             CUDA_OR_FAIL(c, launch_fft_rows_c2r(fp, s));
         }
+    } else if (c->path == LENIA_CONV_DIRECT_BF16 || c->path == LENIA_CONV_DIRECT_BF16X3) {
+        TcConvParams tp = c->tp;
+        tp.U = U;
+        ProfScope ps(c, KIND_DIRECT, s);
+        CUDA_OR_FAIL(c, launch_conv_tc(tp, A, s));
     } else {
         ConvParams cp = c->cp;
         cp.A = A;
@@ -501,7 +536,8 @@ int32_t lenia_launches_per_step(const lenia_ctx* ctx)
     if (!ctx) return -1;
     EpiParams ep = epi_params(const_cast<lenia_ctx*>(ctx));
     const bool fused = epilogue_rows_supported(ep);   // stats reduced inside the epilogue
-    return (ctx->path == LENIA_CONV_FFT ? 3 : 1) + (fused ? 1 : 2);
+    const int conv = ctx->path == LENIA_CONV_FFT ? 3 : (ctx->path == LENIA_CONV_DIRECT ? 1 : 2);
+    return conv + (fused ? 1 : 2);
 }
 
 void lenia_destroy(lenia_ctx* c)
@@ -513,7 +549,8 @@ void lenia_destroy(lenia_ctx* c)
                     c->d_gA[1], c->d_gpre, c->d_gU, c->d_V, c->d_gene_part, c->d_gene_acc,
                     c->d_Ahat_t, c->d_Uhat_t, c->d_ticket, c->d_walls, c->d_alpha_e, c->d_empty,
                     c->d_cnt, c->d_Useg, c->d_hA_in1, c->d_hP_in1, c->d_hA_out1,
-                    c->d_hP_out1, c->d_hstats};
+                    c->d_hP_out1, c->d_hstats, c->d_tc_hi, c->d_tc_lo, c->d_tc_B, c->d_tc_ks,
+                    c->d_tc_grp, c->d_tc_has};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -609,9 +646,15 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
     int path = cfg->conv_path;
     if (path == LENIA_CONV_AUTO)
         path = (fft_size_supported(H, W) && c->max_R > 6) ? LENIA_CONV_FFT : LENIA_CONV_DIRECT;
-    if (path == LENIA_CONV_DIRECT && (size_t)(32 + 2 * c->max_R) * (32 + 2 * c->max_R) * 4 > 200 * 1024) {
+    if (path == LENIA_CONV_DIRECT && (size_t)(38 + 2 * c->max_R) * (32 + 2 * c->max_R) * 4 + 128 > 200 * 1024) {
         lenia_destroy(c);
         fprintf(stderr, "lenia_init: radius too large for the direct path\n");
+        return LENIA_EINVAL;
+    }
+    const bool tc = path == LENIA_CONV_DIRECT_BF16 || path == LENIA_CONV_DIRECT_BF16X3;
+    if (tc && !tc_conv_supported(H, W, c->max_R)) {
+        lenia_destroy(c);
+        fprintf(stderr, "lenia_init: the tensor-core path needs H %% 256 == 0, W %% 32 == 0 and R <= 100\n");
         return LENIA_EINVAL;
     }
     c->path = path;
@@ -714,9 +757,91 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         c->cp.W = W;
         c->cp.C = C;
         c->cp.K = NC;
+        c->cp.status = c->d_status;
         for (int k = 0; k < NC; k++) c->cp.R[k] = c->conv_R[k];
         memcpy(c->cp.kcount, kcount, sizeof(kcount));
         memcpy(c->cp.klist, klist, sizeof(klist));
+    } else if (tc) {
+        // Toeplitz blocks of every plane and row offset dy (BF16 high and low
+        // parts), K-step ranges, and the blocks' kernel groups
+        const int Rm = c->max_R, nt = TC_NT, n_dy = 2 * Rm + 1;
+        const int kp = (nt + 2 * Rm + 15) / 16 * 16;
+        const size_t blk = tc_block_bytes_host(kp);              // bytes of one block
+        const size_t n_el = blk / 2;
+        std::vector<uint16_t> Bt(2 * (size_t)NC * n_dy * n_el, 0);
+        std::vector<int2> ksr((size_t)NC * n_dy);
+        std::vector<int> has(NC, 0);
+        const size_t lo_off = (size_t)NC * n_dy * n_el;
+        for (int k = 0; k < NC; k++) {
+            const int Rk = c->conv_R[k], nk = 2 * Rk + 1;
+            for (int dyi = 0; dyi < n_dy; dyi++) {
+                const int dy = dyi - Rm;
+                int dmin = 1 << 30, dmax = -(1 << 30);
+                if (std::abs(dy) <= Rk)
+                    for (int dx = -Rk; dx <= Rk; dx++)
+                        if (c->conv_w[k][(size_t)(dy + Rk) * nk + (dx + Rk)] != 0.0) {
+                            dmin = std::min(dmin, dx);
+                            dmax = std::max(dmax, dx);
+                        }
+                if (dmax < dmin) {
+                    ksr[(size_t)k * n_dy + dyi] = make_int2(1, 0);
+                    continue;
+                }
+                has[k] = 1;
+                ksr[(size_t)k * n_dy + dyi] = make_int2((dmin + Rm) / 16, (dmax + Rm + nt - 1) / 16);
+                uint16_t* bh = Bt.data() + ((size_t)k * n_dy + dyi) * n_el;
+                uint16_t* bl = bh + lo_off;
+                for (int kc = 0; kc < kp / 8; kc++)
+                    for (int x = 0; x < nt; x++)
+                        for (int e8 = 0; e8 < 8; e8++) {
+                            const int dx = 8 * kc + e8 - x - Rm;
+                            if (std::abs(dx) > Rk) continue;
+                            const double w = c->conv_w[k][(size_t)(dy + Rk) * nk + (dx + Rk)];
+                            const size_t o = ((size_t)kc * nt + x) * 8 + e8;
+                            bh[o] = bf16_bits((float)w);
+                            bl[o] = bf16_bits((float)(w - (double)bf16_value(bh[o])));
+                        }
+            }
+        }
+        std::vector<int> grp;
+        for (int ch = 0; ch < C; ch++)
+            for (int t0 = 0; t0 < kcount[ch]; t0 += TC_NG) {
+                const int n = std::min(TC_NG, kcount[ch] - t0);
+                grp.push_back(ch);
+                grp.push_back(n);
+                for (int t = 0; t < TC_NG; t++) grp.push_back(t < n ? klist[ch][t0 + t] : 0);
+            }
+        const int Hp = H + 2 * Rm, Wp = (W + 2 * Rm + 7) / 8 * 8;
+        ALLOC(c->d_tc_hi, (size_t)C * Hp * Wp);
+        if (path == LENIA_CONV_DIRECT_BF16X3) ALLOC(c->d_tc_lo, (size_t)C * Hp * Wp);
+        ALLOC(c->d_tc_B, Bt.size() * 2);
+        ALLOC(c->d_tc_ks, ksr.size());
+        ALLOC(c->d_tc_grp, grp.size());
+        ALLOC(c->d_tc_has, has.size());
+        CK_INIT(cudaMemcpy(c->d_tc_B, Bt.data(), Bt.size() * 2, cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_tc_ks, ksr.data(), ksr.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_tc_grp, grp.data(), grp.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CK_INIT(cudaMemcpy(c->d_tc_has, has.data(), has.size() * sizeof(int), cudaMemcpyHostToDevice));
+        memset(&c->tp, 0, sizeof(c->tp));
+        c->tp.Ap_hi = c->d_tc_hi;
+        c->tp.Ap_lo = c->d_tc_lo;
+        c->tp.B = c->d_tc_B;
+        c->tp.B_lo_off = lo_off * 2;
+        c->tp.ks = c->d_tc_ks;
+        c->tp.grp = c->d_tc_grp;
+        c->tp.has_taps = c->d_tc_has;
+        c->tp.status = c->d_status;
+        c->tp.H = H;
+        c->tp.W = W;
+        c->tp.C = C;
+        c->tp.R = Rm;
+        c->tp.Hp = Hp;
+        c->tp.Wp = Wp;
+        c->tp.KP = kp;
+        c->tp.rows_pad = (256 + 2 * Rm + 15) / 16 * 16;
+        c->tp.n_dy = n_dy;
+        c->tp.n_groups = (int)grp.size() / (2 + TC_NG);
+        c->tp.terms = path == LENIA_CONV_DIRECT_BF16X3 ? 3 : 1;
     } else {
         const int M = W / 2, HS = H / 2 + 1;
         ALLOC(c->d_Ahat, (size_t)C * H * M);

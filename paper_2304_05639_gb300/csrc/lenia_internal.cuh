@@ -110,7 +110,29 @@ struct ConvParams {
     int R[kMaxConvPlanes];
     int kcount[kMaxChannels];
     int klist[kMaxChannels][kMaxKernels];
+    int* status;               // device status word (bounded TMA waits)
+    int tma;                   // set by the launcher: interior tiles staged by TMA
 };
+
+// Direct convolution on the tensor cores (conv_tc.cu): BF16 Toeplitz blocks,
+// FP32 accumulation in tensor memory.
+constexpr int TC_NT = 32;       // output columns per block
+constexpr int TC_NG = 4;        // kernels per block (its accumulators: 2 x TC_NG x TC_NT TMEM columns)
+struct TcConvParams {
+    uint16_t* Ap_hi;            // [C][Hp][Wp] BF16 padded copy of A (periodic halo of R)
+    uint16_t* Ap_lo;            // low parts A - hi (TERMS = 3) or null
+    const unsigned char* B;     // Toeplitz blocks [plane][dy + R][KP / 8][TC_NT][8] BF16 (high parts)
+    size_t B_lo_off;            // byte offset of the low parts
+    const int2* ks;             // [plane][dy + R]: first and last K step (16 columns) with a non-zero tap
+    const int* grp;             // per block z: channel, kernel count, up to TC_NG kernels
+    const int* has_taps;        // [plane]: 0 for a kernel without any non-zero tap
+    float* U;
+    int* status;
+    int H, W, C, R, Hp, Wp, KP, rows_pad, n_dy, n_groups, terms;
+};
+bool tc_conv_supported(int H, int W, int max_R);
+size_t tc_block_bytes_host(int kp);
+cudaError_t launch_conv_tc(const TcConvParams& p, const float* A, cudaStream_t s);
 
 // Spectral (FFT) convolution.
 struct FftParams {

@@ -2,6 +2,11 @@
 // epilogue, and per-channel statistics (arXiv 2304.05639, Sections 2.1-2.4,
 // Algorithm 2).
 #include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "lenia_internal.cuh"
 #include "ptx_util.cuh"
@@ -18,68 +23,146 @@ __device__ __forceinline__ int wrapi(int i, int n)
 // ------------------------------------------------------- direct convolution
 // U_k(y, x) = sum_d K~_k(d) A_src(k)(y + d, x + d), periodic (K~ is point
 // symmetric, so this is the convolution K~ * A).  A block computes a 32 x 32
-// output tile of one channel for every kernel reading that channel.  Each
-// thread owns one column x and four rows; for each tap column dx it slides a
-// four-row register window down the non-zero taps of that column.
+// output tile of one kernel (grid z runs over the kernels, so that small
+// worlds still fill the GPU).  The input tile with its R halo is staged in
+// shared memory: by one tiled TMA box (the mbarrier wait is bounded) when it
+// lies inside the world, else - at the torus edges, where it wraps - by plain
+// loads.  Box columns start at a multiple of 4 floats (16 bytes), so the tile
+// carries up to 3 extra columns on the left: `off`.  Each thread owns one
+// column x and four rows; for each tap column dx it slides a four-row
+// register window down the non-zero taps of that column.
 constexpr int DC_TX = 32, DC_TY = 32, DC_ROWS = 4;
 
-__global__ void __launch_bounds__(256) k_direct_conv(ConvParams p, int maxR)
+__host__ __device__ constexpr int dc_pitch(int maxR) { return (DC_TX + 2 * maxR + 3 + 3) / 4 * 4; }
+__host__ __device__ constexpr int dc_rows(int maxR) { return DC_TY + 2 * maxR; }
+
+__global__ void __launch_bounds__(256) k_direct_conv(ConvParams p, int maxR, const __grid_constant__ CUtensorMap tm_a)
 {
-    extern __shared__ float tile[];
-    const int c = blockIdx.z;
+    extern __shared__ __align__(128) unsigned char dc_raw[];
+    float* tile = reinterpret_cast<float*>(dc_raw + ((128 - (smem_addr(dc_raw) & 127)) & 127));
+    __shared__ __align__(8) uint64_t bar;
+    // grid z enumerates (channel, kernel of that channel) pairs
+    int c = 0, t = blockIdx.z;
+    while (c < p.C - 1 && t >= p.kcount[c]) t -= p.kcount[c++];
+    const int k = p.klist[c][t];
     const int x0 = blockIdx.x * DC_TX, y0 = blockIdx.y * DC_TY;
-    const int pitch = DC_TX + 2 * maxR;
-    const int rows = DC_TY + 2 * maxR;
+    const int pitch = dc_pitch(maxR), rows = dc_rows(maxR);
+    const int xs = (x0 - maxR) & ~3;                 // first staged column (may be negative)
+    const int off = x0 - maxR - xs;                  // 0..3
+    const int ys = y0 - maxR;
+    const bool inside = p.tma && xs >= 0 && xs + pitch <= p.W && ys >= 0 && ys + rows <= p.H;
     const float* A = p.A + (size_t)c * p.H * p.W;
-    for (int u = threadIdx.y * 32 + threadIdx.x; u < rows * pitch; u += 256) {
-        const int ty = u / pitch, tx = u % pitch;
-        tile[u] = __ldg(&A[(size_t)wrapi(y0 - maxR + ty, p.H) * p.W + wrapi(x0 - maxR + tx, p.W)]);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    if (inside) {
+        if (tid == 0) {
+            mbar_init(&bar, 1);
+            mbar_fence_init();
+            mbar_arrive_expect_tx(&bar, (uint32_t)(pitch * rows * 4));
+            tma_load_3d(tile, &tm_a, xs, ys, c, &bar);
+        }
+        __syncthreads();
+        if (!__syncthreads_and(mbar_wait_bounded(&bar, 0))) {
+            if (tid == 0) {
+                atomicExch(p.status, kStatusWaitTimeout);
+                mbar_wait_bounded(&bar, 0);
+            }
+            return;
+        }
+    } else {
+        for (int u = tid; u < rows * pitch; u += 256) {
+            const int ty = u / pitch, tx = u % pitch;
+            tile[u] = __ldg(&A[(size_t)wrapi(ys + ty, p.H) * p.W + wrapi(xs + tx, p.W)]);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const int tx = threadIdx.x;
     const int ty = threadIdx.y * DC_ROWS;
     const int x = x0 + tx;
-    for (int t = 0; t < p.kcount[c]; t++) {
-        const int k = p.klist[c][t];
-        const int R = p.R[k];
-        const float* w = p.w + p.w_off[k];       // [dx + R][dy + R]
-        const int* yr = p.yr + p.yr_off[k];
-        float acc[DC_ROWS] = {0.f, 0.f, 0.f, 0.f};
-        for (int dx = -R; dx <= R; dx++) {
-            const int r = __ldg(&yr[dx + R]);
-            if (r < 0) continue;
-            const float* col = tile + (size_t)(ty + maxR) * pitch + (tx + maxR + dx);
-            const float* wc = w + (dx + R) * (2 * R + 1) + R;
-            float v[DC_ROWS];
+    const int R = p.R[k];
+    const float* w = p.w + p.w_off[k];       // [dx + R][dy + R]
+    const int* yr = p.yr + p.yr_off[k];
+    float acc[DC_ROWS] = {0.f, 0.f, 0.f, 0.f};
+    for (int dx = -R; dx <= R; dx++) {
+        const int r = __ldg(&yr[dx + R]);
+        if (r < 0) continue;
+        const float* col = tile + (size_t)(ty + maxR) * pitch + (tx + off + maxR + dx);
+        const float* wc = w + (dx + R) * (2 * R + 1) + R;
+        float v[DC_ROWS];
 #pragma unroll
-            for (int o = 0; o < DC_ROWS - 1; o++) v[o] = col[(o - r) * pitch];
-            for (int dy = -r; dy <= r; dy++) {
-                v[DC_ROWS - 1] = col[(dy + DC_ROWS - 1) * pitch];
-                const float wv = __ldg(&wc[dy]);
+        for (int o = 0; o < DC_ROWS - 1; o++) v[o] = col[(o - r) * pitch];
+        for (int dy = -r; dy <= r; dy++) {
+            v[DC_ROWS - 1] = col[(dy + DC_ROWS - 1) * pitch];
+            const float wv = __ldg(&wc[dy]);
 #pragma unroll
-                for (int o = 0; o < DC_ROWS; o++) acc[o] = fmaf(wv, v[o], acc[o]);
+            for (int o = 0; o < DC_ROWS; o++) acc[o] = fmaf(wv, v[o], acc[o]);
 #pragma unroll
-                for (int o = 0; o < DC_ROWS - 1; o++) v[o] = v[o + 1];
-            }
+            for (int o = 0; o < DC_ROWS - 1; o++) v[o] = v[o + 1];
         }
-        if (x < p.W) {
+    }
+    if (x < p.W) {
 #pragma unroll
-            for (int o = 0; o < DC_ROWS; o++) {
-                const int y = y0 + ty + o;
-                if (y < p.H) p.U[((size_t)k * p.H + y) * p.W + x] = acc[o];
-            }
+        for (int o = 0; o < DC_ROWS; o++) {
+            const int y = y0 + ty + o;
+            if (y < p.H) p.U[((size_t)k * p.H + y) * p.W + x] = acc[o];
         }
     }
 }
 
+// Tensor map of a phenospace [C][H][W] (FP32) with boxes of the direct
+// convolution's staged tile; cached by argument.
+static bool dc_map(CUtensorMap* out, const float* base, int W, int H, int C, int bx, int by)
+{
+    struct Key {
+        const void* base;
+        int W, H, C, bx, by;
+        bool operator==(const Key& o) const
+        {
+            return base == o.base && W == o.W && H == o.H && C == o.C && bx == o.bx && by == o.by;
+        }
+    };
+    static std::mutex mu;
+    static std::vector<std::pair<Key, CUtensorMap>> cache;
+    const Key key{base, W, H, C, bx, by};
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& e : cache)
+        if (e.first == key) {
+            *out = e.second;
+            return true;
+        }
+    auto fn = tensor_map_encoder();
+    if (!fn || ((uintptr_t)base & 15) != 0 || W % 4 != 0 || bx > 256 || by > 256) return false;
+    CUtensorMap m;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)C};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)W * H * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    cache.insert(cache.begin(), {key, m});
+    if (cache.size() > 32) cache.pop_back();
+    *out = m;
+    return true;
+}
+
 cudaError_t launch_direct_conv(const ConvParams& p, int max_R, cudaStream_t s)
 {
-    const size_t smem = (size_t)(DC_TX + 2 * max_R) * (DC_TY + 2 * max_R) * sizeof(float);
+    const int pitch = dc_pitch(max_R), rows = dc_rows(max_R);
+    const size_t smem = (size_t)pitch * rows * sizeof(float) + 128;     // + alignment of the TMA destination
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = smem_limit<k_direct_conv>(smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((p.W + DC_TX - 1) / DC_TX, (p.H + DC_TY - 1) / DC_TY, p.C);
-    k_direct_conv<<<grid, dim3(32, DC_TY / DC_ROWS), smem, s>>>(p, max_R);
+    ConvParams q = p;
+    CUtensorMap tm;
+    memset(&tm, 0, sizeof(tm));
+    // worlds too narrow or short for an interior tile use plain loads only
+    q.tma = p.W >= pitch && p.H >= rows && dc_map(&tm, p.A, p.W, p.H, p.C, pitch, rows);
+    int planes = 0;
+    for (int c = 0; c < p.C; c++) planes += p.kcount[c];
+    if (planes == 0) return cudaSuccess;
+    dim3 grid((p.W + DC_TX - 1) / DC_TX, (p.H + DC_TY - 1) / DC_TY, planes);
+    k_direct_conv<<<grid, dim3(32, DC_TY / DC_ROWS), smem, s>>>(q, max_R, tm);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ from . import build as _build
 from . import inputs as _inputs
 
 LENIA_OK, LENIA_EINVAL, LENIA_ENOMEM, LENIA_ECUDA, LENIA_ETIMEOUT, LENIA_ENOTSUP = range(6)
-CONV_AUTO, CONV_FFT, CONV_DIRECT = 0, 1, 2
+CONV_AUTO, CONV_FFT, CONV_DIRECT, CONV_DIRECT_BF16, CONV_DIRECT_BF16X3 = 0, 1, 2, 3, 4
 
 # Every function the header declares (checked by the tests).
 EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia_stats",
