@@ -262,6 +262,19 @@ LENIA_API lenia_status lenia_check(lenia_ctx* ctx, void* stream);
  * Nothing faults or traps; the context stays usable. */
 LENIA_API lenia_status lenia_selftest_wait_timeout(lenia_ctx* ctx, int32_t limit_mcycles, void* stream);
 
+/* Failure-injection test hook (no counterpart in the paper; for testing the
+ * error paths without a GPU fault).  Arms a process-wide countdown over the
+ * library's checked CUDA calls: after n_calls further calls succeed, the next
+ * one - which itself runs normally - is reported as failed
+ * (cudaErrorLaunchOutOfResources), so the entry point in progress returns
+ * LENIA_ECUDA with " (injected)" in lenia_last_error; the hook then disarms
+ * itself.  n_calls < 0 disarms it.  The device and the context are left
+ * consistent: the work enqueued before the reported failure runs, the rest
+ * of that call is not enqueued, and later calls work normally (a host-buffer
+ * step waits for its copies before returning the error; a rollout whose
+ * graph capture fails falls back to direct launches and succeeds). */
+LENIA_API lenia_status lenia_debug_fail_after(int32_t n_calls);
+
 /* Measurement helper (no counterpart in the paper): the FP32 throughput of
  * the current device's CUDA cores in TFLOP/s, as the best of five timed
  * launches of independent fused multiply-add chains on every SM, scalar

@@ -5,10 +5,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <array>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lenia.h"
 #include "lenia_internal.cuh"
@@ -129,11 +132,30 @@ lenia_status fail(lenia_ctx* c, lenia_status s, const std::string& msg)
     return s;
 }
 
+// Failure injection (lenia_debug_fail_after, a test hook): while armed, a
+// countdown of checked CUDA calls; the call that takes it below zero is
+// reported as failed (cudaErrorLaunchOutOfResources) after it has run, and
+// the hook disarms itself.
+std::atomic<int> g_fail_after{-1};
+
+cudaError_t checked(cudaError_t e, bool* injected)
+{
+    *injected = false;
+    int v = g_fail_after.load(std::memory_order_relaxed);
+    while (v >= 0 && !g_fail_after.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) {
+    }
+    if (v != 0 || e != cudaSuccess) return e;
+    *injected = true;
+    return cudaErrorLaunchOutOfResources;
+}
+
 #define CUDA_OR_FAIL(ctx, call)                                                      \
     do {                                                                             \
-        cudaError_t e_ = (call);                                                     \
+        bool inj_ = false;                                                           \
+        cudaError_t e_ = checked((call), &inj_);                                     \
         if (e_ != cudaSuccess)                                                       \
-            return fail(ctx, LENIA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return fail(ctx, LENIA_ECUDA,                                            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_) + (inj_ ? " (injected)" : "")); \
     } while (0)
 
 // Kernel shell of the original Lenia: beta[floor(B rho)] core(B rho mod 1),
@@ -307,6 +329,7 @@ struct ProfScope {
     bool on;
     ProfScope(lenia_ctx* c_, int kind, cudaStream_t s_) : c(c_), s(s_), on(false)
     {
+        nvtxRangePushA(kKindNames[kind]);        // named range per launch kind (no-op without a tool)
         if (c->prof && c->ev_used + 2 <= c->ev.size()) {
             on = true;
             c->ev_kind[c->ev_used / 2] = kind;
@@ -315,6 +338,7 @@ struct ProfScope {
     }
     ~ProfScope()
     {
+        nvtxRangePop();
         if (on) {
             cudaEventRecord(c->ev[c->ev_used + 1], s);
             c->ev_used += 2;
@@ -525,6 +549,12 @@ const char* lenia_status_string(lenia_status s)
         case LENIA_ENOTSUP: return "not supported";
     }
     return "unknown status";
+}
+
+lenia_status lenia_debug_fail_after(int32_t n_calls)
+{
+    g_fail_after.store(n_calls < 0 ? -1 : n_calls, std::memory_order_relaxed);
+    return LENIA_OK;
 }
 
 const char* lenia_last_error(const lenia_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -1320,8 +1350,8 @@ lenia_status lenia_selftest_wait_timeout(lenia_ctx* c, int32_t limit_mcycles, vo
     return LENIA_OK;
 }
 
-lenia_status lenia_step_host_async(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
-                                   float* stats_out, void* stream)
+static lenia_status host_step_enqueue(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out,
+                                      float* P_out, float* stats_out, void* stream)
 {
     if (!c) return LENIA_EINVAL;
     if (!A_in || !A_out || (c->n_p && (!P_in || !P_out)))
@@ -1329,21 +1359,41 @@ lenia_status lenia_step_host_async(lenia_ctx* c, const float* A_in, const float*
     const int C = c->cfg.n_channels;
     const size_t nA = c->N * C, nP = c->N * c->n_p * c->cfg.n_kernels;
     if (!c->up_stream) {
-        lenia_status a = dalloc(c, &c->d_hA_in1, nA);
-        if (a == LENIA_OK) a = dalloc(c, &c->d_hA_out1, nA);
-        if (a == LENIA_OK && nP) a = dalloc(c, &c->d_hP_in1, nP);
-        if (a == LENIA_OK && nP) a = dalloc(c, &c->d_hP_out1, nP);
-        if (a == LENIA_OK) a = dalloc(c, &c->d_hstats, (size_t)2 * C * 3);
+        lenia_status a = LENIA_OK;
+        if (!c->d_hA_in1) a = dalloc(c, &c->d_hA_in1, nA);
+        if (a == LENIA_OK && !c->d_hA_out1) a = dalloc(c, &c->d_hA_out1, nA);
+        if (a == LENIA_OK && nP && !c->d_hP_in1) a = dalloc(c, &c->d_hP_in1, nP);
+        if (a == LENIA_OK && nP && !c->d_hP_out1) a = dalloc(c, &c->d_hP_out1, nP);
+        if (a == LENIA_OK && !c->d_hstats) a = dalloc(c, &c->d_hstats, (size_t)2 * C * 3);
         if (a != LENIA_OK) return a;
-        CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking));
-        CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->down_stream, cudaStreamNonBlocking));
-        for (int b = 0; b < 2; b++) {
-            CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_up[b], cudaEventDisableTiming));
-            CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming));
-            CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->ev_down[b], cudaEventDisableTiming));
+        // streams and events are made into locals and kept only once all exist
+        cudaStream_t up = nullptr, down = nullptr;
+        cudaEvent_t evs[6] = {};
+        auto make = [&]() -> lenia_status {
+            CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking));
+            CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking));
+            for (int i = 0; i < 6; i++) CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming));
             // nothing recorded yet: record once so that the first waits are no-ops
-            CUDA_OR_FAIL(c, cudaEventRecord(c->ev_done[b], (cudaStream_t)stream));
-            CUDA_OR_FAIL(c, cudaEventRecord(c->ev_down[b], (cudaStream_t)stream));
+            for (int b = 0; b < 2; b++) {
+                CUDA_OR_FAIL(c, cudaEventRecord(evs[2 + b], (cudaStream_t)stream));
+                CUDA_OR_FAIL(c, cudaEventRecord(evs[4 + b], (cudaStream_t)stream));
+            }
+            return LENIA_OK;
+        };
+        const lenia_status ms = make();
+        if (ms != LENIA_OK) {
+            for (cudaEvent_t e : evs)
+                if (e) cudaEventDestroy(e);
+            if (up) cudaStreamDestroy(up);
+            if (down) cudaStreamDestroy(down);
+            return ms;
+        }
+        c->up_stream = up;
+        c->down_stream = down;
+        for (int b = 0; b < 2; b++) {
+            c->ev_up[b] = evs[b];
+            c->ev_done[b] = evs[2 + b];
+            c->ev_down[b] = evs[4 + b];
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -1380,6 +1430,23 @@ lenia_status lenia_step_host_async(lenia_ctx* c, const float* A_in, const float*
     c->host_set = b ^ 1;
     c->host_pending = true;
     return LENIA_OK;
+}
+
+lenia_status lenia_step_host_async(lenia_ctx* c, const float* A_in, const float* P_in, float* A_out, float* P_out,
+                                   float* stats_out, void* stream)
+{
+    const lenia_status st = host_step_enqueue(c, A_in, P_in, A_out, P_out, stats_out, stream);
+    if (st != LENIA_OK && st != LENIA_EINVAL && c && c->up_stream) {
+        // a failure after part of the step was enqueued: let every copy that
+        // touches the caller's host buffers finish before returning, so that
+        // none of them runs after the caller has reused its buffers
+        cudaStreamSynchronize(c->up_stream);
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaStreamSynchronize(c->down_stream);
+        (void)cudaGetLastError();
+        c->host_pending = false;
+    }
+    return st;
 }
 
 lenia_status lenia_host_wait(lenia_ctx* c, void* stream)

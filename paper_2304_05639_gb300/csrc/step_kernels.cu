@@ -22,22 +22,30 @@ __device__ __forceinline__ int wrapi(int i, int n)
 
 // ------------------------------------------------------- direct convolution
 // U_k(y, x) = sum_d K~_k(d) A_src(k)(y + d, x + d), periodic (K~ is point
-// symmetric, so this is the convolution K~ * A).  A block computes a 32 x 32
-// output tile of one kernel (grid z runs over the kernels, so that small
-// worlds still fill the GPU).  The input tile with its R halo is staged in
-// shared memory: by one tiled TMA box (the mbarrier wait is bounded) when it
-// lies inside the world, else - at the torus edges, where it wraps - by plain
-// loads.  Box columns start at a multiple of 4 floats (16 bytes), so the tile
-// carries up to 3 extra columns on the left: `off`.  Each thread owns one
-// column x and four rows; for each tap column dx it slides a four-row
-// register window down the non-zero taps of that column.
-constexpr int DC_TX = 32, DC_TY = 32, DC_ROWS = 4;
+// symmetric, so this is the convolution K~ * A).  A block of 32 x 8 threads
+// computes a (32 CX) x (8 RY) output tile of one kernel (grid z runs over the
+// kernels, so that small worlds still fill the GPU); thread (tx, ty) owns
+// columns tx + 32 j (j < CX, so that a warp's shared loads are contiguous)
+// and rows RY ty .. RY ty + RY - 1 of its tile.  The input tile with its R
+// halo is staged in shared memory: by one tiled TMA box (the mbarrier wait is
+// bounded) when it lies inside the world, else - at the torus edges, where it
+// wraps - by plain loads.  Box columns start at a multiple of 4 floats (16
+// bytes), so the tile carries up to 3 extra columns on the left: `off`.  For
+// each tap column dx the thread slides an RY-row register window down the
+// non-zero taps of that column: per tap, CX shared loads and one weight load
+// feed CX x RY fused multiply-adds.
+template <int CX, int RY>
+struct DcTile {
+    static constexpr int TW = 32 * CX, TH = 8 * RY;
+    __host__ __device__ static constexpr int pitch(int maxR) { return (TW + 2 * maxR + 3 + 3) / 4 * 4; }
+    __host__ __device__ static constexpr int rows(int maxR) { return TH + 2 * maxR; }
+    static size_t smem(int maxR) { return (size_t)pitch(maxR) * rows(maxR) * sizeof(float) + 128; }
+};
 
-__host__ __device__ constexpr int dc_pitch(int maxR) { return (DC_TX + 2 * maxR + 3 + 3) / 4 * 4; }
-__host__ __device__ constexpr int dc_rows(int maxR) { return DC_TY + 2 * maxR; }
-
+template <int CX, int RY>
 __global__ void __launch_bounds__(256) k_direct_conv(ConvParams p, int maxR, const __grid_constant__ CUtensorMap tm_a)
 {
+    using T = DcTile<CX, RY>;
     extern __shared__ __align__(128) unsigned char dc_raw[];
     float* tile = reinterpret_cast<float*>(dc_raw + ((128 - (smem_addr(dc_raw) & 127)) & 127));
     __shared__ __align__(8) uint64_t bar;
@@ -45,8 +53,8 @@ __global__ void __launch_bounds__(256) k_direct_conv(ConvParams p, int maxR, con
     int c = 0, t = blockIdx.z;
     while (c < p.C - 1 && t >= p.kcount[c]) t -= p.kcount[c++];
     const int k = p.klist[c][t];
-    const int x0 = blockIdx.x * DC_TX, y0 = blockIdx.y * DC_TY;
-    const int pitch = dc_pitch(maxR), rows = dc_rows(maxR);
+    const int x0 = blockIdx.x * T::TW, y0 = blockIdx.y * T::TH;
+    const int pitch = T::pitch(maxR), rows = T::rows(maxR);
     const int xs = (x0 - maxR) & ~3;                 // first staged column (may be negative)
     const int off = x0 - maxR - xs;                  // 0..3
     const int ys = y0 - maxR;
@@ -76,34 +84,46 @@ __global__ void __launch_bounds__(256) k_direct_conv(ConvParams p, int maxR, con
         __syncthreads();
     }
     const int tx = threadIdx.x;
-    const int ty = threadIdx.y * DC_ROWS;
-    const int x = x0 + tx;
+    const int ty = threadIdx.y * RY;
     const int R = p.R[k];
     const float* w = p.w + p.w_off[k];       // [dx + R][dy + R]
     const int* yr = p.yr + p.yr_off[k];
-    float acc[DC_ROWS] = {0.f, 0.f, 0.f, 0.f};
+    float acc[CX][RY];
+#pragma unroll
+    for (int j = 0; j < CX; j++)
+#pragma unroll
+        for (int o = 0; o < RY; o++) acc[j][o] = 0.f;
     for (int dx = -R; dx <= R; dx++) {
         const int r = __ldg(&yr[dx + R]);
         if (r < 0) continue;
         const float* col = tile + (size_t)(ty + maxR) * pitch + (tx + off + maxR + dx);
         const float* wc = w + (dx + R) * (2 * R + 1) + R;
-        float v[DC_ROWS];
+        float v[CX][RY];
 #pragma unroll
-        for (int o = 0; o < DC_ROWS - 1; o++) v[o] = col[(o - r) * pitch];
+        for (int j = 0; j < CX; j++)
+#pragma unroll
+            for (int o = 0; o < RY - 1; o++) v[j][o] = col[(o - r) * pitch + 32 * j];
+#pragma unroll 4
         for (int dy = -r; dy <= r; dy++) {
-            v[DC_ROWS - 1] = col[(dy + DC_ROWS - 1) * pitch];
             const float wv = __ldg(&wc[dy]);
 #pragma unroll
-            for (int o = 0; o < DC_ROWS; o++) acc[o] = fmaf(wv, v[o], acc[o]);
+            for (int j = 0; j < CX; j++) {
+                v[j][RY - 1] = col[(dy + RY - 1) * pitch + 32 * j];
 #pragma unroll
-            for (int o = 0; o < DC_ROWS - 1; o++) v[o] = v[o + 1];
+                for (int o = 0; o < RY; o++) acc[j][o] = fmaf(wv, v[j][o], acc[j][o]);
+#pragma unroll
+                for (int o = 0; o < RY - 1; o++) v[j][o] = v[j][o + 1];
+            }
         }
     }
-    if (x < p.W) {
 #pragma unroll
-        for (int o = 0; o < DC_ROWS; o++) {
+    for (int j = 0; j < CX; j++) {
+        const int x = x0 + tx + 32 * j;
+        if (x >= p.W) continue;
+#pragma unroll
+        for (int o = 0; o < RY; o++) {
             const int y = y0 + ty + o;
-            if (y < p.H) p.U[((size_t)k * p.H + y) * p.W + x] = acc[o];
+            if (y < p.H) p.U[((size_t)k * p.H + y) * p.W + x] = acc[j][o];
         }
     }
 }
@@ -146,24 +166,44 @@ static bool dc_map(CUtensorMap* out, const float* base, int W, int H, int C, int
     return true;
 }
 
-cudaError_t launch_direct_conv(const ConvParams& p, int max_R, cudaStream_t s)
+template <int CX, int RY>
+static cudaError_t launch_dc(const ConvParams& p, int max_R, int planes, cudaStream_t s)
 {
-    const int pitch = dc_pitch(max_R), rows = dc_rows(max_R);
-    const size_t smem = (size_t)pitch * rows * sizeof(float) + 128;     // + alignment of the TMA destination
+    using T = DcTile<CX, RY>;
+    const size_t smem = T::smem(max_R);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = smem_limit<k_direct_conv>(smem);
+    cudaError_t e = smem_limit<k_direct_conv<CX, RY>>(smem);
     if (e != cudaSuccess) return e;
     ConvParams q = p;
     CUtensorMap tm;
     memset(&tm, 0, sizeof(tm));
+    const int pitch = T::pitch(max_R), rows = T::rows(max_R);
     // worlds too narrow or short for an interior tile use plain loads only
     q.tma = p.W >= pitch && p.H >= rows && dc_map(&tm, p.A, p.W, p.H, p.C, pitch, rows);
+    dim3 grid((p.W + T::TW - 1) / T::TW, (p.H + T::TH - 1) / T::TH, planes);
+    k_direct_conv<CX, RY><<<grid, dim3(32, 8), smem, s>>>(q, max_R, tm);
+    return cudaGetLastError();
+}
+
+// 64 x 64 tiles (2 x 8 outputs per thread) when they give at least two blocks
+// per SM, else 32 x 32 (1 x 4) or 32 x 16 (1 x 2) tiles for parallelism.
+cudaError_t launch_direct_conv(const ConvParams& p, int max_R, cudaStream_t s)
+{
     int planes = 0;
     for (int c = 0; c < p.C; c++) planes += p.kcount[c];
     if (planes == 0) return cudaSuccess;
-    dim3 grid((p.W + DC_TX - 1) / DC_TX, (p.H + DC_TY - 1) / DC_TY, planes);
-    k_direct_conv<<<grid, dim3(32, DC_TY / DC_ROWS), smem, s>>>(q, max_R, tm);
-    return cudaGetLastError();
+    static int n_sms = 0;
+    if (n_sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n_sms = 148;
+    }
+    auto blocks = [&](int tw, int th) { return (long long)((p.W + tw - 1) / tw) * ((p.H + th - 1) / th) * planes; };
+    if (blocks(64, 64) >= 2LL * n_sms && DcTile<2, 8>::smem(max_R) <= 200 * 1024)
+        return launch_dc<2, 8>(p, max_R, planes, s);
+    if (blocks(32, 32) >= 2LL * n_sms) return launch_dc<1, 4>(p, max_R, planes, s);
+    return launch_dc<1, 2>(p, max_R, planes, s);
 }
 
 // ------------------------------------------------------------- epilogue

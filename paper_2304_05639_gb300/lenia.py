@@ -28,7 +28,8 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes", "lenia_batch_init",
            "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy",
            "lenia_selftest_wait_timeout", "lenia_set_walls", "lenia_step_evolve",
-           "lenia_step_host_async", "lenia_host_wait", "lenia_batch_group_of", "lenia_measure_fp32_peak")
+           "lenia_step_host_async", "lenia_host_wait", "lenia_batch_group_of", "lenia_measure_fp32_peak",
+           "lenia_debug_fail_after")
 PROFILE_KINDS = 10
 
 
@@ -114,6 +115,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_step_host_async.restype = st
     lib.lenia_host_wait.argtypes = [vp, vp]
     lib.lenia_host_wait.restype = st
+    lib.lenia_debug_fail_after.argtypes = [ctypes.c_int32]
+    lib.lenia_debug_fail_after.restype = st
     lib.lenia_kernel_weights.argtypes = [vp, ctypes.c_int32, vp]
     lib.lenia_kernel_weights.restype = st
     lib.lenia_conv_path.argtypes = [vp]
@@ -303,6 +306,12 @@ def lenia_set_genes(ctx, genes):
 
 def lenia_selftest_wait_timeout(ctx, limit_mcycles: int = 200, stream=None):
     _check(ctx, load().lenia_selftest_wait_timeout(ctx, int(limit_mcycles), _stream(stream)))
+
+
+def lenia_debug_fail_after(n_calls: int):
+    """Test hook: report the checked CUDA call after n_calls successful ones as
+    failed (n_calls < 0 disarms)."""
+    load().lenia_debug_fail_after(int(n_calls))
 
 
 def lenia_check(ctx, stream=None):
