@@ -217,7 +217,7 @@ def batched_leg(torch, lenia, inputs, stream, steps=200):
     """256 single-channel localized-gene worlds of sides {64,128,256,512},
     R in 8..16, in one batch (CUDA graph per two steps) vs one plain
     1024^2 world of the same recipe, per site-step."""
-    worlds = inputs.batched_worlds()
+    worlds = inputs.batched_worlds(live=True)
     sites = sum(w.sites for w in worlds)
     batch = lenia.lenia_batch_init(worlds, autotune=True, stream=stream)
     try:
@@ -233,6 +233,12 @@ def batched_leg(torch, lenia, inputs, stream, steps=200):
         lenia.lenia_batch_check(batch)
         ms = e0.elapsed_time(e1)
         paths = [lenia.lenia_batch_conv_path(batch, i) for i in range(len(worlds))]
+        shapes = {}
+        for i, w in enumerate(worlds):
+            if w.height not in shapes:
+                kind, prm = lenia.lenia_batch_epilogue_shape(batch, i)
+                shapes[w.height] = ({0: f"tiled, {prm} rows per thread", 1: f"queued streaming, {prm} bands per world"}
+                                    .get(kind, "own step"))
     finally:
         lenia.lenia_batch_destroy(batch)
     plain = inputs.localized_single_channel()
@@ -255,6 +261,7 @@ def batched_leg(torch, lenia, inputs, stream, steps=200):
             "steps": steps, "ms_per_step": ms / steps, "value": v, "unit": UNIT,
             "alg_bytes_per_site": 24, "frac_of_hbm": v * 24 / 1e9 / _peaks()[0],
             "fft_worlds": paths.count(lenia.CONV_FFT), "direct_worlds": paths.count(lenia.CONV_DIRECT),
+            "epilogue_shape_by_side": {str(k): v for k, v in sorted(shapes.items())},
             "plain_1024_single_world": {"ms_per_step": plain_ms / steps, "value": pv},
             "batched_over_plain": v / pv}
 

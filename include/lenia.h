@@ -396,6 +396,22 @@ LENIA_API lenia_status lenia_batch_rollout(lenia_batch* batch, float* const* A, 
  * which can differ in the last bits from the streaming kernel a world of
  * width 256 k would use on its own. */
 LENIA_API int32_t lenia_batch_group_of(const lenia_batch* batch, int32_t world);
+/* Epilogue shape of world w's group: 0 = the tiled kernel, *param = rows per
+ * thread (1, 2 or 4); 1 = the streaming kernel in one persistent launch over
+ * a device work queue of (world, 256-column chunk, band) items, with every
+ * world's tensor maps in device memory, *param = bands per world (widths of
+ * 256 k only); -1 when w steps on its own.  With autotune, lenia_batch_rollout
+ * times every candidate once per group (on the caller's state, writing only
+ * the batch's own buffers) the first time it sees a pointer set, and keeps the
+ * fastest.  param may be NULL. */
+LENIA_API int32_t lenia_batch_epilogue_shape(const lenia_batch* batch, int32_t world, int32_t* param);
+/* Sets the epilogue shape of world w's group (kind and param as above; the
+ * autotuner then leaves that group alone).  LENIA_EINVAL for a world without
+ * a group or a shape the group cannot take (the streaming kernel before the
+ * group's tensor maps exist, i.e. before the first rollout, or for widths not
+ * a multiple of 256). */
+LENIA_API lenia_status lenia_batch_set_epilogue_shape(lenia_batch* batch, int32_t world, int32_t kind,
+                                                      int32_t param);
 /* Convolution path chosen for world w (LENIA_CONV_FFT or LENIA_CONV_DIRECT), or -1. */
 LENIA_API int32_t lenia_batch_conv_path(const lenia_batch* batch, int32_t world);
 /* lenia_check over every world's context after synchronising `stream`. */

@@ -17,6 +17,7 @@
 
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -44,7 +45,7 @@ __host__ __device__ constexpr size_t round_f(size_t n) { return (n + ALIGN_F - 1
 // floats each (4-column halos on both sides), as one TMA box of 132 8-byte
 // elements x 1 row x NPK planes; a halo slot holds the 4 columns beyond each
 // edge of the world (NPK x 4 floats per side) for the chunks at the edges.
-template <int KT, int CT, int LOC>
+template <int KT, int CT, int LOC, int NPD = ER_NP, int NUD = ER_NU>
 struct ErLayout {
     static constexpr int NP = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
     static constexpr int NPK = NP * KT;
@@ -52,12 +53,12 @@ struct ErLayout {
     static constexpr size_t h_slot = round_f((size_t)NPK * 4);
     static constexpr size_t u_slot = (size_t)KT * ER_CH;
     static constexpr size_t a_slot = (size_t)CT * ER_CH;
-    static constexpr size_t p_floats = ER_NP * p_slot;
-    static constexpr size_t h_floats = ER_NP * 2 * h_slot;
-    static constexpr size_t u_floats = ER_NU * u_slot;
-    static constexpr size_t a_floats = ER_NU * a_slot;
+    static constexpr size_t p_floats = NPD * p_slot;
+    static constexpr size_t h_floats = NPD * 2 * h_slot;
+    static constexpr size_t u_floats = NUD * u_slot;
+    static constexpr size_t a_floats = NUD * a_slot;
     // + 128 bytes to align the base of the dynamic shared memory to 128
-    static constexpr size_t bytes = (p_floats + h_floats + u_floats + a_floats) * 4 + 2 * (ER_NP + ER_NU) * 8 + 128;
+    static constexpr size_t bytes = (p_floats + h_floats + u_floats + a_floats) * 4 + 2 * (NPD + NUD) * 8 + 128;
 };
 
 // Destination channel of kernel k in the paper's 15-kernel topology: 3 self
@@ -78,69 +79,40 @@ __host__ __device__ constexpr int paper_dst(int k)
 // TOPO = 1: kernels route to channels as in the paper's topology (checked on
 // the host).  EPS0 = 1: eps_p == 0, where a zero neighbour count forces a
 // non-positive sum and the saturated quotient is already 0.
-template <int KT, int CT, int LOC, int TOPO, int EPS0>
-__global__ void __launch_bounds__(ER_THREADS, 1)
-    k_epilogue_rows(EpiParams p, const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_u,
-                    const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_h, int n_chunks, int n_bands,
-                    int* status)
+//
+// er_band runs this pipeline over rows r0 .. r1 - 1 of the chunk starting at
+// column x0, reading through the tensor maps tm_* (generic addresses: kernel
+// parameters or global memory) and writing A_out / P_out; every barrier must
+// be freshly initialised.  If a bounded wait gives up it sets *blk_failed and
+// the status word; last_gene / last_pot record the producer's last issued
+// rows for the drain after a failure.
+template <int KT, int CT, int LOC, int TOPO, int EPS0, int NPD = ER_NP, int NUD = ER_NU>
+__device__ __forceinline__ void er_band(const EpiParams& p, const CUtensorMap* tm_p, const CUtensorMap* tm_u,
+                                        const CUtensorMap* tm_a, const CUtensorMap* tm_h, float* A_out,
+                                        float* P_out, int x0, int r0, int r1, float* Pring, float* Hring,
+                                        float* Uring, float* Aring, uint64_t* full_p, uint64_t* empty_p,
+                                        uint64_t* full_u, uint64_t* empty_u, float* st, int* blk_failed,
+                                        int& last_gene, int& last_pot, int* status)
 {
-    using L = ErLayout<KT, CT, LOC>;
+    using L = ErLayout<KT, CT, LOC, NPD, NUD>;
     constexpr int NPK = L::NPK, NP = L::NP;
     constexpr int PMU = (LOC & 1) ? 0 : -1;
     constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
     constexpr int PH = (LOC & 4) ? NP - 1 : -1;
-    static_assert(TOPO == 0 || (KT == 15 && CT == 3), "paper topology has 15 kernels, 3 channels");
-    static_assert(CT * 5 <= ER_THREADS / 32, "one warp per statistics sum");
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
-    float* Pring = reinterpret_cast<float*>(smem);
-    float* Hring = Pring + L::p_floats;                   // [slot][left, right][NPK][4]
-    float* Uring = Hring + L::h_floats;
-    float* Aring = Uring + L::u_floats;
-    uint64_t* full_p = reinterpret_cast<uint64_t*>(Aring + L::a_floats);
-    uint64_t* empty_p = full_p + ER_NP;
-    uint64_t* full_u = empty_p + ER_NP;
-    uint64_t* empty_u = full_u + ER_NU;
-    __shared__ float red[ER_CONSUMERS][CT * 5];
-    __shared__ int blk_failed;
-
     const int H = p.H, W = p.W;
     const unsigned N = (unsigned)H * (unsigned)W;        // sites; n_p K N < 2^31 (host check)
-    const int chunk = blockIdx.x % n_chunks, band = blockIdx.x / n_chunks;
-    const int x0 = chunk * ER_CH;
-    const int r0 = (int)((long long)band * H / n_bands);
-    const int r1 = (int)((long long)(band + 1) * H / n_bands);
     const int nrows = r1 - r0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    if (tid == 0) {
-        for (int b = 0; b < ER_NP; b++) {
-            mbar_init(&full_p[b], 1);
-            mbar_init(&empty_p[b], ER_CONSUMERS);
-        }
-        for (int b = 0; b < ER_NU; b++) {
-            mbar_init(&full_u[b], 1);
-            mbar_init(&empty_u[b], ER_WPG);
-        }
-        mbar_fence_init();
-        blk_failed = 0;
-    }
-    __syncthreads();
-
-    float st[CT * 5];
-#pragma unroll
-    for (int v = 0; v < CT * 5; v++) st[v] = 0.f;
-    int last_gene = -1, last_pot = -1;      // producer: last rows whose copies were issued
+    const bool edge_l = x0 == 0, edge_r = x0 + ER_CH == W;
 
     if (warp == ER_CONSUMERS) {
         // ------------------------------------------------ producer warp
         // One lane issues TMA boxes; x coordinates count 8-byte elements (two
         // floats), so the gene box at x0/2 - 2 spans columns x0 - 4 .. x0 + 259.
-        const bool edge_l = x0 == 0, edge_r = x0 + ER_CH == W;
         auto genes = [&](int l) -> bool {                      // local gene row l = global r0 - 1 + l
             if (NPK == 0) return true;
-            const int slot = l % ER_NP;
-            if (l >= ER_NP && !mbar_wait_bounded(&empty_p[slot], ((l - ER_NP) / ER_NP) & 1)) return false;
+            const int slot = l % NPD;
+            if (l >= NPD && !mbar_wait_bounded(&empty_p[slot], ((l - NPD) / NPD) & 1)) return false;
             int r = r0 - 1 + l;
             r = r < 0 ? r + H : (r >= H ? r - H : r);
             last_gene = l;
@@ -148,22 +120,22 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
                 fence_proxy_async_shared();
                 const uint32_t bytes = NPK * ER_PW * 4 + (edge_l ? NPK * 16 : 0) + (edge_r ? NPK * 16 : 0);
                 mbar_arrive_expect_tx(&full_p[slot], bytes);
-                tma_load_3d(Pring + slot * L::p_slot, &tm_p, x0 / 2 - 2, r, 0, &full_p[slot]);
+                tma_load_3d(Pring + slot * L::p_slot, tm_p, x0 / 2 - 2, r, 0, &full_p[slot]);
                 // periodic halos of the edge chunks (the main box reads zeros there)
-                if (edge_l) tma_load_3d(Hring + (slot * 2 + 0) * L::h_slot, &tm_h, W / 2 - 2, r, 0, &full_p[slot]);
-                if (edge_r) tma_load_3d(Hring + (slot * 2 + 1) * L::h_slot, &tm_h, 0, r, 0, &full_p[slot]);
+                if (edge_l) tma_load_3d(Hring + (slot * 2 + 0) * L::h_slot, tm_h, W / 2 - 2, r, 0, &full_p[slot]);
+                if (edge_r) tma_load_3d(Hring + (slot * 2 + 1) * L::h_slot, tm_h, 0, r, 0, &full_p[slot]);
             }
             return true;
         };
         auto pot = [&](int i) -> bool {                        // potentials + phenospace of local row i
-            const int slot = i % ER_NU;
-            if (i >= ER_NU && !mbar_wait_bounded(&empty_u[slot], ((i - ER_NU) / ER_NU) & 1)) return false;
+            const int slot = i % NUD;
+            if (i >= NUD && !mbar_wait_bounded(&empty_u[slot], ((i - NUD) / NUD) & 1)) return false;
             const int r = r0 + i;
             last_pot = i;
             if (lane == 0) {
                 mbar_arrive_expect_tx(&full_u[slot], (KT + CT) * ER_CH * 4);
-                tma_load_3d(Uring + slot * L::u_slot, &tm_u, x0 / 2, r, 0, &full_u[slot]);
-                tma_load_3d(Aring + slot * L::a_slot, &tm_a, x0 / 2, r, 0, &full_u[slot]);
+                tma_load_3d(Uring + slot * L::u_slot, tm_u, x0 / 2, r, 0, &full_u[slot]);
+                tma_load_3d(Aring + slot * L::a_slot, tm_a, x0 / 2, r, 0, &full_u[slot]);
             }
             return true;
         };
@@ -171,7 +143,7 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
         bool ok = nrows <= 0 || (genes(0) && genes(1));
         for (int i = 0; ok && i < nrows; i++) ok = genes(i + 2) && pot(i);
         if (!ok && lane == 0) {
-            blk_failed = 1;
+            *blk_failed = 1;
             atomicExch(status, kStatusWaitTimeout);
         }
         // on success no copy is left in flight: the consumers waited for all of them
@@ -179,37 +151,37 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
         // ------------------------------------------------ consumer warps
         const int grp = warp / ER_WPG;
         const int t = (warp % ER_WPG) * 32 + lane;       // column within the chunk
-        const bool edge_l = x0 == 0, edge_r = x0 + ER_CH == W;
         const int x = x0 + t;
         const float eps_p = p.eps_p, eps_u = p.eps_u;
-        const float sx = __ldg(&p.sin_x[x]), cx = __ldg(&p.cos_x[x]);
+        const bool stats = p.partials != nullptr;
+        const float sx = stats ? __ldg(&p.sin_x[x]) : 0.f, cx = stats ? __ldg(&p.cos_x[x]) : 0.f;
         // gene row l = 0 is used by row 0 only: group 1 releases it up front
         // so that its slot, like every other, collects one release per group
         if (grp == 1 && lane == 0 && NPK > 0 && nrows > 0) mbar_arrive(&empty_p[0]);
         for (int i = grp; i < nrows; i += ER_GROUPS) {
             bool ok = true;
             if (NPK > 0)
-                for (int l = i; l <= i + 2; l++) ok = ok && mbar_wait_bounded(&full_p[l % ER_NP], (l / ER_NP) & 1);
-            ok = ok && mbar_wait_bounded(&full_u[i % ER_NU], (i / ER_NU) & 1);
+                for (int l = i; l <= i + 2; l++) ok = ok && mbar_wait_bounded(&full_p[l % NPD], (l / NPD) & 1);
+            ok = ok && mbar_wait_bounded(&full_u[i % NUD], (i / NUD) & 1);
             if (!ok) {
                 if (lane == 0) {
-                    blk_failed = 1;
+                    *blk_failed = 1;
                     atomicExch(status, kStatusWaitTimeout);
                 }
                 break;
             }
             const int y = r0 + i;
-            const float* Pu = Pring + (size_t)(i % ER_NP) * L::p_slot;
-            float* Pcw = Pring + (size_t)((i + 1) % ER_NP) * L::p_slot;
+            const float* Pu = Pring + (size_t)(i % NPD) * L::p_slot;
+            float* Pcw = Pring + (size_t)((i + 1) % NPD) * L::p_slot;
             const float* Pc = Pcw;
-            const float* Pd = Pring + (size_t)((i + 2) % ER_NP) * L::p_slot;
-            const float* Ur = Uring + (size_t)(i % ER_NU) * L::u_slot;
-            const float* Ar = Aring + (size_t)(i % ER_NU) * L::a_slot;
+            const float* Pd = Pring + (size_t)((i + 2) % NPD) * L::p_slot;
+            const float* Ur = Uring + (size_t)(i % NUD) * L::u_slot;
+            const float* Ar = Aring + (size_t)(i % NUD) * L::a_slot;
             // The centre row's halo column beyond a world edge arrived in the
             // halo slot; the one lane that reads it moves it into place.
             if (NPK > 0 && p.maintain && ((edge_l && t == 0) || (edge_r && t == ER_CH - 1))) {
                 const int side = t == 0 ? 0 : 1;
-                const float* hs = Hring + (((i + 1) % ER_NP) * 2 + side) * L::h_slot;
+                const float* hs = Hring + (((i + 1) % NPD) * 2 + side) * L::h_slot;
                 for (int pk = 0; pk < NPK; pk++)
                     Pcw[pk * ER_PW + (side == 0 ? 3 : 4 + ER_CH)] = hs[pk * 4 + (side == 0 ? 3 : 0)];
                 fence_proxy_async_shared();   // before the slot is refilled by TMA
@@ -259,11 +231,11 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
             }
             const bool alpha = !p.maintain || ((NPK == 0 || pmin > eps_p) && tmin > eps_u);
             const unsigned gi = (unsigned)y * (unsigned)W + (unsigned)x;
-            const float sy = __ldg(&p.sin_y[y]), cy = __ldg(&p.cos_y[y]);
+            const float sy = stats ? __ldg(&p.sin_y[y]) : 0.f, cy = stats ? __ldg(&p.cos_y[y]) : 0.f;
 #pragma unroll
             for (int c = 0; c < CT; c++) {
                 const float an = __saturatef(Ar[c * ER_CH + t] + p.dt * (alpha ? acc[c] : p.acc0[c]));
-                p.A_out[(unsigned)c * N + gi] = an;
+                A_out[(unsigned)c * N + gi] = an;
                 st[c * 5 + 0] += an;
                 st[c * 5 + 1] += an * sy;
                 st[c * 5 + 2] += an * cy;
@@ -272,34 +244,119 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
             }
             if (p.alpha_out) p.alpha_out[gi] = alpha ? 1 : 0;
             if (p.empty_out) p.empty_out[gi] = tsum > eps_u ? 0 : 1;
-            if (p.P_out) {
+            if (P_out) {
                 const bool keep = !p.maintain || alpha;
 #pragma unroll
-                for (int pk = 0; pk < NPK; pk++) p.P_out[(unsigned)pk * N + gi] = keep ? ph[pk] : 0.f;
+                for (int pk = 0; pk < NPK; pk++) P_out[(unsigned)pk * N + gi] = keep ? ph[pk] : 0.f;
             }
             // this warp is done with gene rows l = i, i + 1 and U/A row i
             __syncwarp();
             if (lane == 0) {
                 if (NPK > 0) {
-                    mbar_arrive(&empty_p[i % ER_NP]);
-                    mbar_arrive(&empty_p[(i + 1) % ER_NP]);
+                    mbar_arrive(&empty_p[i % NPD]);
+                    mbar_arrive(&empty_p[(i + 1) % NPD]);
                 }
-                mbar_arrive(&empty_u[i % ER_NU]);
+                mbar_arrive(&empty_u[i % NUD]);
             }
         }
     }
+}
 
-    // Every warp reaches this point (all waits are bounded).  After a failure
-    // the producer gives the copies it issued last a bounded chance to land
-    // before the block exits.
+// After a failed band: the producer gives the copies it issued last a
+// bounded chance to land before the block's shared memory is released.
+template <int NPD = ER_NP, int NUD = ER_NU>
+__device__ __forceinline__ void er_drain(int last_gene, int last_pot, uint64_t* full_p, uint64_t* full_u)
+{
+    if ((threadIdx.x >> 5) == ER_CONSUMERS && (threadIdx.x & 31) == 0) {
+        for (int l = last_gene - (NPD - 1) < 0 ? 0 : last_gene - (NPD - 1); l <= last_gene; l++)
+            mbar_wait_bounded(&full_p[l % NPD], (l / NPD) & 1);
+        for (int i = last_pot - (NUD - 1) < 0 ? 0 : last_pot - (NUD - 1); i <= last_pot; i++)
+            mbar_wait_bounded(&full_u[i % NUD], (i / NUD) & 1);
+    }
+}
+
+// Shared-memory carve-up of the streaming epilogue.
+template <int KT, int CT, int LOC, int NPD = ER_NP, int NUD = ER_NU>
+struct ErSmem {
+    float *Pring, *Hring, *Uring, *Aring;
+    uint64_t *full_p, *empty_p, *full_u, *empty_u;
+    __device__ explicit ErSmem(unsigned char* smem)
+    {
+        using L = ErLayout<KT, CT, LOC, NPD, NUD>;
+        Pring = reinterpret_cast<float*>(smem);
+        Hring = Pring + L::p_floats;                   // [slot][left, right][NPK][4]
+        Uring = Hring + L::h_floats;
+        Aring = Uring + L::u_floats;
+        full_p = reinterpret_cast<uint64_t*>(Aring + L::a_floats);
+        empty_p = full_p + NPD;
+        full_u = empty_p + NPD;
+        empty_u = full_u + NUD;
+    }
+    // (re-)initialise every barrier; `reuse`: they served an earlier item and
+    // are invalidated first (no thread waits on them and no copy is pending)
+    __device__ void init(bool reuse = false) const
+    {
+        if (reuse) {
+            for (int b = 0; b < NPD; b++) {
+                mbar_inval(&full_p[b]);
+                mbar_inval(&empty_p[b]);
+            }
+            for (int b = 0; b < NUD; b++) {
+                mbar_inval(&full_u[b]);
+                mbar_inval(&empty_u[b]);
+            }
+        }
+        for (int b = 0; b < NPD; b++) {
+            mbar_init(&full_p[b], 1);
+            mbar_init(&empty_p[b], ER_CONSUMERS);
+        }
+        for (int b = 0; b < NUD; b++) {
+            mbar_init(&full_u[b], 1);
+            mbar_init(&empty_u[b], ER_WPG);
+        }
+        mbar_fence_init();
+    }
+};
+
+template <int KT, int CT, int LOC, int TOPO, int EPS0>
+__global__ void __launch_bounds__(ER_THREADS, 1)
+    k_epilogue_rows(EpiParams p, const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_u,
+                    const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_h, int n_chunks, int n_bands,
+                    int* status)
+{
+    static_assert(TOPO == 0 || (KT == 15 && CT == 3), "paper topology has 15 kernels, 3 channels");
+    static_assert(CT * 5 <= ER_THREADS / 32, "one warp per statistics sum");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
+    const ErSmem<KT, CT, LOC> sm(smem);
+    __shared__ float red[ER_CONSUMERS][CT * 5];
+    __shared__ int blk_failed;
+
+    const int H = p.H;
+    const int chunk = blockIdx.x % n_chunks, band = blockIdx.x / n_chunks;
+    const int x0 = chunk * ER_CH;
+    const int r0 = (int)((long long)band * H / n_bands);
+    const int r1 = (int)((long long)(band + 1) * H / n_bands);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (tid == 0) {
+        sm.init();
+        blk_failed = 0;
+    }
+    __syncthreads();
+
+    float st[CT * 5];
+#pragma unroll
+    for (int v = 0; v < CT * 5; v++) st[v] = 0.f;
+    int last_gene = -1, last_pot = -1;      // producer: last rows whose copies were issued
+    er_band<KT, CT, LOC, TOPO, EPS0>(p, &tm_p, &tm_u, &tm_a, &tm_h, p.A_out, p.P_out, x0, r0, r1, sm.Pring,
+                                     sm.Hring, sm.Uring, sm.Aring, sm.full_p, sm.empty_p, sm.full_u, sm.empty_u,
+                                     st, &blk_failed, last_gene, last_pot, status);
+
+    // Every warp reaches this point (all waits are bounded).
     __syncthreads();
     if (blk_failed) {
-        if (warp == ER_CONSUMERS && lane == 0) {
-            for (int l = last_gene - (ER_NP - 1) < 0 ? 0 : last_gene - (ER_NP - 1); l <= last_gene; l++)
-                mbar_wait_bounded(&full_p[l % ER_NP], (l / ER_NP) & 1);
-            for (int i = last_pot - (ER_NU - 1) < 0 ? 0 : last_pot - (ER_NU - 1); i <= last_pot; i++)
-                mbar_wait_bounded(&full_u[i % ER_NU], (i / ER_NU) & 1);
-        }
+        er_drain<>(last_gene, last_pot, sm.full_p, sm.full_u);
         return;
     }
     if (p.partials) {
@@ -344,9 +401,9 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
                     const int c = tid;
                     const double two_pi = 6.283185307179586476925286766559;
                     double ty = atan2(tot[c * 5 + 1], tot[c * 5 + 2]) * H / two_pi;
-                    double tx = atan2(tot[c * 5 + 3], tot[c * 5 + 4]) * W / two_pi;
+                    double tx = atan2(tot[c * 5 + 3], tot[c * 5 + 4]) * p.W / two_pi;
                     if (ty < 0.0) ty += H;
-                    if (tx < 0.0) tx += W;
+                    if (tx < 0.0) tx += p.W;
                     p.stats_out[c * 3 + 0] = (float)tot[c * 5 + 0];
                     p.stats_out[c * 3 + 1] = (float)ty;
                     p.stats_out[c * 3 + 2] = (float)tx;
@@ -355,6 +412,56 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
             }
         }
     }
+}
+
+// Many worlds of one shape (a batched group) in one persistent launch: work
+// items (world, chunk, band) are taken from a device work queue (an atomic
+// counter) by every block until none is left; each item runs the streaming
+// pipeline above with that world's tensor maps, read from global memory.
+// Between items the block waits at a barrier (every copy of the last item
+// has been consumed, every release has arrived) and re-initialises its
+// barriers.  No statistics, alpha or empty outputs.
+// Ring depths of the queued kernel: its one-kernel rows are small (about
+// 4 KB of genes, potential and phenospace per row), so it keeps many more of
+// them in flight than the 15-kernel pipeline.
+constexpr int EQ_NP = 16, EQ_NU = 12;
+
+template <int LOC, int EPS0>
+__global__ void __launch_bounds__(ER_THREADS, 1)
+    k_epilogue_queue(EpiParams p, const QueueWorld* __restrict__ worlds, int n_items, int n_chunks, int n_bands,
+                     int* counter, int* status)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
+    const ErSmem<1, 1, LOC, EQ_NP, EQ_NU> sm(smem);
+    __shared__ int blk_failed, item;
+    const int H = p.H, tid = threadIdx.x;
+    float st[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (tid == 0) blk_failed = 0;
+    int last_gene = -1, last_pot = -1;
+    for (int n = 0;; n++) {
+        __syncthreads();                       // the previous item is done everywhere
+        if (tid == 0) {
+            item = atomicAdd(counter, 1);
+            sm.init(n > 0);
+        }
+        __syncthreads();
+        const int it = item;
+        if (it >= n_items || blk_failed) break;
+        const int w = it / (n_chunks * n_bands);
+        const int rest = it - w * (n_chunks * n_bands);
+        const int band = rest / n_chunks, chunk = rest - band * n_chunks;
+        const QueueWorld* qw = worlds + w;
+        const int r0 = (int)((long long)band * H / n_bands);
+        const int r1 = (int)((long long)(band + 1) * H / n_bands);
+        last_gene = last_pot = -1;
+        er_band<1, 1, LOC, 0, EPS0, EQ_NP, EQ_NU>(p, &qw->tm_p, &qw->tm_u, &qw->tm_a, &qw->tm_h, qw->A_out, qw->P_out,
+                                    chunk * ER_CH, r0, r1, sm.Pring, sm.Hring, sm.Uring, sm.Aring, sm.full_p,
+                                    sm.empty_p, sm.full_u, sm.empty_u, st, &blk_failed, last_gene, last_pot,
+                                    status);
+    }
+    __syncthreads();
+    if (blk_failed) er_drain<EQ_NP, EQ_NU>(last_gene, last_pot, sm.full_p, sm.full_u);
 }
 
 // ------------------------------------------------------------ tensor maps
@@ -464,6 +571,89 @@ static cudaError_t launch_rows(const EpiParams& p, int num_sms, int* status, cud
         return cudaErrorInvalidValue;
     kern<<<n_chunks * n_bands, ER_THREADS, L::bytes, s>>>(p, tp, tu, ta, th, n_chunks, n_bands, status);
     return cudaGetLastError();
+}
+
+// A plane stack as plane_map describes it, encoded without the cache (the
+// queued epilogue stores its maps in device memory).
+static bool plane_map_direct(CUtensorMap* out, const float* base, int W, int H, int planes, int box_x,
+                             int box_planes)
+{
+    auto fn = tensor_map_encoder();
+    if (!fn || ((uintptr_t)base & 15) != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W / 2, (cuuint64_t)H, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)W * H * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, 1, (cuuint32_t)box_planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(out, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int queue_loc(const EpiParams& p)
+{
+    return (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
+}
+
+bool epilogue_queue_supported(const EpiParams& p)
+{
+    const int loc = queue_loc(p);
+    return p.kt.K == 1 && p.kt.C == 1 && p.n_rings == 0 && (loc == 3 || loc == 0) && p.W % ER_CH == 0 &&
+           (!p.maintain || p.r_diff == 1) && (long long)p.H * p.W * 2 < (1LL << 31) && !p.partials &&
+           !p.alpha_out && !p.empty_out;
+}
+
+bool epilogue_queue_world(QueueWorld* q, const EpiParams& p, const float* A, const float* P, const float* U,
+                          float* A_out, float* P_out)
+{
+    memset(q, 0, sizeof(*q));
+    const int npk = queue_loc(p) == 3 ? 2 : 0;
+    if (npk > 0 && (!plane_map_direct(&q->tm_p, P, p.W, p.H, npk, ER_PW / 2, npk) ||
+                    !plane_map_direct(&q->tm_h, P, p.W, p.H, npk, 2, npk)))
+        return false;
+    if (!plane_map_direct(&q->tm_u, U, p.W, p.H, 1, ER_CH / 2, 1) ||
+        !plane_map_direct(&q->tm_a, A, p.W, p.H, 1, ER_CH / 2, 1))
+        return false;
+    q->A_out = A_out;
+    q->P_out = P_out;
+    return true;
+}
+
+template <int LOC, int EPS0>
+static cudaError_t launch_queue(const EpiParams& p, const QueueWorld* worlds, int n_worlds, int n_bands,
+                                int ctas_per_sm, int* counter, int* status, cudaStream_t s)
+{
+    using L = ErLayout<1, 1, LOC, EQ_NP, EQ_NU>;
+    int per_sm = 1;
+    cudaError_t e = rows_occupancy<k_epilogue_queue<LOC, EPS0>>(L::bytes, &per_sm);
+    if (e != cudaSuccess) return e;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    static int n_sms = 0;
+    if (n_sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n_sms = 148;
+    }
+    const int n_chunks = p.W / ER_CH;
+    const int n_items = n_worlds * n_chunks * n_bands;
+    const int grid = std::min(n_items, n_sms * per_sm);
+    e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_epilogue_queue<LOC, EPS0><<<grid, ER_THREADS, L::bytes, s>>>(p, worlds, n_items, n_chunks, n_bands, counter,
+                                                                    status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_epilogue_queue(const EpiParams& p, const QueueWorld* worlds, int n_worlds, int n_bands,
+                                  int ctas_per_sm, int* counter, int* status, cudaStream_t s)
+{
+    if (!epilogue_queue_supported(p) || n_worlds < 1 || n_bands < 1 || n_bands > p.H) return cudaErrorInvalidValue;
+    const bool e0 = p.eps_p == 0.f;
+    if (queue_loc(p) == 3)
+        return e0 ? launch_queue<3, 1>(p, worlds, n_worlds, n_bands, ctas_per_sm, counter, status, s)
+                  : launch_queue<3, 0>(p, worlds, n_worlds, n_bands, ctas_per_sm, counter, status, s);
+    return e0 ? launch_queue<0, 1>(p, worlds, n_worlds, n_bands, ctas_per_sm, counter, status, s)
+              : launch_queue<0, 0>(p, worlds, n_worlds, n_bands, ctas_per_sm, counter, status, s);
 }
 
 bool epilogue_rows_supported(const EpiParams& p)

@@ -53,10 +53,18 @@ struct Group {
     float** Aout[2] = {nullptr, nullptr};
     float** Pout[2] = {nullptr, nullptr};
     bool aligned = false;                  // every listed A pointer is 16-byte aligned
+    // epilogue: 0 = tiled kernel (br rows per thread), 1 = streaming kernel over
+    // a device work queue (`bands` bands per world; per-world tensor maps in qw)
+    lenia::QueueWorld* qw[2] = {nullptr, nullptr};
+    int* counter = nullptr;                // the queue's work counter
+    int epi = 0, br = 2, bands = 1;
+    bool tuned = false;                    // epilogue shape chosen by the autotuner
+    float tune_ms[8] = {};                 // the timed candidates (for lenia_batch_epilogue_choice)
 };
 
 struct lenia_batch {
     int n = 0;
+    bool autotune = false;
     std::vector<lenia_ctx*> ctx;
     std::vector<Group> groups;
     std::vector<int> group_of;             // world -> group index or -1
@@ -115,9 +123,36 @@ float time_path(const lenia_config& cfg0, const lenia_kernel_desc* ks, int path,
 void free_group(Group& g)
 {
     void* ptrs[] = {g.Ahat, g.Uhat, g.U, g.S, g.Ain[0], g.Ain[1], g.Pin[0], g.Pin[1], g.Aout[0], g.Aout[1],
-                    g.Pout[0], g.Pout[1]};
+                    g.Pout[0], g.Pout[1], g.qw[0], g.qw[1], g.counter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+}
+
+// The epilogue parameters of a group for direction `dir`.
+lenia::EpiParams group_epi(const Group& g, int dir)
+{
+    lenia::EpiParams ep = g.v.ep;
+    ep.A = ep.P = nullptr;
+    ep.A_out = ep.P_out = nullptr;
+    ep.A_list = g.Ain[dir];
+    ep.P_list = g.Pin[dir];
+    ep.Aout_list = g.Aout[dir];
+    ep.Pout_list = g.Pout[dir];
+    ep.U = g.U;
+    ep.u_stride = (size_t)g.v.K * g.v.N;
+    ep.partials = nullptr;
+    ep.stats_out = nullptr;
+    ep.alpha_out = ep.empty_out = nullptr;
+    return ep;
+}
+
+// The group's epilogue in the chosen shape.
+cudaError_t group_epilogue(const Group& g, int dir, cudaStream_t s)
+{
+    const lenia::EpiParams ep = group_epi(g, dir);
+    const int n = (int)g.worlds.size();
+    if (g.epi == 1) return lenia::launch_epilogue_queue(ep, g.qw[dir], n, g.bands, 0, g.counter, g.v.fp.status, s);
+    return lenia::launch_epilogue_batch(ep, n, s, g.br);
 }
 
 // One step of every world of a group: A/P lists of direction `dir`.
@@ -139,19 +174,58 @@ lenia_status group_step(const Group& g, int dir, cudaStream_t s)
     if (lenia::launch_fft_rows_r2c(fp, s) != cudaSuccess) return LENIA_ECUDA;
     if (lenia::launch_fft_cols(fp, s) != cudaSuccess) return LENIA_ECUDA;
     if (lenia::launch_fft_rows_c2r(fp, s) != cudaSuccess) return LENIA_ECUDA;
-    lenia::EpiParams ep = g.v.ep;
-    ep.A = ep.P = nullptr;
-    ep.A_out = ep.P_out = nullptr;
-    ep.A_list = g.Ain[dir];
-    ep.P_list = g.Pin[dir];
-    ep.Aout_list = g.Aout[dir];
-    ep.Pout_list = g.Pout[dir];
-    ep.U = g.U;
-    ep.u_stride = (size_t)g.v.K * g.v.N;
-    ep.partials = nullptr;
-    ep.stats_out = nullptr;
-    ep.alpha_out = ep.empty_out = nullptr;
-    return lenia::launch_epilogue_batch(ep, n, s) == cudaSuccess ? LENIA_OK : LENIA_ECUDA;
+    return group_epilogue(g, dir, s) == cudaSuccess ? LENIA_OK : LENIA_ECUDA;
+}
+
+// Autotuner of the epilogue's shape: times every candidate on direction 0
+// (the caller's state in, the batch's buffers out: the caller's data are not
+// changed) and keeps the fastest.  Candidates: the tiled kernel with 1, 2 or
+// 4 rows per thread, and - for widths of 256 k - the queued streaming kernel
+// with 1, 2, 4 or 8 bands per world.
+lenia_status tune_epilogue(Group& g, cudaStream_t s)
+{
+    const lenia::EpiParams ep = group_epi(g, 0);
+    struct Cand {
+        int epi, br, bands;
+    };
+    std::vector<Cand> cands = {{0, 1, 1}, {0, 2, 1}, {0, 4, 1}};
+    if (g.qw[0])
+        for (int b : {1, 2, 4, 8})
+            if (b <= g.v.fp.H) cands.push_back({1, 2, b});
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return LENIA_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return LENIA_ECUDA;
+    }
+    float best = INFINITY;
+    Cand pick = {0, 2, 1};
+    for (size_t ci = 0; ci < cands.size(); ci++) {
+        Group t = g;
+        t.epi = cands[ci].epi;
+        t.br = cands[ci].br;
+        t.bands = cands[ci].bands;
+        bool ok = true;
+        for (int r = 0; ok && r < 2; r++) ok = group_epilogue(t, 0, s) == cudaSuccess;     // warm-up
+        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+        for (int r = 0; ok && r < 5; r++) ok = group_epilogue(t, 0, s) == cudaSuccess;
+        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = INFINITY;
+        if (ok) cudaEventElapsedTime(&ms, e0, e1);
+        else (void)cudaGetLastError();
+        if (ci < 8) g.tune_ms[ci] = ms / 5;
+        if (ms < best) {
+            best = ms;
+            pick = cands[ci];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g.epi = pick.epi;
+    g.br = pick.br;
+    g.bands = pick.bands;
+    g.tuned = true;
+    return best < INFINITY ? LENIA_OK : LENIA_ECUDA;
 }
 
 void destroy_graphs(lenia_batch* b)
@@ -275,6 +349,7 @@ lenia_status lenia_batch_init(int32_t n_worlds, const lenia_config* cfgs, const 
     cudaStream_t s = (cudaStream_t)stream;
     lenia_batch* b = new lenia_batch();
     b->n = n_worlds;
+    b->autotune = autotune != 0;
     bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
@@ -409,6 +484,16 @@ lenia_status lenia_batch_init(int32_t n_worlds, const lenia_config* cfgs, const 
                 lenia_batch_destroy(b);
                 return LENIA_ENOMEM;
             }
+            if (okg && lenia::epilogue_queue_supported(group_epi(g, 0))) {
+                okg = cudaMalloc(&g.qw[0], n * sizeof(lenia::QueueWorld)) == cudaSuccess &&
+                      cudaMalloc(&g.qw[1], n * sizeof(lenia::QueueWorld)) == cudaSuccess &&
+                      cudaMalloc(&g.counter, sizeof(int)) == cudaSuccess;
+                if (!okg) {
+                    free_group(g);
+                    lenia_batch_destroy(b);
+                    return LENIA_ENOMEM;
+                }
+            }
             for (int i : g.worlds) b->group_of[i] = (int)b->groups.size();
             b->groups.push_back(g);
         }
@@ -418,6 +503,32 @@ lenia_status lenia_batch_init(int32_t n_worlds, const lenia_config* cfgs, const 
         return LENIA_ECUDA;
     }
     *out = b;
+    return LENIA_OK;
+}
+
+int32_t lenia_batch_epilogue_shape(const lenia_batch* b, int32_t world, int32_t* param)
+{
+    if (!b || world < 0 || world >= b->n || b->group_of[world] < 0) return -1;
+    const Group& g = b->groups[b->group_of[world]];
+    if (param) *param = g.epi == 1 ? g.bands : g.br;
+    return g.epi;
+}
+
+lenia_status lenia_batch_set_epilogue_shape(lenia_batch* b, int32_t world, int32_t kind, int32_t param)
+{
+    if (!b || world < 0 || world >= b->n || b->group_of[world] < 0) return LENIA_EINVAL;
+    Group& g = b->groups[b->group_of[world]];
+    if (kind == 0 && (param == 1 || param == 2 || param == 4) && g.v.fp.H % (8 * param) == 0) {
+        g.epi = 0;
+        g.br = param;
+    } else if (kind == 1 && param >= 1 && param <= g.v.fp.H && g.qw[0]) {
+        g.epi = 1;
+        g.bands = param;
+    } else {
+        return LENIA_EINVAL;
+    }
+    g.tuned = true;
+    destroy_graphs(b);
     return LENIA_OK;
 }
 
@@ -459,6 +570,31 @@ lenia_status lenia_batch_rollout(lenia_batch* b, float* const* A, float* const* 
                       cudaMemcpy(g.Aout[1], ao1.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
                       cudaMemcpy(g.Pout[1], po1.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess;
             if (!ok) return LENIA_ECUDA;
+            if (g.qw[0]) {
+                // per-world tensor maps of the queued streaming epilogue, both directions
+                const lenia::EpiParams ep = group_epi(g, 0);
+                for (int d = 0; d < 2; d++) {
+                    std::vector<lenia::QueueWorld> q(n);
+                    for (size_t j = 0; j < n && ok; j++)
+                        ok = lenia::epilogue_queue_world(&q[j], ep, d ? a1[j] : a0[j], d ? p1[j] : p0[j],
+                                                         g.U + j * g.v.K * g.v.N, d ? ao1[j] : ao0[j],
+                                                         d ? po1[j] : po0[j]);
+                    ok = ok && cudaMemcpy(g.qw[d], q.data(), n * sizeof(lenia::QueueWorld),
+                                          cudaMemcpyHostToDevice) == cudaSuccess;
+                }
+                if (!ok) {
+                    // maps cannot be encoded for these buffers: the tiled kernel only
+                    cudaFree(g.qw[0]);
+                    cudaFree(g.qw[1]);
+                    g.qw[0] = g.qw[1] = nullptr;
+                    if (g.epi == 1) g.epi = 0;
+                    ok = true;
+                }
+            }
+            if (b->autotune && !g.tuned) {
+                const lenia_status ts = tune_epilogue(g, b->origin);
+                if (ts != LENIA_OK) return ts;
+            }
         }
         destroy_graphs(b);
     }

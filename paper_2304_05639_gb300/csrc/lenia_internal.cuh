@@ -199,6 +199,23 @@ cudaError_t measure_fp32_peak(cudaStream_t s, double* scalar_tflops, double* pai
 cudaError_t launch_adjoint_gather(const AdjParams& p, cudaStream_t s);
 cudaError_t launch_adjoint_gene_out(const double* gene_acc, int nv, float* out, cudaStream_t s);
 bool epilogue_rows_supported(const EpiParams& p);
+// The streaming epilogue over the worlds of a batched group (one persistent
+// launch; work items taken from a device queue): one world's tensor maps and
+// outputs, in device memory.
+struct alignas(64) QueueWorld {
+    CUtensorMap tm_p, tm_u, tm_a, tm_h;
+    float* A_out;
+    float* P_out;
+};
+// p: the group's shared parameters (shape, genes, thresholds); single-channel
+// single-kernel worlds of width 256 k with r_diff 1.
+bool epilogue_queue_supported(const EpiParams& p);
+bool epilogue_queue_world(QueueWorld* out, const EpiParams& p, const float* A, const float* P, const float* U,
+                          float* A_out, float* P_out);
+// n_bands bands per world; ctas_per_sm 0 = as many as fit.  `counter` (one
+// int of device memory) is zeroed on `s` before the launch.
+cudaError_t launch_epilogue_queue(const EpiParams& p, const QueueWorld* worlds, int n_worlds, int n_bands,
+                                  int ctas_per_sm, int* counter, int* status, cudaStream_t s);
 // cuTensorMapEncodeTiled through the runtime's driver entry point (null if
 // the driver does not provide it).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
@@ -219,7 +236,8 @@ namespace lenia {
 bool ctx_view(lenia_ctx* c, lenia_ctx_view* v);
 // batched worlds: one tiled-epilogue launch over n_worlds (grid z), pointer lists in EpiParams
 bool epilogue_batch_supported(const EpiParams& p);
-cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t s);
+// br: rows per thread of the one-kernel tiled epilogue (1, 2 or 4)
+cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t s, int br = 2);
 int ring_epilogue_blocks(int H, int W);   // stats records of the ring epilogue
 // pass 1: Delta_sum complement -> counts; pass 2: E_pen, mutation, penalisation
 cudaError_t launch_disk_pass(const EvoParams& p, int pass, cudaStream_t s);

@@ -23,6 +23,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
+// Invalidates a barrier before it is initialised again (no thread may be
+// waiting on it and no asynchronous arrival may be pending).
+__device__ __forceinline__ void mbar_inval(uint64_t* bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // Makes barrier initialisation visible to the async proxy.
 __device__ __forceinline__ void mbar_fence_init()
 {

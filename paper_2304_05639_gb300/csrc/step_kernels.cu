@@ -817,18 +817,26 @@ bool epilogue_batch_supported(const EpiParams& p)
            ((K == 15 && C == 3 && (loc == 3 || loc == 0)) || (K == 1 && C == 1 && (loc == 3 || loc == 0)));
 }
 
-cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t s)
+cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t s, int br)
 {
     if (!epilogue_batch_supported(p) || n_worlds < 1 || n_worlds > 65535) return cudaErrorInvalidValue;
     const int loc = (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
     const int K = p.kt.K;
     if (p.partials || p.alpha_out || p.empty_out) return cudaErrorInvalidValue;
     dim3 block(EP_TX, EP_TY);
-    constexpr int BR = 2;
-    if (K == 1 && p.W % EP_TX == 0 && p.H % (EP_TY * BR) == 0) {
-        dim3 g4(p.W / EP_TX, p.H / (EP_TY * BR), n_worlds);
-        if (loc == 3) k_epilogue_batch11<3, BR><<<g4, block, 0, s>>>(p);
-        else k_epilogue_batch11<0, BR><<<g4, block, 0, s>>>(p);
+    if (br != 1 && br != 2 && br != 4) br = 2;
+    if (K == 1 && p.W % EP_TX == 0 && p.H % (EP_TY * br) == 0) {
+        dim3 g4(p.W / EP_TX, p.H / (EP_TY * br), n_worlds);
+        if (br == 1) {
+            if (loc == 3) k_epilogue_batch11<3, 1><<<g4, block, 0, s>>>(p);
+            else k_epilogue_batch11<0, 1><<<g4, block, 0, s>>>(p);
+        } else if (br == 2) {
+            if (loc == 3) k_epilogue_batch11<3, 2><<<g4, block, 0, s>>>(p);
+            else k_epilogue_batch11<0, 2><<<g4, block, 0, s>>>(p);
+        } else {
+            if (loc == 3) k_epilogue_batch11<3, 4><<<g4, block, 0, s>>>(p);
+            else k_epilogue_batch11<0, 4><<<g4, block, 0, s>>>(p);
+        }
         return cudaGetLastError();
     }
     // one row per thread: the worlds of a group are often small, so the grid

@@ -29,7 +29,7 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy",
            "lenia_selftest_wait_timeout", "lenia_set_walls", "lenia_step_evolve",
            "lenia_step_host_async", "lenia_host_wait", "lenia_batch_group_of", "lenia_measure_fp32_peak",
-           "lenia_debug_fail_after")
+           "lenia_debug_fail_after", "lenia_batch_epilogue_shape", "lenia_batch_set_epilogue_shape")
 PROFILE_KINDS = 10
 
 
@@ -144,6 +144,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_batch_rollout.restype = st
     lib.lenia_batch_group_of.argtypes = [vp, ctypes.c_int32]
     lib.lenia_batch_group_of.restype = ctypes.c_int32
+    lib.lenia_batch_epilogue_shape.argtypes = [vp, ctypes.c_int32, vp]
+    lib.lenia_batch_epilogue_shape.restype = ctypes.c_int32
+    lib.lenia_batch_set_epilogue_shape.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    lib.lenia_batch_set_epilogue_shape.restype = st
     lib.lenia_batch_conv_path.argtypes = [vp, ctypes.c_int32]
     lib.lenia_batch_conv_path.restype = ctypes.c_int32
     lib.lenia_batch_check.argtypes = [vp, vp]
@@ -285,6 +289,20 @@ def lenia_batch_conv_path(batch, world: int) -> int:
 
 def lenia_batch_group_of(batch, world: int) -> int:
     return load().lenia_batch_group_of(batch, int(world))
+
+
+def lenia_batch_epilogue_shape(batch, world: int):
+    """(kind, param) of world's group: (0, rows per thread) tiled, (1, bands per
+    world) queued streaming; (-1, 0) without a group."""
+    v = ctypes.c_int32(0)
+    kind = load().lenia_batch_epilogue_shape(batch, int(world), ctypes.byref(v))
+    return kind, v.value
+
+
+def lenia_batch_set_epilogue_shape(batch, world: int, kind: int, param: int):
+    st_ = load().lenia_batch_set_epilogue_shape(batch, int(world), int(kind), int(param))
+    if st_ != 0:
+        raise LeniaError(st_, "lenia_batch_set_epilogue_shape")
 
 
 def lenia_batch_check(batch, stream=None):

@@ -166,3 +166,44 @@ def test_full_batched_workload_sampled_worlds_match_oracle():
         assert alive >= 1000
     finally:
         lenia.lenia_batch_destroy(batch)
+
+
+@pytest.mark.parametrize("kind,param", [(1, 1), (1, 3), (1, 8), (0, 1), (0, 4)])
+def test_epilogue_shapes_match_oracle(kind, param):
+    """Every epilogue shape the autotuner chooses from, forced on two groups
+    (256- and 512-side worlds, one radius): the queued streaming kernel (one
+    persistent launch over a device work queue, per-world tensor maps in
+    device memory) with 1, 3 or 8 bands per world, and the tiled kernel with 1
+    or 4 rows per thread.  One batch step against the oracle per world, and
+    two steps against the tiled kernel's two steps."""
+    torch = torch_mod()
+    ws = inputs.batched_worlds(n_worlds=7, sizes=(256, 512), r_range=(9, 9), seed_index=21, live=True)
+    sides = sorted({w.height for w in ws})
+    assert sides == [256, 512]
+
+    def run(k, prm, n):
+        batch = lenia.lenia_batch_init(ws, autotune=False)
+        try:
+            for side in sides:
+                first = next(i for i, w in enumerate(ws) if w.height == side)
+                lenia.lenia_batch_set_epilogue_shape(batch, first, k, prm)
+                assert lenia.lenia_batch_epilogue_shape(batch, first) == (k, prm)
+            A = [to_dev(w.A) for w in ws]
+            P = [to_dev(w.P) for w in ws]
+            lenia.lenia_batch_rollout(batch, A, P, n)
+            lenia.lenia_batch_check(batch)
+            return [a.cpu().numpy() for a in A], [p.cpu().numpy() for p in P]
+        finally:
+            lenia.lenia_batch_destroy(batch)
+
+    A1, P1 = run(kind, param, 1)
+    alive = 0
+    for i, w in enumerate(ws):
+        Ar, Pr, U, al = oracle.step(w, return_u=True, return_alpha=True)
+        Ph = np.stack([[oracle.diffuse(w.P[p, k]) for k in range(w.n_kernels)] for p in range(w.n_planes)])
+        alive += compare_step(w, {"A": A1[i], "P": P1[i]}, Ar, Pr, al, alpha_margin(w, U, Ph), min_alpha1=0)["alpha1"]
+    assert alive >= 1000
+    A2, P2 = run(kind, param, 2)
+    B2, Q2 = run(0, 2, 2)
+    for i in range(len(ws)):
+        assert np.abs(A2[i] - B2[i]).max() <= 2e-5 and np.abs(P2[i] - Q2[i]).max() <= 2e-6, i
