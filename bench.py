@@ -445,7 +445,7 @@ def _time_steps(torch, lenia, ctx, A, P, A2, P2, stream, n):
     return step_ms, {k: v[0] / max(1, v[1]) for k, v in prof.items()}
 
 
-def direct_leg(torch, lenia, inputs, stream, fp32_peak=None, bf16_peak=None, steps=50):
+def direct_leg(torch, lenia, inputs, stream, fp32_peak=None, bf16_peak=None, steps=50, only=None):
     """The direct convolution routes.  FP32 direct sums (TMA-staged tiles,
     kernels over grid z): the 64^2 one-kernel world (R = 13) as a rollout, and
     R = 5 worlds where the automatic choice is the direct path (1024^2 one
@@ -456,8 +456,12 @@ def direct_leg(torch, lenia, inputs, stream, fp32_peak=None, bf16_peak=None, ste
     out = {}
     w = inputs.single_kernel_global()
     cfg, ks = lenia.config_from_world(w, lenia.CONV_DIRECT)
-    ctx = lenia.lenia_init(cfg, ks, stream)
+    if only not in (None, "c1_direct"):
+        cfg = None
+    ctx = lenia.lenia_init(cfg, ks, stream) if cfg is not None else None
     try:
+        if ctx is None:
+            raise StopIteration
         a = torch.from_numpy(w.A).cuda()
         lenia.lenia_rollout(ctx, a, None, 10, None, stream)
         torch.cuda.synchronize()
@@ -469,14 +473,19 @@ def direct_leg(torch, lenia, inputs, stream, fp32_peak=None, bf16_peak=None, ste
         lenia.lenia_check(ctx)
         out["c1_direct"] = {"workload": "64x64, 1 channel, 1 kernel R=13, global genes, 100-step rollout, direct path",
                             "us_per_step": e0.elapsed_time(e1) * 1e3 / 100}
+    except StopIteration:
+        pass
     finally:
-        lenia.lenia_destroy(ctx)
+        if ctx is not None:
+            lenia.lenia_destroy(ctx)
     cases = (("r5_1024", inputs.localized_single_channel(R=5), lenia.CONV_AUTO),
              ("r5_2048_c3", inputs.multi_channel(R=5, matched=True), lenia.CONV_AUTO),
              ("c3_fft", inputs.multi_channel(matched=True), lenia.CONV_FFT),
              ("c3_bf16", inputs.multi_channel(matched=True), lenia.CONV_DIRECT_BF16),
              ("c3_bf16x3", inputs.multi_channel(matched=True), lenia.CONV_DIRECT_BF16X3))
     for name, w, path in cases:
+        if only is not None and name != only:
+            continue
         cfg, ks = lenia.config_from_world(w, path)
         ctx = lenia.lenia_init(cfg, ks, stream)
         try:
@@ -803,6 +812,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batched-world, evolution, ring and small-world legs")
     ap.add_argument("--size", type=int, default=2048, help="torus side (2048 = the benchmark workload)")
     ap.add_argument("--conv-path", type=int, default=0, help="0 auto, 1 fft, 2 direct")
+    ap.add_argument("--direct-case", default=None,
+                    choices=["c1_direct", "r5_1024", "r5_2048_c3", "c3_fft", "c3_bf16", "c3_bf16x3"],
+                    help="with --leg direct: run this case alone (for profiling)")
     ap.add_argument("--leg", default=None, choices=["adjoint", "batched", "evolve", "rings", "small", "direct"],
                     help="run only this extra leg (N = 1) and print its JSON object (for profiling)")
     args = ap.parse_args()
@@ -835,7 +847,8 @@ def run_leg(args):
     elif args.leg == "small":
         out = small_legs(torch, lenia, inputs, stream, max(lenia.lenia_measure_fp32_peak(stream)))
     elif args.leg == "direct":
-        out = direct_leg(torch, lenia, inputs, stream, max(lenia.lenia_measure_fp32_peak(stream)), _bf16_peak())
+        out = direct_leg(torch, lenia, inputs, stream, max(lenia.lenia_measure_fp32_peak(stream)), _bf16_peak(),
+                         steps=args.steps, only=args.direct_case)
     else:
         out = rings_leg(torch, lenia, inputs, stream, steps=args.steps)
     print(json.dumps({"leg": args.leg, **out}), flush=True)

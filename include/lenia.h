@@ -166,7 +166,14 @@ LENIA_API lenia_status lenia_step(lenia_ctx* ctx, const float* A_in, const float
  * device) receives n_steps * C * 3 floats, step s at offset s*C*3.
  * Without stats_out and with n_steps >= 4, pairs of steps replay a CUDA
  * graph that the context captures for its (A, P) pointers and genes (the
- * first such call captures it; calls with other buffers capture again). */
+ * first such call captures it; calls with other buffers capture again).
+ * Small worlds with global genes on the direct route (conv_path
+ * LENIA_CONV_DIRECT, no gene maps, H and W multiples of 8, H W <= 128 x 128)
+ * instead run a rollout without stats_out of n_steps >= 2 as one cooperative
+ * launch: every block keeps an 8 x 8 tile for the whole rollout and the
+ * blocks meet at a bounded grid barrier after each step; its results equal
+ * repeated lenia_step calls to FP32 rounding (direct sums in the same order,
+ * the growth through expf). */
 LENIA_API lenia_status lenia_rollout(lenia_ctx* ctx, float* A, float* P, int32_t n_steps,
                            float* stats_out, void* stream);
 

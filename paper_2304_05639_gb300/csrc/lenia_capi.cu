@@ -34,6 +34,9 @@ struct lenia_ctx {
     // device scratch (library-owned)
     float* d_w = nullptr;
     int* d_w_off = nullptr;
+    // small worlds with global genes: rollouts in one cooperative launch
+    bool small = false;
+    unsigned* d_small_count = nullptr;
     // tensor-core route (LENIA_CONV_DIRECT_BF16 / _BF16X3)
     uint16_t* d_tc_hi = nullptr;
     uint16_t* d_tc_lo = nullptr;
@@ -580,7 +583,7 @@ void lenia_destroy(lenia_ctx* c)
                     c->d_Ahat_t, c->d_Uhat_t, c->d_ticket, c->d_walls, c->d_alpha_e, c->d_empty,
                     c->d_cnt, c->d_Useg, c->d_hA_in1, c->d_hP_in1, c->d_hA_out1,
                     c->d_hP_out1, c->d_hstats, c->d_tc_hi, c->d_tc_lo, c->d_tc_B, c->d_tc_ks,
-                    c->d_tc_grp, c->d_tc_has};
+                    c->d_tc_grp, c->d_tc_has, c->d_small_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -753,7 +756,12 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         klist[sc][kcount[sc]++] = k;
     }
 
-    if (path == LENIA_CONV_DIRECT) {
+    // small worlds with global genes on the direct route: their rollouts run
+    // as one cooperative launch over the direct tap tables
+    c->small = c->n_p == 0 && !cfg->maintain_genes && c->cfg.n_rings == 0 && cfg->conv_path == LENIA_CONV_DIRECT &&
+               small_rollout_supported(H, W, C, NC, c->max_R);
+    if (c->small) ALLOC(c->d_small_count, 1);
+    if (path == LENIA_CONV_DIRECT || c->small) {
         std::vector<float> w;
         std::vector<int> woff(NC), yr, yroff(NC);
         for (int k = 0; k < NC; k++) {
@@ -791,6 +799,9 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         for (int k = 0; k < NC; k++) c->cp.R[k] = c->conv_R[k];
         memcpy(c->cp.kcount, kcount, sizeof(kcount));
         memcpy(c->cp.klist, klist, sizeof(klist));
+    }
+    if (path == LENIA_CONV_DIRECT) {
+        // tables built above
     } else if (tc) {
         // Toeplitz blocks of every plane and row offset dy (BF16 high and low
         // parts), K-step ranges, and the blocks' kernel groups
@@ -1034,6 +1045,31 @@ lenia_status lenia_rollout(lenia_ctx* c, float* A, float* P, int32_t n_steps, fl
     if (!A || (c->n_p && !P)) return fail(c, LENIA_EINVAL, "A (and P with localized genes) must be non-null");
     if (n_steps == 0) return LENIA_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (c->small && !stats_out && n_steps >= 2) {
+        // one cooperative launch for the whole rollout (small world, global genes)
+        SmallRolloutParams sp;
+        memset(&sp, 0, sizeof(sp));
+        sp.A = A;
+        sp.buf = c->d_A2;
+        sp.w = c->cp.w;
+        sp.w_off = c->cp.w_off;
+        sp.yr = c->cp.yr;
+        sp.yr_off = c->cp.yr_off;
+        for (int k = 0; k < c->cfg.n_kernels; k++) sp.R[k] = c->cp.R[k];
+        sp.kt = c->kt;
+        sp.H = c->cfg.height;
+        sp.W = c->cfg.width;
+        sp.C = c->cfg.n_channels;
+        sp.maxR = c->max_R;
+        sp.growth_form = c->cfg.growth_form;
+        sp.dt = c->cfg.dt;
+        sp.n_steps = n_steps;
+        sp.count = c->d_small_count;
+        sp.status = c->d_status;
+        ProfScope ps(c, KIND_DIRECT, s);
+        CUDA_OR_FAIL(c, launch_small_rollout(sp, s));
+        return LENIA_OK;
+    }
     // per-step statistics go to per-step addresses, and short rollouts do not
     // repay a capture: launch directly
     if (stats_out || n_steps < 4) return rollout_body(c, A, P, n_steps, stats_out, s);

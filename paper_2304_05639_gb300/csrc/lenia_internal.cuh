@@ -134,6 +134,26 @@ bool tc_conv_supported(int H, int W, int max_R);
 size_t tc_block_bytes_host(int kp);
 cudaError_t launch_conv_tc(const TcConvParams& p, const float* A, cudaStream_t s);
 
+// Rollouts of small worlds with global genes in one cooperative launch
+// (small_rollout.cu); tap tables as in ConvParams.
+struct SmallRolloutParams {
+    float* A;                  // [C][H][W], in and out
+    float* buf;                // second state
+    const float* w;
+    const int* w_off;
+    const int* yr;
+    const int* yr_off;
+    int R[kMaxKernels];
+    KernelTable kt;
+    int H, W, C, maxR, growth_form, n_steps;
+    float dt;
+    unsigned* count;           // grid barrier counter (zeroed by the launcher)
+    int* status;
+};
+size_t small_rollout_smem(int C, int maxR);
+bool small_rollout_supported(int H, int W, int C, int K, int maxR);
+cudaError_t launch_small_rollout(const SmallRolloutParams& p, cudaStream_t s);
+
 // Spectral (FFT) convolution.
 struct FftParams {
     const float* A;            // [C][H][W]
