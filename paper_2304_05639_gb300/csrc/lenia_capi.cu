@@ -37,6 +37,8 @@ struct lenia_ctx {
     // small worlds with global genes: rollouts in one cooperative launch
     bool small = false;
     unsigned* d_small_count = nullptr;
+    int2* d_small_taps = nullptr;
+    std::vector<int> small_tap_off;
     // tensor-core route (LENIA_CONV_DIRECT_BF16 / _BF16X3)
     uint16_t* d_tc_hi = nullptr;
     uint16_t* d_tc_lo = nullptr;
@@ -583,7 +585,7 @@ void lenia_destroy(lenia_ctx* c)
                     c->d_Ahat_t, c->d_Uhat_t, c->d_ticket, c->d_walls, c->d_alpha_e, c->d_empty,
                     c->d_cnt, c->d_Useg, c->d_hA_in1, c->d_hP_in1, c->d_hA_out1,
                     c->d_hP_out1, c->d_hstats, c->d_tc_hi, c->d_tc_lo, c->d_tc_B, c->d_tc_ks,
-                    c->d_tc_grp, c->d_tc_has, c->d_small_count};
+                    c->d_tc_grp, c->d_tc_has, c->d_small_count, c->d_small_taps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -757,11 +759,33 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
     }
 
     // small worlds with global genes on the direct route: their rollouts run
-    // as one cooperative launch over the direct tap tables
-    c->small = c->n_p == 0 && !cfg->maintain_genes && c->cfg.n_rings == 0 && cfg->conv_path == LENIA_CONV_DIRECT &&
-               small_rollout_supported(H, W, C, NC, c->max_R);
-    if (c->small) ALLOC(c->d_small_count, 1);
-    if (path == LENIA_CONV_DIRECT || c->small) {
+    // as one cooperative launch over every kernel's non-zero taps (in the
+    // direct route's order: tap columns dx, then rows dy)
+    if (c->n_p == 0 && !cfg->maintain_genes && c->cfg.n_rings == 0 && cfg->conv_path == LENIA_CONV_DIRECT &&
+        NC == K) {
+        std::vector<int2> taps;
+        c->small_tap_off.assign(1, 0);
+        for (int k = 0; k < NC; k++) {
+            const int R = c->conv_R[k], n = 2 * R + 1;
+            for (int dx = -R; dx <= R; dx++)
+                for (int dy = -R; dy <= R; dy++) {
+                    const double v = c->conv_w[k][(size_t)(dy + R) * n + (dx + R)];
+                    if (v == 0.0) continue;
+                    const float f = (float)v;
+                    int bits;
+                    memcpy(&bits, &f, 4);
+                    taps.push_back(make_int2((dy + 1024) * 2048 + (dx + 1024), bits));
+                }
+            c->small_tap_off.push_back((int)taps.size());
+        }
+        c->small = small_rollout_supported(H, W, C, NC, c->max_R, (int)taps.size());
+        if (c->small) {
+            ALLOC(c->d_small_count, 1);
+            ALLOC(c->d_small_taps, taps.size());
+            CK_INIT(cudaMemcpy(c->d_small_taps, taps.data(), taps.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        }
+    }
+    if (path == LENIA_CONV_DIRECT) {
         std::vector<float> w;
         std::vector<int> woff(NC), yr, yroff(NC);
         for (int k = 0; k < NC; k++) {
@@ -800,9 +824,7 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         memcpy(c->cp.kcount, kcount, sizeof(kcount));
         memcpy(c->cp.klist, klist, sizeof(klist));
     }
-    if (path == LENIA_CONV_DIRECT) {
-        // tables built above
-    } else if (tc) {
+    if (tc) {
         // Toeplitz blocks of every plane and row offset dy (BF16 high and low
         // parts), K-step ranges, and the blocks' kernel groups
         const int Rm = c->max_R, nt = TC_NT, n_dy = 2 * Rm + 1;
@@ -883,7 +905,7 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
         c->tp.n_dy = n_dy;
         c->tp.n_groups = (int)grp.size() / (2 + TC_NG);
         c->tp.terms = path == LENIA_CONV_DIRECT_BF16X3 ? 3 : 1;
-    } else {
+    } else if (path == LENIA_CONV_FFT) {
         const int M = W / 2, HS = H / 2 + 1;
         ALLOC(c->d_Ahat, (size_t)C * H * M);
         ALLOC(c->d_Uhat, (size_t)NC * H * M);
@@ -1051,11 +1073,9 @@ lenia_status lenia_rollout(lenia_ctx* c, float* A, float* P, int32_t n_steps, fl
         memset(&sp, 0, sizeof(sp));
         sp.A = A;
         sp.buf = c->d_A2;
-        sp.w = c->cp.w;
-        sp.w_off = c->cp.w_off;
-        sp.yr = c->cp.yr;
-        sp.yr_off = c->cp.yr_off;
-        for (int k = 0; k < c->cfg.n_kernels; k++) sp.R[k] = c->cp.R[k];
+        sp.taps = c->d_small_taps;
+        for (int k = 0; k <= c->cfg.n_kernels; k++) sp.tap_off[k] = c->small_tap_off[k];
+        sp.n_taps = c->small_tap_off.back();
         sp.kt = c->kt;
         sp.H = c->cfg.height;
         sp.W = c->cfg.width;
@@ -1353,12 +1373,9 @@ lenia_status lenia_step_evolve(lenia_ctx* c, float* A, float* P, float* A_out, f
     e.pen_thresh = t < -1.0 ? -1LL : (t > e.n_disk2 ? (long long)e.n_disk2 : (long long)t);
     if (!c->n_p) e.mut_plane = e.pen_plane = -1;
     {
-        ProfScope ps(c, KIND_OXY, s);
-        CUDA_OR_FAIL(c, launch_disk_pass(e, 1, s));
-    }
-    {
+        // both disk passes in one launch (kind "pen_disk")
         ProfScope ps(c, KIND_PEN, s);
-        CUDA_OR_FAIL(c, launch_disk_pass(e, 2, s));
+        CUDA_OR_FAIL(c, launch_disk_fused(e, s));
     }
     return LENIA_OK;
 }

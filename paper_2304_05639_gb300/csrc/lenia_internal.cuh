@@ -139,19 +139,17 @@ cudaError_t launch_conv_tc(const TcConvParams& p, const float* A, cudaStream_t s
 struct SmallRolloutParams {
     float* A;                  // [C][H][W], in and out
     float* buf;                // second state
-    const float* w;
-    const int* w_off;
-    const int* yr;
-    const int* yr_off;
-    int R[kMaxKernels];
+    const int2* taps;          // non-zero taps of every kernel: ((dy + 1024) 2048 + dx + 1024, weight bits)
+    int tap_off[kMaxKernels + 1];   // kernel k's taps: tap_off[k] .. tap_off[k + 1] - 1
+    int n_taps;
     KernelTable kt;
     int H, W, C, maxR, growth_form, n_steps;
     float dt;
     unsigned* count;           // grid barrier counter (zeroed by the launcher)
     int* status;
 };
-size_t small_rollout_smem(int C, int maxR);
-bool small_rollout_supported(int H, int W, int C, int K, int maxR);
+size_t small_rollout_smem(int C, int maxR, int n_taps);
+bool small_rollout_supported(int H, int W, int C, int K, int maxR, int n_taps);
 cudaError_t launch_small_rollout(const SmallRolloutParams& p, cudaStream_t s);
 
 // Spectral (FFT) convolution.
@@ -261,6 +259,8 @@ cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t
 int ring_epilogue_blocks(int H, int W);   // stats records of the ring epilogue
 // pass 1: Delta_sum complement -> counts; pass 2: E_pen, mutation, penalisation
 cudaError_t launch_disk_pass(const EvoParams& p, int pass, cudaStream_t s);
+// both passes in one launch (counts kept in shared memory)
+cudaError_t launch_disk_fused(const EvoParams& p, cudaStream_t s);
 cudaError_t launch_walls_zero(const int* idx, int n, float* A, int C, float* P, int npk, size_t N,
                               cudaStream_t s);
 

@@ -5,11 +5,12 @@
 // A world of a few thousand sites cannot fill the GPU with one launch per
 // stage: every step of the regular route is four or five short launches, and
 // their start-up latency, not the arithmetic, sets the step time.  Here every
-// block owns an 8 x 8 tile of sites for the whole rollout.  Per step it
+// block owns an 8 x 8 tile of sites for the whole rollout (four threads per
+// site).  Per step it
 // stages the tile's neighbourhood of every channel (radius maxR, periodic)
 // from the current state into shared memory, computes each kernel's
-// potential at its sites as a direct sum (the same FP32 tap tables as the
-// direct route), the growth G = h (2 g - 1) or h g with g = exp(-(U - mu)^2 /
+// potential at its sites as a direct sum over the kernel's non-zero taps (in
+// the order of the direct route: tap columns dx, then rows dy), the growth G = h (2 g - 1) or h g with g = exp(-(U - mu)^2 /
 // 2 sigma^2), and the clipped update, writes the next state, and meets the
 // other blocks at a grid barrier.  The barrier is a counter in device memory
 // (zeroed before the launch) that each block increments once per step and
@@ -39,7 +40,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, int* status)
 {
     __shared__ int ok;
     __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
+    if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(count, 1u);
         ok = 1;
@@ -58,20 +59,39 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, int* status)
     return ok != 0;
 }
 
-__global__ void __launch_bounds__(SR_T* SR_T) k_small_rollout(SmallRolloutParams p)
+// Four threads per site (consecutive lanes), each summing every fourth tap
+// of each kernel with two alternating accumulators; the four partial sums
+// meet in a shuffle tree, and the first thread of the site forms the growth
+// and the update.  The non-zero taps of every kernel (offset in the staged
+// tile, weight) are copied into shared memory once per rollout, so the tap
+// loop reads shared memory only.
+constexpr int SR_Q = 4;
+constexpr int SR_THREADS = SR_T * SR_T * SR_Q;
+
+__global__ void __launch_bounds__(SR_THREADS) k_small_rollout(SmallRolloutParams p)
 {
-    extern __shared__ float tiles[];                 // [C][(T + 2R)^2]
+    extern __shared__ float smem_f[];
     const int R = p.maxR, TP = SR_T + 2 * R;
     const int H = p.H, W = p.W, C = p.C;
     const size_t N = (size_t)H * W;
+    float* tiles = smem_f;                               // [C][TP * TP]
+    float* tw = tiles + (size_t)C * TP * TP;             // [n_taps] weights
+    int* toff = reinterpret_cast<int*>(tw + p.n_taps);   // [n_taps] offsets dy TP + dx
+    for (int i = threadIdx.x; i < p.n_taps; i += SR_THREADS) {
+        const int2 t = __ldg(&p.taps[i]);                // ((dy + 1024) 2048 + dx + 1024, weight bits)
+        const int dy = t.x / 2048 - 1024, dx = t.x % 2048 - 1024;
+        toff[i] = dy * TP + dx;
+        tw[i] = __int_as_float(t.y);
+    }
     const int tiles_x = W / SR_T;
     const int x0 = (blockIdx.x % tiles_x) * SR_T, y0 = (blockIdx.x / tiles_x) * SR_T;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * SR_T + tx;
+    const int tid = threadIdx.x, site = tid / SR_Q, q = tid % SR_Q;
+    const int tx = site % SR_T, ty = site / SR_T;
     const int x = x0 + tx, y = y0 + ty;
     for (int t = 0; t < p.n_steps; t++) {
         const float* src = (t % 2 == 0) ? p.A : p.buf;
         float* dst = (t % 2 == 0) ? p.buf : p.A;
-        for (int u = tid; u < C * TP * TP; u += SR_T * SR_T) {
+        for (int u = tid; u < C * TP * TP; u += SR_THREADS) {
             const int c = u / (TP * TP), r = u % (TP * TP);
             int yy = y0 - R + r / TP, xx = x0 - R + r % TP;
             yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
@@ -82,29 +102,33 @@ __global__ void __launch_bounds__(SR_T* SR_T) k_small_rollout(SmallRolloutParams
         float acc[kMaxChannels];
         for (int c = 0; c < C; c++) acc[c] = 0.f;
         for (int k = 0; k < p.kt.K; k++) {
-            const int Rk = p.R[k];
-            const float* wk = p.w + p.w_off[k];      // [dx + Rk][dy + Rk]
-            const int* yr = p.yr + p.yr_off[k];
             const float* tl = tiles + (size_t)p.kt.src[k] * TP * TP + (ty + R) * TP + (tx + R);
-            float u = 0.f;
-            for (int dx = -Rk; dx <= Rk; dx++) {
-                const int r = __ldg(&yr[dx + Rk]);
-                const float* wc = wk + (dx + Rk) * (2 * Rk + 1) + Rk;
-                for (int dy = -r; dy <= r; dy++) u = fmaf(__ldg(&wc[dy]), tl[dy * TP + dx], u);
+            const int i0 = p.tap_off[k], i1 = p.tap_off[k + 1];
+            float u0 = 0.f, u1 = 0.f;
+            int i = i0 + q;
+            for (; i + SR_Q < i1; i += 2 * SR_Q) {
+                u0 = fmaf(tw[i], tl[toff[i]], u0);
+                u1 = fmaf(tw[i + SR_Q], tl[toff[i + SR_Q]], u1);
             }
+            if (i < i1) u0 = fmaf(tw[i], tl[toff[i]], u0);
+            float u = u0 + u1;
+            u += __shfl_xor_sync(0xffffffffu, u, 1);
+            u += __shfl_xor_sync(0xffffffffu, u, 2);
             const float sg = p.kt.sigma[k], h = p.kt.h[k];
             const float z = (u - p.kt.mu[k]) / sg;
             const float g = sg > 0.f ? expf(-0.5f * z * z) : 0.f;
             acc[p.kt.dst[k]] += p.growth_form == 0 ? h * (2.f * g - 1.f) : h * g;
         }
-        const size_t i = (size_t)y * W + x;
-        for (int c = 0; c < C; c++) {
-            const float a = tiles[(size_t)c * TP * TP + (ty + R) * TP + (tx + R)] + p.dt * acc[c];
-            dst[(size_t)c * N + i] = fminf(fmaxf(a, 0.f), 1.f);
+        if (q == 0) {
+            const size_t i = (size_t)y * W + x;
+            for (int c = 0; c < C; c++) {
+                const float a = tiles[(size_t)c * TP * TP + (ty + R) * TP + (tx + R)] + p.dt * acc[c];
+                dst[(size_t)c * N + i] = fminf(fmaxf(a, 0.f), 1.f);
+            }
         }
         if (!grid_barrier(p.count, (unsigned)(t + 1) * gridDim.x, p.status)) return;
     }
-    if (p.n_steps % 2) {
+    if (p.n_steps % 2 && q == 0) {
         // the last step wrote the second buffer: this block's sites back to A
         const size_t i = (size_t)y * W + x;
         for (int c = 0; c < C; c++) p.A[(size_t)c * N + i] = __ldcg(&p.buf[(size_t)c * N + i]);
@@ -113,24 +137,24 @@ __global__ void __launch_bounds__(SR_T* SR_T) k_small_rollout(SmallRolloutParams
 
 }  // namespace
 
-size_t small_rollout_smem(int C, int maxR)
+size_t small_rollout_smem(int C, int maxR, int n_taps)
 {
     const size_t tp = SR_T + 2 * (size_t)maxR;
-    return (size_t)C * tp * tp * sizeof(float);
+    return (size_t)C * tp * tp * sizeof(float) + (size_t)n_taps * 8;
 }
 
-bool small_rollout_supported(int H, int W, int C, int K, int maxR)
+bool small_rollout_supported(int H, int W, int C, int K, int maxR, int n_taps)
 {
     if (H % SR_T || W % SR_T || (long long)H * W > 128 * 128 || C > kMaxChannels || K > kMaxKernels) return false;
-    if (small_rollout_smem(C, maxR) > 96 * 1024) return false;
+    if (small_rollout_smem(C, maxR, n_taps) > 160 * 1024) return false;
     int dev = 0, n_sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return false;
-    const size_t smem = small_rollout_smem(C, maxR);
+    const size_t smem = small_rollout_smem(C, maxR, n_taps);
     if (cudaFuncSetAttribute(k_small_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_rollout, SR_T * SR_T, smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_rollout, SR_THREADS, smem) != cudaSuccess)
         return false;
     return (long long)(H / SR_T) * (W / SR_T) <= (long long)per_sm * n_sms;
 }
@@ -139,12 +163,12 @@ cudaError_t launch_small_rollout(const SmallRolloutParams& p, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(p.count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    const size_t smem = small_rollout_smem(p.C, p.maxR);
+    const size_t smem = small_rollout_smem(p.C, p.maxR, p.n_taps);
     e = cudaFuncSetAttribute(k_small_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SmallRolloutParams q = p;
     void* args[] = {&q};
-    const dim3 grid((p.H / SR_T) * (p.W / SR_T)), block(SR_T, SR_T);
+    const dim3 grid((p.H / SR_T) * (p.W / SR_T)), block(SR_THREADS);
     return cudaLaunchCooperativeKernel((const void*)k_small_rollout, grid, block, args, smem, s);
 }
 
