@@ -34,7 +34,7 @@ namespace lenia {
 // from there (its stores follow the pass's barrier, so the two layouts may
 // share the buffer).  Otherwise the first pass reads A directly.
 template <int M, int T, int NB, bool BULK>
-__global__ void __launch_bounds__(T) k_rows_r2c(FftParams p)
+__global__ void __launch_bounds__(T, 3) k_rows_r2c(FftParams p)
 {
     extern __shared__ float4 sm4[];
     float2* sm = reinterpret_cast<float2*>(sm4);
