@@ -51,7 +51,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, int* status)
                 atomicExch(status, kStatusWaitTimeout);
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(20);
         }
         __threadfence();
     }
@@ -60,7 +60,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, int* status)
 }
 
 // Four threads per site (consecutive lanes), each summing every fourth tap
-// of each kernel with two alternating accumulators; the four partial sums
+// of each kernel with four alternating accumulators; the four partial sums
 // meet in a shuffle tree, and the first thread of the site forms the growth
 // and the update.  The non-zero taps of every kernel (offset in the staged
 // tile, weight) are copied into shared memory once per rollout, so the tap
@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(SR_THREADS) k_small_rollout(SmallRolloutParams
     for (int t = 0; t < p.n_steps; t++) {
         const float* src = (t % 2 == 0) ? p.A : p.buf;
         float* dst = (t % 2 == 0) ? p.buf : p.A;
+#pragma unroll 4
         for (int u = tid; u < C * TP * TP; u += SR_THREADS) {
             const int c = u / (TP * TP), r = u % (TP * TP);
             int yy = y0 - R + r / TP, xx = x0 - R + r % TP;
@@ -104,14 +105,16 @@ __global__ void __launch_bounds__(SR_THREADS) k_small_rollout(SmallRolloutParams
         for (int k = 0; k < p.kt.K; k++) {
             const float* tl = tiles + (size_t)p.kt.src[k] * TP * TP + (ty + R) * TP + (tx + R);
             const int i0 = p.tap_off[k], i1 = p.tap_off[k + 1];
-            float u0 = 0.f, u1 = 0.f;
+            float u0 = 0.f, u1 = 0.f, u2 = 0.f, u3 = 0.f;
             int i = i0 + q;
-            for (; i + SR_Q < i1; i += 2 * SR_Q) {
+            for (; i + 3 * SR_Q < i1; i += 4 * SR_Q) {
                 u0 = fmaf(tw[i], tl[toff[i]], u0);
                 u1 = fmaf(tw[i + SR_Q], tl[toff[i + SR_Q]], u1);
+                u2 = fmaf(tw[i + 2 * SR_Q], tl[toff[i + 2 * SR_Q]], u2);
+                u3 = fmaf(tw[i + 3 * SR_Q], tl[toff[i + 3 * SR_Q]], u3);
             }
-            if (i < i1) u0 = fmaf(tw[i], tl[toff[i]], u0);
-            float u = u0 + u1;
+            for (; i < i1; i += SR_Q) u0 = fmaf(tw[i], tl[toff[i]], u0);
+            float u = (u0 + u1) + (u2 + u3);
             u += __shfl_xor_sync(0xffffffffu, u, 1);
             u += __shfl_xor_sync(0xffffffffu, u, 2);
             const float sg = p.kt.sigma[k], h = p.kt.h[k];
