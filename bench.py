@@ -237,8 +237,9 @@ def batched_leg(torch, lenia, inputs, stream, steps=200):
         for i, w in enumerate(worlds):
             if w.height not in shapes:
                 kind, prm = lenia.lenia_batch_epilogue_shape(batch, i)
-                shapes[w.height] = ({0: f"tiled, {prm} rows per thread", 1: f"queued streaming, {prm} bands per world"}
-                                    .get(kind, "own step"))
+                shapes[w.height] = ({0: f"tiled, {prm} rows per thread",
+                                     1: f"queued streaming, {prm} bands per world",
+                                     2: f"tiled, 4 columns x {prm} rows per thread"}.get(kind, "own step"))
     finally:
         lenia.lenia_batch_destroy(batch)
     plain = inputs.localized_single_channel()

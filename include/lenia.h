@@ -404,7 +404,10 @@ LENIA_API lenia_status lenia_batch_rollout(lenia_batch* batch, float* const* A, 
  * width 256 k would use on its own. */
 LENIA_API int32_t lenia_batch_group_of(const lenia_batch* batch, int32_t world);
 /* Epilogue shape of world w's group: 0 = the tiled kernel, *param = rows per
- * thread (1, 2 or 4); 1 = the streaming kernel in one persistent launch over
+ * thread (1, 2 or 4); 2 = the tiled kernel with four adjacent columns per
+ * thread (float4 loads; one-kernel worlds of width 128 k with 16-byte aligned
+ * state buffers), *param = rows per thread (1 or 2); 1 = the streaming kernel
+ * in one persistent launch over
  * a device work queue of (world, 256-column chunk, band) items, with every
  * world's tensor maps in device memory, *param = bands per world (widths of
  * 256 k only); -1 when w steps on its own.  With autotune, lenia_batch_rollout

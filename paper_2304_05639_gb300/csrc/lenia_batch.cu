@@ -53,6 +53,7 @@ struct Group {
     float** Aout[2] = {nullptr, nullptr};
     float** Pout[2] = {nullptr, nullptr};
     bool aligned = false;                  // every listed A pointer is 16-byte aligned
+    bool aligned_all = false;              // every listed A and P pointer is 16-byte aligned
     // epilogue: 0 = tiled kernel (br rows per thread), 1 = streaming kernel over
     // a device work queue (`bands` bands per world; per-world tensor maps in qw)
     lenia::QueueWorld* qw[2] = {nullptr, nullptr};
@@ -152,7 +153,8 @@ cudaError_t group_epilogue(const Group& g, int dir, cudaStream_t s)
     const lenia::EpiParams ep = group_epi(g, dir);
     const int n = (int)g.worlds.size();
     if (g.epi == 1) return lenia::launch_epilogue_queue(ep, g.qw[dir], n, g.bands, 0, g.counter, g.v.fp.status, s);
-    return lenia::launch_epilogue_batch(ep, n, s, g.br);
+    // the four-column form needs 16-byte aligned state buffers
+    return lenia::launch_epilogue_batch(ep, n, s, g.br < 0 && !g.aligned_all ? 2 : g.br);
 }
 
 // One step of every world of a group: A/P lists of direction `dir`.
@@ -189,6 +191,10 @@ lenia_status tune_epilogue(Group& g, cudaStream_t s)
         int epi, br, bands;
     };
     std::vector<Cand> cands = {{0, 1, 1}, {0, 2, 1}, {0, 4, 1}};
+    // four columns per thread (float4 loads; widths of 128 k, every listed pointer 16-byte aligned)
+    if (g.v.K == 1 && g.v.C == 1 && g.v.fp.W % 128 == 0 && g.aligned_all)
+        for (int b : {-1, -2})
+            if (g.v.fp.H % (8 * -b) == 0) cands.push_back({0, b, 1});
     if (g.qw[0])
         for (int b : {1, 2, 4, 8})
             if (b <= g.v.fp.H) cands.push_back({1, 2, b});
@@ -510,8 +516,8 @@ int32_t lenia_batch_epilogue_shape(const lenia_batch* b, int32_t world, int32_t*
 {
     if (!b || world < 0 || world >= b->n || b->group_of[world] < 0) return -1;
     const Group& g = b->groups[b->group_of[world]];
-    if (param) *param = g.epi == 1 ? g.bands : g.br;
-    return g.epi;
+    if (param) *param = g.epi == 1 ? g.bands : (g.br < 0 ? -g.br : g.br);
+    return g.epi == 1 ? 1 : (g.br < 0 ? 2 : 0);
 }
 
 lenia_status lenia_batch_set_epilogue_shape(lenia_batch* b, int32_t world, int32_t kind, int32_t param)
@@ -521,6 +527,10 @@ lenia_status lenia_batch_set_epilogue_shape(lenia_batch* b, int32_t world, int32
     if (kind == 0 && (param == 1 || param == 2 || param == 4) && g.v.fp.H % (8 * param) == 0) {
         g.epi = 0;
         g.br = param;
+    } else if (kind == 2 && (param == 1 || param == 2) && g.v.K == 1 && g.v.C == 1 && g.v.fp.W % 128 == 0 &&
+               g.v.fp.H % (8 * param) == 0) {
+        g.epi = 0;
+        g.br = -param;
     } else if (kind == 1 && param >= 1 && param <= g.v.fp.H && g.qw[0]) {
         g.epi = 1;
         g.bands = param;
@@ -548,6 +558,7 @@ lenia_status lenia_batch_rollout(lenia_batch* b, float* const* A, float* const* 
             std::vector<const float*> a0(n), p0(n), a1(n), p1(n);
             std::vector<float*> ao0(n), po0(n), ao1(n), po1(n);
             g.aligned = true;
+            g.aligned_all = true;
             for (size_t j = 0; j < n; j++) {
                 const int i = g.worlds[j];
                 a0[j] = A[i];
@@ -559,6 +570,8 @@ lenia_status lenia_batch_rollout(lenia_batch* b, float* const* A, float* const* 
                 ao1[j] = A[i];
                 po1[j] = P ? P[i] : nullptr;
                 g.aligned = g.aligned && ((uintptr_t)A[i] % 16 == 0) && ((uintptr_t)b->A2[i] % 16 == 0);
+                g.aligned_all = g.aligned_all && ((uintptr_t)A[i] % 16 == 0) && ((uintptr_t)b->A2[i] % 16 == 0) &&
+                                ((uintptr_t)(P ? P[i] : nullptr) % 16 == 0) && ((uintptr_t)b->P2[i] % 16 == 0);
             }
             const size_t pb = n * sizeof(float*);
             bool ok = cudaMemcpy(g.Ain[0], a0.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&

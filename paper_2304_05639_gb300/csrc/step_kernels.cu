@@ -807,6 +807,114 @@ __global__ void __launch_bounds__(256) k_epilogue_batch11(EpiParams p)
     }
 }
 
+// The same per-site arithmetic with four adjacent columns per thread: every
+// row of a gene plane, the potential and the phenospace come in as float4
+// loads (the diffusion's left and right neighbours of the four columns as two
+// scalar loads), so a thread issues 12 loads for four sites instead of 48.
+// A block of 32 x 8 threads covers 128 columns x 8 BR rows.  Needs
+// W % 128 == 0 and H % (8 BR) == 0; results are those of k_epilogue_batch11.
+template <int LOC, int BR>
+__global__ void __launch_bounds__(256) k_epilogue_batch11v(EpiParams p)
+{
+    constexpr int NP = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
+    constexpr int PMU = (LOC & 1) ? 0 : -1;
+    constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
+    constexpr int PH = (LOC & 4) ? NP - 1 : -1;
+    const int H = p.H, W = p.W;
+    const size_t N = (size_t)H * W;
+    const int x = (blockIdx.x * EP_TX + threadIdx.x) * 4;        // first of the thread's four columns
+    const int xm = x == 0 ? W - 1 : x - 1;
+    const int xp = x + 4 == W ? 0 : x + 4;
+    const float eps_p = p.eps_p, eps_u = p.eps_u;
+    const int wz = blockIdx.z;
+    const float* pA = p.A_list[wz];
+    const float* pP = p.P_list ? p.P_list[wz] : nullptr;
+    float* pAo = p.Aout_list[wz];
+    float* pPo = p.Pout_list ? p.Pout_list[wz] : nullptr;
+    const float* pU = p.U + (size_t)wz * p.u_stride;
+
+    float4 up[BR][NP > 0 ? NP : 1], ce[BR][NP > 0 ? NP : 1], dn[BR][NP > 0 ? NP : 1];
+    float lf[BR][NP > 0 ? NP : 1], rt[BR][NP > 0 ? NP : 1];
+    float4 u[BR], a[BR];
+    size_t ic[BR];
+#pragma unroll
+    for (int j = 0; j < BR; j++) {
+        const int y = blockIdx.y * (EP_TY * BR) + j * EP_TY + threadIdx.y;
+        const size_t rc = (size_t)y * W;
+        const size_t ru = (size_t)(y == 0 ? H - 1 : y - 1) * W;
+        const size_t rd = (size_t)(y == H - 1 ? 0 : y + 1) * W;
+        ic[j] = rc + x;
+#pragma unroll
+        for (int pk = 0; pk < NP; pk++) {
+            const float* pl = pP + (size_t)pk * N;
+            ce[j][pk] = __ldg(reinterpret_cast<const float4*>(pl + rc + x));
+            if (p.maintain) {
+                up[j][pk] = __ldg(reinterpret_cast<const float4*>(pl + ru + x));
+                dn[j][pk] = __ldg(reinterpret_cast<const float4*>(pl + rd + x));
+                lf[j][pk] = __ldg(pl + rc + xm);
+                rt[j][pk] = __ldg(pl + rc + xp);
+            }
+        }
+        u[j] = __ldg(reinterpret_cast<const float4*>(pU + ic[j]));
+        a[j] = __ldg(reinterpret_cast<const float4*>(pA + ic[j]));
+    }
+#pragma unroll
+    for (int j = 0; j < BR; j++) {
+        float outA[4], outP[4][NP > 0 ? NP : 1];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            float ph[NP > 0 ? NP : 1];
+            bool alpha = true;
+#pragma unroll
+            for (int pk = 0; pk < NP; pk++) {
+                const float* cv = reinterpret_cast<const float*>(&ce[j][pk]);
+                if (p.maintain) {
+                    const float v0 = reinterpret_cast<const float*>(&up[j][pk])[c];
+                    const float v1 = c == 0 ? lf[j][pk] : cv[c - 1];
+                    const float v2 = cv[c];
+                    const float v3 = c == 3 ? rt[j][pk] : cv[c + 1];
+                    const float v4 = reinterpret_cast<const float*>(&dn[j][pk])[c];
+                    const float sm = (((v0 + v1) + v2) + v3) + v4;
+                    const int n = (v0 > eps_p) + (v1 > eps_p) + (v2 > eps_p) + (v3 > eps_p) + (v4 > eps_p);
+                    const float vv = n > 0 ? fminf(fmaxf(sm / (float)n, 0.f), 1.f) : 0.f;
+                    alpha = alpha && (vv > eps_p);
+                    ph[pk] = vv;
+                } else {
+                    ph[pk] = cv[c];
+                }
+            }
+            const float uu = reinterpret_cast<const float*>(&u[j])[c];
+            float acc = 0.f;
+            {
+                const float m = PMU >= 0 ? ph[PMU >= 0 ? PMU : 0] : p.kt.mu[0];
+                const float sg = PSG >= 0 ? ph[PSG >= 0 ? PSG : 0] : p.kt.sigma[0];
+                const float hh = PH >= 0 ? ph[PH >= 0 ? PH : 0] : p.kt.h[0];
+                float gk = 0.f;
+                if (sg > 0.f) {
+                    const float z = (uu - m) / sg;
+                    gk = expf(-0.5f * z * z);
+                }
+                const float tt = p.alpha_on ? uu : hh * gk;
+                if (p.maintain) alpha = alpha && (tt > eps_u);
+                const float G = p.growth_form == 0 ? hh * (2.f * gk - 1.f) : hh * gk;
+                acc += G;
+            }
+            if (!p.maintain) alpha = true;
+            outA[c] = fminf(fmaxf(reinterpret_cast<const float*>(&a[j])[c] + p.dt * (alpha ? acc : p.acc0[0]), 0.f),
+                            1.f);
+#pragma unroll
+            for (int pk = 0; pk < NP; pk++) outP[c][pk] = (p.maintain && !alpha) ? 0.f : ph[pk];
+        }
+        *reinterpret_cast<float4*>(pAo + ic[j]) = make_float4(outA[0], outA[1], outA[2], outA[3]);
+        if (pPo) {
+#pragma unroll
+            for (int pk = 0; pk < NP; pk++)
+                *reinterpret_cast<float4*>(pPo + (size_t)pk * N + ic[j]) =
+                    make_float4(outP[0][pk], outP[1][pk], outP[2][pk], outP[3][pk]);
+        }
+    }
+}
+
 // One launch over n_worlds batched worlds of the same shape (tiled epilogue;
 // EpiParams carries the pointer lists).  False if the shape has no tiled kernel.
 bool epilogue_batch_supported(const EpiParams& p)
@@ -824,6 +932,18 @@ cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t
     const int K = p.kt.K;
     if (p.partials || p.alpha_out || p.empty_out) return cudaErrorInvalidValue;
     dim3 block(EP_TX, EP_TY);
+    // br < 0: four columns per thread, |br| rows (float4 form; widths of 128 k)
+    if ((br == -1 || br == -2) && K == 1 && p.W % (4 * EP_TX) == 0 && p.H % (EP_TY * -br) == 0) {
+        dim3 g4(p.W / (4 * EP_TX), p.H / (EP_TY * -br), n_worlds);
+        if (br == -1) {
+            if (loc == 3) k_epilogue_batch11v<3, 1><<<g4, block, 0, s>>>(p);
+            else k_epilogue_batch11v<0, 1><<<g4, block, 0, s>>>(p);
+        } else {
+            if (loc == 3) k_epilogue_batch11v<3, 2><<<g4, block, 0, s>>>(p);
+            else k_epilogue_batch11v<0, 2><<<g4, block, 0, s>>>(p);
+        }
+        return cudaGetLastError();
+    }
     if (br != 1 && br != 2 && br != 4) br = 2;
     if (K == 1 && p.W % EP_TX == 0 && p.H % (EP_TY * br) == 0) {
         dim3 g4(p.W / EP_TX, p.H / (EP_TY * br), n_worlds);

@@ -168,13 +168,13 @@ def test_full_batched_workload_sampled_worlds_match_oracle():
         lenia.lenia_batch_destroy(batch)
 
 
-@pytest.mark.parametrize("kind,param", [(1, 1), (1, 3), (1, 8), (0, 1), (0, 4)])
+@pytest.mark.parametrize("kind,param", [(1, 1), (1, 3), (1, 8), (0, 1), (0, 4), (2, 1), (2, 2)])
 def test_epilogue_shapes_match_oracle(kind, param):
     """Every epilogue shape the autotuner chooses from, forced on two groups
     (256- and 512-side worlds, one radius): the queued streaming kernel (one
     persistent launch over a device work queue, per-world tensor maps in
-    device memory) with 1, 3 or 8 bands per world, and the tiled kernel with 1
-    or 4 rows per thread.  One batch step against the oracle per world, and
+    device memory) with 1, 3 or 8 bands per world, the tiled kernel with 1 or 4
+    rows per thread, and its four-columns-per-thread form with 1 or 2 rows.  One batch step against the oracle per world, and
     two steps against the tiled kernel's two steps."""
     torch = torch_mod()
     ws = inputs.batched_worlds(n_worlds=7, sizes=(256, 512), r_range=(9, 9), seed_index=21, live=True)
