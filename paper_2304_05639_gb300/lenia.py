@@ -292,8 +292,9 @@ def lenia_batch_group_of(batch, world: int) -> int:
 
 
 def lenia_batch_epilogue_shape(batch, world: int):
-    """(kind, param) of world's group: (0, rows per thread) tiled, (1, bands per
-    world) queued streaming; (-1, 0) without a group."""
+    """(kind, param) of world's group: (0, rows per thread) tiled, (2, rows per
+    thread) tiled with four columns per thread, (1, bands per world) queued
+    streaming; (-1, 0) without a group."""
     v = ctypes.c_int32(0)
     kind = load().lenia_batch_epilogue_shape(batch, int(world), ctypes.byref(v))
     return kind, v.value
