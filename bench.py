@@ -332,20 +332,25 @@ def evolve_leg(torch, lenia, inputs, stream, plain_ms, steps=100):
         for i in range(3):
             step(i)
         torch.cuda.synchronize()
-        lenia.lenia_profile_start(ctx, 16 * steps)
+        # timed without per-launch events, then a separate profiled region
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(steps):
             step(3 + i)
         e1.record(stream)
         torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        n_prof = min(steps, 50)
+        lenia.lenia_profile_start(ctx, 16 * n_prof)
+        for i in range(n_prof):
+            step(3 + i)
+        torch.cuda.synchronize()
         prof = lenia.lenia_profile_stop(ctx)
         lenia.lenia_check(ctx)
-        ms = e0.elapsed_time(e1) / steps
     finally:
         lenia.lenia_destroy(ctx)
     sites = H * W
-    disk_ms = sum(prof[k][0] for k in ("oxy_disk", "pen_disk") if k in prof) / steps
+    disk_ms = sum(prof[k][0] / max(1, prof[k][1]) for k in ("oxy_disk", "pen_disk") if k in prof)
     # each disk pass reads its input (1 or 2 bytes per site) and the second the
     # alpha byte, and writes 2 bytes (counts) or the touched gene values
     disk_bytes = sites * (1 + 2) + sites * (2 + 1)
@@ -378,16 +383,21 @@ def rings_leg(torch, lenia, inputs, stream, steps=100):
         for i in range(3):
             step(i)
         torch.cuda.synchronize()
-        lenia.lenia_profile_start(ctx, 8 * steps)
+        # timed without per-launch events, then a separate profiled region
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(steps):
             step(3 + i)
         e1.record(stream)
         torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        n_prof = min(steps, 50)
+        lenia.lenia_profile_start(ctx, 8 * n_prof)
+        for i in range(n_prof):
+            step(3 + i)
+        torch.cuda.synchronize()
         prof = lenia.lenia_profile_stop(ctx)
         lenia.lenia_check(ctx)
-        ms = e0.elapsed_time(e1) / steps
         path = lenia.lenia_conv_path(ctx)
     finally:
         lenia.lenia_destroy(ctx)
@@ -472,8 +482,10 @@ def direct_leg(torch, lenia, inputs, stream, fp32_peak=None, bf16_peak=None, ste
         e1.record(stream)
         torch.cuda.synchronize()
         lenia.lenia_check(ctx)
+        route = {lenia.ROUTE_STEPS: "launches per step (graph)", lenia.ROUTE_COOPERATIVE: "one cooperative launch",
+                 lenia.ROUTE_CLUSTER: "one thread-block cluster"}.get(lenia.lenia_rollout_route(ctx), "?")
         out["c1_direct"] = {"workload": "64x64, 1 channel, 1 kernel R=13, global genes, 100-step rollout, direct path",
-                            "us_per_step": e0.elapsed_time(e1) * 1e3 / 100}
+                            "us_per_step": e0.elapsed_time(e1) * 1e3 / 100, "route": route}
     except StopIteration:
         pass
     finally:

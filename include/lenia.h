@@ -173,7 +173,12 @@ LENIA_API lenia_status lenia_step(lenia_ctx* ctx, const float* A_in, const float
  * launch: every block keeps an 8 x 8 tile for the whole rollout and the
  * blocks meet at a bounded grid barrier after each step; its results equal
  * repeated lenia_step calls to FP32 rounding (direct sums in the same order,
- * the growth through expf). */
+ * the growth through expf).  The smallest of them (H W <= 8192, W a multiple
+ * of 32, H a multiple of 16 or 8, kernel radius <= 16, A 16-byte aligned) run
+ * in one thread-block cluster of 16 (or 8) blocks that keep the world in
+ * shared memory and meet at the cluster barrier: dense (2R+1)^2 sums in
+ * another order, equal to repeated lenia_step calls to FP32 rounding.
+ * lenia_rollout_route tells which form a context uses. */
 LENIA_API lenia_status lenia_rollout(lenia_ctx* ctx, float* A, float* P, int32_t n_steps,
                            float* stats_out, void* stream);
 
@@ -366,6 +371,16 @@ LENIA_API lenia_status lenia_kernel_weights(const lenia_ctx* ctx, int32_t k, dou
 
 /* Convolution path in use: LENIA_CONV_FFT, _DIRECT, _DIRECT_BF16 or _DIRECT_BF16X3. */
 LENIA_API int32_t lenia_conv_path(const lenia_ctx* ctx);
+
+/* Form of lenia_rollout (without stats_out, n_steps >= 2) for this context:
+ * LENIA_ROUTE_STEPS (launches per step, pairs of steps replayed from a CUDA
+ * graph), LENIA_ROUTE_COOPERATIVE (one cooperative launch) or
+ * LENIA_ROUTE_CLUSTER (one thread-block cluster; a caller's A that is not
+ * 16-byte aligned takes the cooperative launch instead); -1 for NULL. */
+#define LENIA_ROUTE_STEPS 0
+#define LENIA_ROUTE_COOPERATIVE 1
+#define LENIA_ROUTE_CLUSTER 2
+LENIA_API int32_t lenia_rollout_route(const lenia_ctx* ctx);
 
 /* Number of CUDA kernel launches one lenia_step enqueues (with stats). */
 LENIA_API int32_t lenia_launches_per_step(const lenia_ctx* ctx);

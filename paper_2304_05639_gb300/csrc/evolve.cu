@@ -11,9 +11,11 @@
 // and the penalising test E_pen > eps_pen is M > floor(eps_pen n^2), decided
 // on the host in FP64 once per step.
 //
-// Each disk pass loads a (32 + 2r)^2 tile with its periodic halo into shared
-// memory, turns every tile row into exclusive prefix sums, and adds, for each
-// of the 2r + 1 rows of the disk, the difference of two prefix sums.
+// One kernel takes both disk averages per 32 x 32 tile: it loads the tile's
+// empty bytes with a periodic halo of 2 r into shared memory, turns every row
+// into exclusive prefix sums, forms n - c over the tile plus a halo of r (for
+// each of the 2 r + 1 rows of the disk, the difference of two prefix sums),
+// takes those rows' prefix sums, and sums M over each output site's disk.
 #include "lenia_internal.cuh"
 
 namespace lenia {
@@ -28,85 +30,6 @@ __device__ __forceinline__ int wrap_i(int v, int n)
     if (v >= 0 && v < n) return v;
     v %= n;
     return v < 0 ? v + n : v;
-}
-
-// PASS 1: empty (0/1 bytes) -> c.  PASS 2: c -> M, then mutation, penalisation
-// and the optional E_pen output at each site.
-template <int PASS>
-__global__ void __launch_bounds__(DK_THREADS) k_disk_pass(EvoParams p)
-{
-    extern __shared__ int pre[];                // [S][S + 1] exclusive row prefix sums
-    const int r = p.r_oxy;
-    const int S = DK_T + 2 * r;
-    const int SP = S + 1;                       // odd row pitch: the row scans hit distinct banks
-    const int y0 = blockIdx.y * DK_T - r, x0 = blockIdx.x * DK_T - r;
-    for (int ty = threadIdx.x >> 5; ty < S; ty += DK_THREADS / 32) {
-        const size_t row = (size_t)wrap_i(y0 + ty, p.H) * p.W;
-        for (int tx = threadIdx.x & 31; tx < S; tx += 32) {
-            const size_t gi = row + wrap_i(x0 + tx, p.W);
-            pre[ty * SP + tx + 1] = PASS == 1 ? (int)p.empty[gi] : p.n_disk - (int)p.cnt_in[gi];
-        }
-    }
-    __syncthreads();
-    // prefix sums, one warp per tile row: each lane owns up to 3 consecutive
-    // entries (S <= 96), then a warp scan of the lanes' totals
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int per = (S + 31) / 32;
-        for (int row = warp; row < S; row += DK_THREADS / 32) {
-            int* q = pre + row * SP;
-            int part[3];
-            int sum = 0;
-#pragma unroll
-            for (int t = 0; t < 3; t++) {
-                const int j = lane * per + t;
-                sum += (t < per && j < S) ? q[j + 1] : 0;
-                part[t] = sum;
-            }
-            int incl = sum;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int n = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += n;
-            }
-            const int excl = incl - sum;
-#pragma unroll
-            for (int t = 0; t < 3; t++) {
-                const int j = lane * per + t;
-                if (t < per && j < S) q[j + 1] = excl + part[t];
-            }
-            if (lane == 0) q[0] = 0;
-        }
-    }
-    __syncthreads();
-    const int tx = threadIdx.x & 31, tyb = threadIdx.x >> 5;
-    const int x = blockIdx.x * DK_T + tx;
-    if (x >= p.W) return;
-    const size_t N = (size_t)p.H * p.W;
-    for (int j = 0; j < DK_T / 8; j++) {
-        const int ty = tyb + 8 * j;
-        const int y = blockIdx.y * DK_T + ty;
-        if (y >= p.H) break;
-        int s = 0;
-        for (int dy = -r; dy <= r; dy++) {
-            const int hw = p.half_width[dy < 0 ? -dy : dy];
-            const int* q = pre + (ty + r + dy) * SP;
-            s += q[tx + r + hw + 1] - q[tx + r - hw];
-        }
-        const size_t i = (size_t)y * p.W + x;
-        if (PASS == 1) {
-            p.cnt_out[i] = (uint16_t)s;
-        } else {
-            if (p.epen_out) p.epen_out[i] = (float)((double)s / p.n_disk2);
-            if (p.alpha[i]) {
-                if (p.mut_plane >= 0 && wrap_i(x - p.mut_x0 + p.mut_half, p.W) < 2 * p.mut_half &&
-                    wrap_i(y - p.mut_y0 + p.mut_half, p.H) < 2 * p.mut_half)
-                    p.P[(size_t)p.mut_plane * N + i] += p.mut_add;
-                if (p.pen_plane >= 0 && (long long)s > p.pen_thresh)
-                    p.P[(size_t)p.pen_plane * N + i] += p.pen_add;
-            }
-        }
-    }
 }
 
 // Exclusive prefix sums of S rows of `pre` (row pitch SP, entries 1..S hold
@@ -205,6 +128,131 @@ __global__ void __launch_bounds__(DK_THREADS) k_disk_fused(EvoParams p)
     }
 }
 
+// Half-width of the disk |d| <= R at row offset dy: the largest w with
+// w^2 + dy^2 <= R^2 (the host's definition of the same disk).
+__host__ __device__ constexpr int disk_hw(int R, int dy)
+{
+    int w = 0;
+    while ((w + 1) * (w + 1) + dy * dy <= R * R) w++;
+    return w;
+}
+
+template <int R>
+struct DiskRows {
+    int hw[2 * R + 1];
+    constexpr DiskRows() : hw()
+    {
+        for (int dy = -R; dy <= R; dy++) hw[dy + R] = disk_hw(R, dy < 0 ? -dy : dy);
+    }
+};
+
+// Exclusive prefix sums of `rows` rows of LEN values (entries 1..LEN of each
+// row, row pitch SP; entry 0 receives 0), one thread per row, in order.
+template <int LEN>
+__device__ __forceinline__ void row_scans_seq(int* pre, int rows, int SP)
+{
+    for (int row = threadIdx.x; row < rows; row += DK_THREADS) {
+        int* q = pre + row * SP;
+        int sum = 0;
+        q[0] = 0;
+#pragma unroll 8
+        for (int j = 1; j <= LEN; j++) {
+            sum += q[j];
+            q[j] = sum;
+        }
+    }
+}
+
+// k_disk_fused for a disk radius known at compile time: the same integer
+// arithmetic with the disk's row half-widths as constants (every prefix-sum
+// difference is a shared load at a fixed offset), one thread per row for the
+// prefix sums (a row of at most 64 entries), and the interior blocks' tile
+// loads without the periodic wrap.
+template <int R>
+__global__ void __launch_bounds__(DK_THREADS) k_disk_fused_t(EvoParams p)
+{
+    constexpr int E = DK_T + 4 * R, EP = E + 1;     // empty bytes: tile + 2 R halo
+    constexpr int S = DK_T + 2 * R, SP = S + 1;     // n - c: tile + R halo
+    constexpr DiskRows<R> D{};
+    __shared__ int preE[E * EP];
+    __shared__ int preM[S * SP];
+    const int H = p.H, W = p.W;
+    const int by = blockIdx.y * DK_T, bx = blockIdx.x * DK_T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int any = 0, all = 1;
+    if (by >= 2 * R && by + DK_T + 2 * R <= H && bx >= 2 * R && bx + DK_T + 2 * R <= W) {
+        const uint8_t* src = p.empty + (size_t)(by - 2 * R) * W + (bx - 2 * R);
+        for (int ty = warp; ty < E; ty += DK_THREADS / 32)
+            for (int tx = lane; tx < E; tx += 32) {
+                const int v = (int)src[(size_t)ty * W + tx];
+                any |= v;
+                all &= v;
+                preE[ty * EP + tx + 1] = v;
+            }
+    } else {
+        for (int ty = warp; ty < E; ty += DK_THREADS / 32) {
+            const size_t row = (size_t)wrap_i(by - 2 * R + ty, H) * W;
+            for (int tx = lane; tx < E; tx += 32) {
+                const int v = (int)p.empty[row + wrap_i(bx - 2 * R + tx, W)];
+                any |= v;
+                all &= v;
+                preE[ty * EP + tx + 1] = v;
+            }
+        }
+    }
+    // a tile whose whole 2 R neighbourhood is one value has the same M at
+    // every site: n^2 with no empty site (c = 0), 0 with every site empty
+    any = __syncthreads_or(any);
+    all = __syncthreads_and(all);
+    const bool uniform = !any || all;
+    if (!uniform) {
+        row_scans_seq<E>(preE, E, EP);
+        __syncthreads();
+        // n - c at region coordinates (cy, cx) = the disk centred on empty-region (cy + R, cx + R)
+        for (int u = threadIdx.x; u < S * S; u += DK_THREADS) {
+            const int cy = u / S, cx = u % S;
+            const int* q = preE + (cy + R) * EP + cx + R;
+            int c = 0;
+#pragma unroll
+            for (int dy = -R; dy <= R; dy++) c += q[dy * EP + D.hw[dy + R] + 1] - q[dy * EP - D.hw[dy + R]];
+            preM[cy * SP + cx + 1] = p.n_disk - c;
+        }
+        __syncthreads();
+        row_scans_seq<S>(preM, S, SP);
+        __syncthreads();
+    }
+    const int x = bx + lane;
+    if (x >= W) return;
+    const size_t N = (size_t)H * W;
+    const bool mut_x = p.mut_plane >= 0 && wrap_i(x - p.mut_x0 + p.mut_half, W) < 2 * p.mut_half;
+    for (int j = 0; j < DK_T / 8; j++) {
+        const int ty = warp + 8 * j;
+        const int y = by + ty;
+        if (y >= H) break;
+        int s = any ? 0 : p.n_disk * p.n_disk;
+        if (!uniform) {
+            const int* q = preM + (ty + R) * SP + lane + R;
+#pragma unroll
+            for (int dy = -R; dy <= R; dy++) s += q[dy * SP + D.hw[dy + R] + 1] - q[dy * SP - D.hw[dy + R]];
+        }
+        const size_t i = (size_t)y * W + x;
+        if (p.epen_out) p.epen_out[i] = (float)((double)s / p.n_disk2);
+        if (p.alpha[i]) {
+            if (mut_x && wrap_i(y - p.mut_y0 + p.mut_half, H) < 2 * p.mut_half)
+                p.P[(size_t)p.mut_plane * N + i] += p.mut_add;
+            if (p.pen_plane >= 0 && (long long)s > p.pen_thresh) p.P[(size_t)p.pen_plane * N + i] += p.pen_add;
+        }
+    }
+}
+
+template <int R>
+static cudaError_t launch_disk_t(const EvoParams& p, cudaStream_t s)
+{
+    const dim3 grid((p.W + DK_T - 1) / DK_T, (p.H + DK_T - 1) / DK_T);
+    k_disk_fused_t<R><<<grid, DK_THREADS, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 size_t disk_fused_smem(int r)
 {
     const size_t E = DK_T + 4 * (size_t)r, S = DK_T + 2 * (size_t)r;
@@ -213,6 +261,16 @@ size_t disk_fused_smem(int r)
 
 cudaError_t launch_disk_fused(const EvoParams& p, cudaStream_t s)
 {
+    switch (p.r_oxy) {
+        case 1: return launch_disk_t<1>(p, s);
+        case 2: return launch_disk_t<2>(p, s);
+        case 3: return launch_disk_t<3>(p, s);
+        case 4: return launch_disk_t<4>(p, s);
+        case 5: return launch_disk_t<5>(p, s);
+        case 6: return launch_disk_t<6>(p, s);
+        case 7: return launch_disk_t<7>(p, s);
+        case 8: return launch_disk_t<8>(p, s);
+    }
     const size_t smem = disk_fused_smem(p.r_oxy);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = smem_limit<k_disk_fused>(smem);
@@ -222,39 +280,28 @@ cudaError_t launch_disk_fused(const EvoParams& p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// A and P are zeroed at each listed wall site (in place).
+// A and P are zeroed at each listed wall site (in place): one thread per
+// (plane, wall site), sites fastest, so a warp writes neighbouring wall sites
+// of one plane together (the list is in increasing site order).
 __global__ void k_walls_zero(const int* idx, int n, float* A, int C, float* P, int npk, size_t N)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const size_t i = (size_t)idx[t];
-    for (int c = 0; c < C; c++) A[(size_t)c * N + i] = 0.f;
-    for (int pk = 0; pk < npk; pk++) P[(size_t)pk * N + i] = 0.f;
-}
-
-size_t disk_pass_smem(int r)
-{
-    const int S = DK_T + 2 * r;
-    return (size_t)S * (S + 1) * sizeof(int);
-}
-
-cudaError_t launch_disk_pass(const EvoParams& p, int pass, cudaStream_t s)
-{
-    // at most (32 + 64) x 97 ints = 37 KB for r_oxy = 32: no opt-in needed
-    const size_t smem = disk_pass_smem(p.r_oxy);
-    const dim3 grid((p.W + DK_T - 1) / DK_T, (p.H + DK_T - 1) / DK_T);
-    if (pass == 1)
-        k_disk_pass<1><<<grid, DK_THREADS, smem, s>>>(p);
+    if (t >= n * (C + npk)) return;
+    const int plane = t / n, j = t - plane * n;
+    const size_t i = (size_t)__ldg(&idx[j]);
+    if (plane < C)
+        A[(size_t)plane * N + i] = 0.f;
     else
-        k_disk_pass<2><<<grid, DK_THREADS, smem, s>>>(p);
-    return cudaGetLastError();
+        P[(size_t)(plane - C) * N + i] = 0.f;
 }
 
 cudaError_t launch_walls_zero(const int* idx, int n, float* A, int C, float* P, int npk, size_t N,
                               cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_walls_zero<<<(n + 255) / 256, 256, 0, s>>>(idx, n, A, C, P, npk, N);
+    const long long total = (long long)n * (C + npk);
+    if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_walls_zero<<<(int)((total + 255) / 256), 256, 0, s>>>(idx, n, A, C, P, npk, N);
     return cudaGetLastError();
 }
 

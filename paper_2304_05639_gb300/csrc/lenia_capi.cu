@@ -39,6 +39,9 @@ struct lenia_ctx {
     unsigned* d_small_count = nullptr;
     int2* d_small_taps = nullptr;
     std::vector<int> small_tap_off;
+    // the smallest of them: rollouts in one thread-block cluster (cr_Q blocks)
+    int cr_Q = 0;
+    float* d_cr_w = nullptr;
     // tensor-core route (LENIA_CONV_DIRECT_BF16 / _BF16X3)
     uint16_t* d_tc_hi = nullptr;
     uint16_t* d_tc_lo = nullptr;
@@ -90,7 +93,6 @@ struct lenia_ctx {
     int n_walls = 0;
     uint8_t* d_alpha_e = nullptr;          // [H][W] alpha of the evolving step
     uint8_t* d_empty = nullptr;            // [H][W] not Delta_sum(U)
-    uint16_t* d_cnt = nullptr;             // [H][W] empty sites per K_oxy disk
     // host-buffer steps (lenia_step_host[_async]): a stream for gene uploads and
     // one for downloads, and the events that order them against the compute
     // host-buffer pipeline (lenia_step_host_async): two staging sets used by
@@ -566,6 +568,12 @@ const char* lenia_last_error(const lenia_ctx* ctx) { return ctx ? ctx->err.c_str
 
 int32_t lenia_conv_path(const lenia_ctx* ctx) { return ctx ? ctx->path : -1; }
 
+int32_t lenia_rollout_route(const lenia_ctx* ctx)
+{
+    if (!ctx) return -1;
+    return ctx->cr_Q ? LENIA_ROUTE_CLUSTER : (ctx->small ? LENIA_ROUTE_COOPERATIVE : LENIA_ROUTE_STEPS);
+}
+
 int32_t lenia_launches_per_step(const lenia_ctx* ctx)
 {
     if (!ctx) return -1;
@@ -583,9 +591,9 @@ void lenia_destroy(lenia_ctx* c)
                     c->d_A3, c->d_P3, c->d_stats, c->d_status, c->d_ckpt, c->d_seg, c->d_gA[0],
                     c->d_gA[1], c->d_gpre, c->d_gU, c->d_V, c->d_gene_part, c->d_gene_acc,
                     c->d_Ahat_t, c->d_Uhat_t, c->d_ticket, c->d_walls, c->d_alpha_e, c->d_empty,
-                    c->d_cnt, c->d_Useg, c->d_hA_in1, c->d_hP_in1, c->d_hA_out1,
+                    c->d_Useg, c->d_hA_in1, c->d_hP_in1, c->d_hA_out1,
                     c->d_hP_out1, c->d_hstats, c->d_tc_hi, c->d_tc_lo, c->d_tc_B, c->d_tc_ks,
-                    c->d_tc_grp, c->d_tc_has, c->d_small_count, c->d_small_taps};
+                    c->d_tc_grp, c->d_tc_has, c->d_small_count, c->d_small_taps, c->d_cr_w};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -783,6 +791,20 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
             ALLOC(c->d_small_count, 1);
             ALLOC(c->d_small_taps, taps.size());
             CK_INIT(cudaMemcpy(c->d_small_taps, taps.data(), taps.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        }
+        // dense (2 maxR + 1)^2 kernels, each centred, for the cluster rollout
+        c->cr_Q = cluster_rollout_blocks(H, W, C, NC, c->max_R);
+        if (c->cr_Q) {
+            const int KW = 2 * c->max_R + 1;
+            std::vector<float> dense((size_t)NC * KW * KW, 0.f);
+            for (int k = 0; k < NC; k++) {
+                const int R = c->conv_R[k], n = 2 * R + 1, o = c->max_R - R;
+                for (int dy = 0; dy < n; dy++)
+                    for (int dx = 0; dx < n; dx++)
+                        dense[((size_t)k * KW + dy + o) * KW + dx + o] = (float)c->conv_w[k][(size_t)dy * n + dx];
+            }
+            ALLOC(c->d_cr_w, dense.size());
+            CK_INIT(cudaMemcpy(c->d_cr_w, dense.data(), dense.size() * sizeof(float), cudaMemcpyHostToDevice));
         }
     }
     if (path == LENIA_CONV_DIRECT) {
@@ -1067,6 +1089,25 @@ lenia_status lenia_rollout(lenia_ctx* c, float* A, float* P, int32_t n_steps, fl
     if (!A || (c->n_p && !P)) return fail(c, LENIA_EINVAL, "A (and P with localized genes) must be non-null");
     if (n_steps == 0) return LENIA_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (c->cr_Q && !stats_out && n_steps >= 2 && ((uintptr_t)A & 15) == 0) {
+        // the whole rollout in one thread-block cluster (the smallest worlds)
+        ClusterRolloutParams cp;
+        memset(&cp, 0, sizeof(cp));
+        cp.A = A;
+        cp.w = c->d_cr_w;
+        cp.kt = c->kt;
+        cp.H = c->cfg.height;
+        cp.W = c->cfg.width;
+        cp.C = c->cfg.n_channels;
+        cp.maxR = c->max_R;
+        cp.growth_form = c->cfg.growth_form;
+        cp.n_steps = n_steps;
+        cp.Q = c->cr_Q;
+        cp.dt = c->cfg.dt;
+        ProfScope ps(c, KIND_DIRECT, s);
+        CUDA_OR_FAIL(c, launch_cluster_rollout(cp, s));
+        return LENIA_OK;
+    }
     if (c->small && !stats_out && n_steps >= 2) {
         // one cooperative launch for the whole rollout (small world, global genes)
         SmallRolloutParams sp;
@@ -1327,7 +1368,6 @@ lenia_status lenia_step_evolve(lenia_ctx* c, float* A, float* P, float* A_out, f
     if (!c->d_empty) {
         st = dalloc(c, &c->d_alpha_e, c->N);
         if (st == LENIA_OK) st = dalloc(c, &c->d_empty, c->N);
-        if (st == LENIA_OK) st = dalloc(c, &c->d_cnt, c->N);
         if (st != LENIA_OK) return st;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -1344,8 +1384,6 @@ lenia_status lenia_step_evolve(lenia_ctx* c, float* A, float* P, float* A_out, f
     EvoParams e;
     memset(&e, 0, sizeof(e));
     e.empty = c->d_empty;
-    e.cnt_in = c->d_cnt;
-    e.cnt_out = c->d_cnt;
     e.alpha = alpha;
     e.P = c->n_p ? P_out : nullptr;
     e.epen_out = epen_out;

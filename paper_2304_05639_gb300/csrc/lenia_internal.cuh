@@ -84,8 +84,6 @@ struct EpiParams {
 constexpr int kMaxROxy = 32;
 struct EvoParams {
     const uint8_t* empty;      // [H][W] 1 where Delta_sum(U) is false
-    const uint16_t* cnt_in;    // [H][W] empty sites in each disk (pass 2 input)
-    uint16_t* cnt_out;         // same buffer, pass 1 output
     const uint8_t* alpha;      // [H][W] alpha mask of the step
     float* P;                  // P' [n_p K][H][W], updated in place
     float* epen_out;           // [H][W] E_pen or null
@@ -148,6 +146,21 @@ struct SmallRolloutParams {
     unsigned* count;           // grid barrier counter (zeroed by the launcher)
     int* status;
 };
+// Rollouts of small worlds with global genes in one thread-block cluster
+// (the world in the blocks' shared memory).
+struct ClusterRolloutParams {
+    float* A;                  // [C][H][W], in and out (16-byte aligned)
+    const float* w;            // dense kernels [K][2 maxR + 1][2 maxR + 1] (row dy, column dx), zero-padded
+    KernelTable kt;
+    int H, W, C, maxR, growth_form, n_steps;
+    int Q;                     // blocks in the cluster (16 or 8)
+    float dt;
+};
+// Blocks of the cluster the world can run on (16 or 8), or 0 if it cannot.
+int cluster_rollout_blocks(int H, int W, int C, int K, int maxR);
+size_t cluster_rollout_smem(int H, int W, int C, int K, int maxR, int Q);
+cudaError_t launch_cluster_rollout(const ClusterRolloutParams& p, cudaStream_t s);
+
 size_t small_rollout_smem(int C, int maxR, int n_taps);
 bool small_rollout_supported(int H, int W, int C, int K, int maxR, int n_taps);
 cudaError_t launch_small_rollout(const SmallRolloutParams& p, cudaStream_t s);
@@ -220,7 +233,7 @@ bool epilogue_rows_supported(const EpiParams& p);
 // The streaming epilogue over the worlds of a batched group (one persistent
 // launch; work items taken from a device queue): one world's tensor maps and
 // outputs, in device memory.
-struct alignas(64) QueueWorld {
+struct QueueWorld {             // aligned as CUtensorMap
     CUtensorMap tm_p, tm_u, tm_a, tm_h;
     float* A_out;
     float* P_out;
@@ -258,7 +271,6 @@ bool epilogue_batch_supported(const EpiParams& p);
 cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t s, int br = 2);
 int ring_epilogue_blocks(int H, int W);   // stats records of the ring epilogue
 // pass 1: Delta_sum complement -> counts; pass 2: E_pen, mutation, penalisation
-cudaError_t launch_disk_pass(const EvoParams& p, int pass, cudaStream_t s);
 // both passes in one launch (counts kept in shared memory)
 cudaError_t launch_disk_fused(const EvoParams& p, cudaStream_t s);
 cudaError_t launch_walls_zero(const int* idx, int n, float* A, int C, float* P, int npk, size_t N,

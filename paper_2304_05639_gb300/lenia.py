@@ -19,11 +19,12 @@ from . import inputs as _inputs
 
 LENIA_OK, LENIA_EINVAL, LENIA_ENOMEM, LENIA_ECUDA, LENIA_ETIMEOUT, LENIA_ENOTSUP = range(6)
 CONV_AUTO, CONV_FFT, CONV_DIRECT, CONV_DIRECT_BF16, CONV_DIRECT_BF16X3 = 0, 1, 2, 3, 4
+ROUTE_STEPS, ROUTE_COOPERATIVE, ROUTE_CLUSTER = 0, 1, 2
 
 # Every function the header declares (checked by the tests).
 EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia_stats",
            "lenia_potentials", "lenia_update_from_potentials", "lenia_step_host",
-           "lenia_kernel_weights", "lenia_conv_path", "lenia_launches_per_step",
+           "lenia_kernel_weights", "lenia_conv_path", "lenia_rollout_route", "lenia_launches_per_step",
            "lenia_last_error", "lenia_status_string", "lenia_destroy", "lenia_profile_start",
            "lenia_profile_stop", "lenia_profile_kind_name", "lenia_stats_noalloc", "lenia_check", "lenia_set_genes", "lenia_batch_init",
            "lenia_batch_rollout", "lenia_batch_conv_path", "lenia_batch_check", "lenia_batch_destroy",
@@ -121,6 +122,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lenia_kernel_weights.restype = st
     lib.lenia_conv_path.argtypes = [vp]
     lib.lenia_conv_path.restype = ctypes.c_int32
+    lib.lenia_rollout_route.argtypes = [vp]
+    lib.lenia_rollout_route.restype = ctypes.c_int32
     lib.lenia_launches_per_step.argtypes = [vp]
     lib.lenia_launches_per_step.restype = ctypes.c_int32
     lib.lenia_last_error.argtypes = [vp]
@@ -386,6 +389,11 @@ def lenia_kernel_weights(ctx, k: int, radius: int) -> np.ndarray:
 
 def lenia_conv_path(ctx) -> int:
     return load().lenia_conv_path(ctx)
+
+
+def lenia_rollout_route(ctx) -> int:
+    """ROUTE_STEPS, ROUTE_COOPERATIVE or ROUTE_CLUSTER: the form of lenia_rollout."""
+    return load().lenia_rollout_route(ctx)
 
 
 def lenia_launches_per_step(ctx) -> int:

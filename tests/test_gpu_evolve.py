@@ -303,7 +303,8 @@ def test_evolve_argument_errors():
         lenia.lenia_destroy(ctx)
 
 
-def test_full_size_evolve_properties_and_sampled_epen():
+@pytest.mark.parametrize("r", [4, 10])
+def test_full_size_evolve_properties_and_sampled_epen(r):
     """The 2048 x 2048, 3-channel, 15-kernel world: the evolution step adds
     exactly gamma delta on (square AND alpha) and on (E_pen > eps_pen AND
     alpha) to lenia_step's genes, leaves A' unchanged, and E_pen at sampled
@@ -312,7 +313,8 @@ def test_full_size_evolve_properties_and_sampled_epen():
     torch = torch_mod()
     w = _potential_alpha(inputs.multi_channel(live=True))
     H, W, K = w.height, w.width, w.n_kernels
-    r = 10
+    # r = 4 runs the compile-time-radius disk kernel (with tiles of one value
+    # inside the bodies and in the empty background), r = 10 the general one
     # the first site (stride 16) whose 200 x 200 window is all matter, and the
     # left ends of the matter on rows through it (a body's edge)
     S = (w.A[0] > 0).astype(np.int64).cumsum(0).cumsum(1)

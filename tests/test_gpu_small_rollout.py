@@ -1,8 +1,9 @@
 """Rollouts of small worlds with global genes on the direct route run as one
 cooperative launch (every block keeps an 8 x 8 tile for the whole rollout and
-meets the others at a bounded grid barrier after each step).  Against the FP64
-oracle's rollout (the 1e-3 gate after 10 steps) and against repeated
-lenia_step calls (FP32 rounding).  GPU only."""
+meets the others at a bounded grid barrier after each step), the smallest of
+them in one thread-block cluster that keeps the world in shared memory.
+Against the FP64 oracle's rollout (the 1e-3 gate after 10 steps) and against
+repeated lenia_step calls (FP32 rounding).  GPU only."""
 import numpy as np
 import pytest
 
@@ -34,7 +35,13 @@ WORLDS = {
     "c5s": lambda: _live(inputs.global_multi_channel(H=64, W=64, R=13, patch=24)),  # 3 channels, 15 kernels
     "rect": lambda: _live(inputs.global_multi_channel(H=32, W=120, R=7, patch=16)), # 15 x 4 tiles
     "max": lambda: inputs.single_kernel_global(H=128, W=128, R=18, patch=40),       # the largest size taken
+    "q8": lambda: _live(inputs.single_kernel_global(H=40, W=64, R=9, patch=16)),    # a cluster of 8
+    "r3": lambda: _live(inputs.single_kernel_global(H=64, W=96, R=3, patch=20)),    # a small radius
 }
+
+# the form lenia_rollout takes for each world (16-byte aligned A)
+ROUTES = {"c1": lenia.ROUTE_CLUSTER, "c5s": lenia.ROUTE_CLUSTER, "rect": lenia.ROUTE_COOPERATIVE,
+          "max": lenia.ROUTE_COOPERATIVE, "q8": lenia.ROUTE_CLUSTER, "r3": lenia.ROUTE_CLUSTER}
 
 
 @pytest.mark.parametrize("name", list(WORLDS))
@@ -45,6 +52,7 @@ def test_small_rollout_matches_oracle_and_steps(name, n):
     cfg, ks = lenia.config_from_world(w, lenia.CONV_DIRECT)
     ctx = lenia.lenia_init(cfg, ks)
     try:
+        assert lenia.lenia_rollout_route(ctx) == ROUTES[name]
         A = to_dev(w.A)
         lenia.lenia_rollout(ctx, A, None, n)
         lenia.lenia_check(ctx)
@@ -66,3 +74,25 @@ def test_small_rollout_matches_oracle_and_steps(name, n):
     assert err <= 1e-3
     assert d_steps <= 1e-5 * n
     assert got.max() > 0                      # the compared state is not empty
+
+
+def test_cluster_rollout_unaligned_state_takes_the_cooperative_launch():
+    """A caller's A that is not 16-byte aligned runs the cooperative launch
+    (scalar accesses); both forms give the same state to FP32 rounding."""
+    torch = torch_mod()
+    w = WORLDS["c1"]()
+    cfg, ks = lenia.config_from_world(w, lenia.CONV_DIRECT)
+    ctx = lenia.lenia_init(cfg, ks)
+    try:
+        A = to_dev(w.A)
+        store = torch.zeros(w.A.size + 1, dtype=torch.float32, device="cuda")
+        B = store[1:].view(w.A.shape)                 # 4 bytes past a 16-byte boundary
+        B.copy_(A)
+        lenia.lenia_rollout(ctx, A, None, 10)
+        lenia.lenia_rollout(ctx, B, None, 10)
+        lenia.lenia_check(ctx)
+        d = float((A - B).abs().max())
+    finally:
+        lenia.lenia_destroy(ctx)
+    print(f"cluster vs cooperative after 10 steps: {d:.2e}")
+    assert d <= 1e-4
