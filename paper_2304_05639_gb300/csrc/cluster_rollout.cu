@@ -19,11 +19,14 @@
 //
 // The convolution is a dense sum over the (2R + 1)^2 square of each kernel
 // (zero weights included, R at compile time): a thread takes a strip of 8
-// sites of one row and a group of kernel rows dy, keeps the strip's input
-// window for that row (2R + 8 values) in registers and adds 8 products per
-// weight; the 8 row groups of a strip sit in neighbouring lanes and meet in a
-// reduce-scatter of shuffles, after which each lane holds one site's
-// potential.
+// sites of one row and every eighth kernel row dy (row group g: dy + R = g,
+// g + 8, ...), keeps the strip's input window for that row (2R + 8 values) in
+// registers and adds 8 products per weight; the 8 row groups of a strip sit
+// in neighbouring lanes and meet in a reduce-scatter of shuffles, after which
+// lane g holds the potential of the strip's site g.  A warp takes four
+// strips 8 columns apart and the tile's row pitch is 1 modulo 32, so its 32
+// lanes (8 consecutive rows, four strips) read 32 different banks.  (Sixteen
+// warps with 16 row groups measured the same.)
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -40,22 +43,18 @@ constexpr int CR_G = 8;           // kernel-row groups per strip (lane bits 0..2
 constexpr int CR_THREADS = 256;
 constexpr int CR_MIN_R = 1, CR_MAX_R = 16;
 
-__host__ __device__ constexpr int cr_round4(int v) { return (v + 3) / 4 * 4; }
-
 // Shared-memory layout (floats): own[2][C][HS][W], tile[C][TH][TW],
-// weights[K][KW][KW].  Tile column PADL + x holds column x of the world
-// (x = -R .. W + R - 1, periodic); PADL = R rounded up to 4 keeps the
-// interior 16-byte aligned.
+// weights[K][KW][KW].  Tile column R + x holds column x of the world
+// (x = -R .. W + R - 1, periodic); TW = 1 mod 32.
 struct CrLayout {
-    int HS, TH, TW, PADL, KW;
+    int HS, TH, TW, KW;
     size_t own, tile, wts;
     __host__ __device__ CrLayout(int H, int W, int C, int K, int R, int Q)
     {
         HS = H / Q;
         KW = 2 * R + 1;
         TH = HS + 2 * R;
-        PADL = cr_round4(R);
-        TW = cr_round4(PADL + W + R);
+        TW = (W + 2 * R + 30) / 32 * 32 + 1;
         own = (size_t)C * HS * W;
         tile = (size_t)C * TH * TW;
         wts = (size_t)K * KW * KW;
@@ -67,12 +66,11 @@ template <int R>
 __global__ void __launch_bounds__(CR_THREADS, 1) k_cluster_rollout(ClusterRolloutParams p)
 {
     constexpr int KW = 2 * R + 1;
-    constexpr int RPG = (KW + CR_G - 1) / CR_G;     // kernel rows per group
     cg::cluster_group cl = cg::this_cluster();
     const int Q = (int)cl.num_blocks(), q = (int)cl.block_rank();
     const int H = p.H, W = p.W, C = p.C, K = p.kt.K;
     const CrLayout L(H, W, C, K, R, Q);
-    const int HS = L.HS, TH = L.TH, TW = L.TW, PADL = L.PADL;
+    const int HS = L.HS, TH = L.TH, TW = L.TW;
     extern __shared__ float4 cr_sm4[];
     float* own0 = reinterpret_cast<float*>(cr_sm4);
     float* own1 = own0 + L.own;
@@ -92,34 +90,36 @@ __global__ void __launch_bounds__(CR_THREADS, 1) k_cluster_rollout(ClusterRollou
     cl.sync();
 
     const int lane = tid & 31, warp = tid >> 5;
-    const int g = lane & (CR_G - 1), ss = lane >> 3;     // row group, strip within the warp's four
+    const int g = lane & (CR_G - 1), ss = lane >> 3;     // row group, strip of the warp's four
     const int quads = W / (4 * CR_XS);                   // four-strip groups per row
     const int n_items = HS * quads;
+    // gather: a warp takes whole tile rows, lpr lanes per row (W / 4 = 8, 16: several rows per warp)
+    const int lpr = (W4 < 32 && 32 % W4 == 0) ? W4 : 32;
+    const int rpw = 32 / lpr, sub = lane / lpr, xl = lane % lpr;
     for (int t = 0; t < p.n_steps; t++) {
         const float* cur = (t & 1) ? own1 : own0;
         float* nxt = (t & 1) ? own0 : own1;
-        // gather rows -R .. HS + R - 1 (relative to this block's first row) from their owners
-        for (int u = tid; u < C * TH * W4; u += CR_THREADS) {
-            const int c = u / (TH * W4), r = u % (TH * W4);
-            const int row = r / W4, x4 = r % W4;
-            int y = q * HS + row - R;
-            y %= H;
+        // rows -R .. HS + R - 1 (relative to this block's first row) from their
+        // owners, each value also into the periodic column halo
+        for (int rr = warp * rpw + sub; rr < C * TH; rr += (CR_THREADS / 32) * rpw) {
+            const int c = rr / TH, row = rr - c * TH;
+            int y = (q * HS + row - R) % H;
             if (y < 0) y += H;
-            const int owner = y / HS, ly = y % HS;
-            const float* src = cl.map_shared_rank(const_cast<float*>(cur), owner);
-            const float4 v = reinterpret_cast<const float4*>(src + ((size_t)c * HS + ly) * W)[x4];
-            reinterpret_cast<float4*>(tile + ((size_t)c * TH + row) * TW + PADL)[x4] = v;
-        }
-        __syncthreads();
-        // periodic column halo from the tile's own interior
-        for (int u = tid; u < C * TH * 2 * R; u += CR_THREADS) {
-            const int c = u / (TH * 2 * R), r = u % (TH * 2 * R);
-            const int row = r / (2 * R), j = r % (2 * R);
-            const int x = j < R ? j - R : W + (j - R);        // -R .. -1, then W .. W + R - 1
-            int xs = x % W;
-            if (xs < 0) xs += W;
-            float* trow = tile + ((size_t)c * TH + row) * TW + PADL;
-            trow[x] = trow[xs];
+            const int owner = y / HS, ly = y - owner * HS;
+            const float4* src = reinterpret_cast<const float4*>(
+                cl.map_shared_rank(const_cast<float*>(cur), owner) + ((size_t)c * HS + ly) * W);
+            float* trow = tile + ((size_t)c * TH + row) * TW + R;
+            for (int x4 = xl; x4 < W4; x4 += lpr) {
+                const float4 v4 = src[x4];
+                const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int x = 4 * x4 + e;
+                    trow[x] = v[e];
+                    if (x < R) trow[W + x] = v[e];
+                    if (x >= W - R) trow[x - W] = v[e];
+                }
+            }
         }
         __syncthreads();
         for (int it = warp; it < n_items; it += CR_THREADS / 32) {
@@ -129,15 +129,13 @@ __global__ void __launch_bounds__(CR_THREADS, 1) k_cluster_rollout(ClusterRollou
 #pragma unroll
             for (int c = 0; c < kMaxChannels; c++) gsum[c] = 0.f;
             for (int k = 0; k < K; k++) {
-                const float* tk = tile + (size_t)p.kt.src[k] * TH * TW + PADL - R + x0;
+                const float* tk = tile + (size_t)p.kt.src[k] * TH * TW + x0;
                 const float* wk = wt + (size_t)k * KW * KW;
                 float acc[CR_XS];
 #pragma unroll
                 for (int s = 0; s < CR_XS; s++) acc[s] = 0.f;
 #pragma unroll 1
-                for (int i = 0; i < RPG; i++) {
-                    const int dyi = g * RPG + i;                 // kernel row 0 .. KW - 1 (dy = dyi - R)
-                    if (dyi >= KW) break;
+                for (int dyi = g; dyi < KW; dyi += CR_G) {       // kernel row dyi (dy = dyi - R)
                     const float* trow = tk + (size_t)(yl + dyi) * TW;
                     const float* wrow = wk + dyi * KW;
                     float v[KW + CR_XS - 1];
@@ -182,7 +180,7 @@ __global__ void __launch_bounds__(CR_THREADS, 1) k_cluster_rollout(ClusterRollou
 #pragma unroll
             for (int c = 0; c < kMaxChannels; c++) {
                 if (c >= C) break;
-                const float a = tile[((size_t)c * TH + yl + R) * TW + PADL + x] + p.dt * gsum[c];
+                const float a = tile[((size_t)c * TH + yl + R) * TW + R + x] + p.dt * gsum[c];
                 nxt[((size_t)c * HS + yl) * W + x] = fminf(fmaxf(a, 0.f), 1.f);
             }
         }
