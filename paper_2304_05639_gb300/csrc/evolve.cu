@@ -180,15 +180,37 @@ __global__ void __launch_bounds__(DK_THREADS) k_disk_fused_t(EvoParams p)
     const int by = blockIdx.y * DK_T, bx = blockIdx.x * DK_T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int any = 0, all = 1;
-    if (by >= 2 * R && by + DK_T + 2 * R <= H && bx >= 2 * R && bx + DK_T + 2 * R <= W) {
-        const uint8_t* src = p.empty + (size_t)(by - 2 * R) * W + (bx - 2 * R);
-        for (int ty = warp; ty < E; ty += DK_THREADS / 32)
-            for (int tx = lane; tx < E; tx += 32) {
-                const int v = (int)src[(size_t)ty * W + tx];
+    if (by >= 2 * R && by + DK_T + 2 * R <= H && bx >= 2 * R && bx + DK_T + 2 * R <= W && W % 4 == 0) {
+        // interior tile: 4-byte words covering each row segment (bx is a
+        // multiple of 32, so the segment starts OFF bytes into its first
+        // word), every load of a thread issued before its stores
+        constexpr int OFF = (4 - (2 * R) % 4) % 4;
+        constexpr int NWD = (OFF + E + 3) / 4;                 // words per row
+        constexpr int PER = (E * NWD + DK_THREADS - 1) / DK_THREADS;
+        const unsigned* src =
+            reinterpret_cast<const unsigned*>(p.empty + (size_t)(by - 2 * R) * W + (bx - 2 * R - OFF));
+        const int W4 = W / 4;
+        unsigned wv[PER];
+#pragma unroll
+        for (int i = 0; i < PER; i++) {
+            const int u = threadIdx.x + i * DK_THREADS;
+            wv[i] = u < E * NWD ? __ldg(&src[(size_t)(u / NWD) * W4 + u % NWD]) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < PER; i++) {
+            const int u = threadIdx.x + i * DK_THREADS;
+            if (u >= E * NWD) break;
+            const int ty = u / NWD, x0 = 4 * (u % NWD) - OFF;
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const int tx = x0 + b;
+                if (tx < 0 || tx >= E) continue;
+                const int v = (int)((wv[i] >> (8 * b)) & 0xffu);
                 any |= v;
                 all &= v;
                 preE[ty * EP + tx + 1] = v;
             }
+        }
     } else {
         for (int ty = warp; ty < E; ty += DK_THREADS / 32) {
             const size_t row = (size_t)wrap_i(by - 2 * R + ty, H) * W;
@@ -225,6 +247,13 @@ __global__ void __launch_bounds__(DK_THREADS) k_disk_fused_t(EvoParams p)
     if (x >= W) return;
     const size_t N = (size_t)H * W;
     const bool mut_x = p.mut_plane >= 0 && wrap_i(x - p.mut_x0 + p.mut_half, W) < 2 * p.mut_half;
+    uint8_t al[DK_T / 8];
+#pragma unroll
+    for (int j = 0; j < DK_T / 8; j++) {
+        const int y = by + warp + 8 * j;
+        al[j] = y < H ? __ldg(&p.alpha[(size_t)y * W + x]) : 0;
+    }
+#pragma unroll
     for (int j = 0; j < DK_T / 8; j++) {
         const int ty = warp + 8 * j;
         const int y = by + ty;
@@ -237,7 +266,7 @@ __global__ void __launch_bounds__(DK_THREADS) k_disk_fused_t(EvoParams p)
         }
         const size_t i = (size_t)y * W + x;
         if (p.epen_out) p.epen_out[i] = (float)((double)s / p.n_disk2);
-        if (p.alpha[i]) {
+        if (al[j]) {
             if (mut_x && wrap_i(y - p.mut_y0 + p.mut_half, H) < 2 * p.mut_half)
                 p.P[(size_t)p.mut_plane * N + i] += p.mut_add;
             if (p.pen_plane >= 0 && (long long)s > p.pen_thresh) p.P[(size_t)p.pen_plane * N + i] += p.pen_add;
