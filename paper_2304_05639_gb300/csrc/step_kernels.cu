@@ -502,9 +502,37 @@ __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
 // falls below 2^-40 of the peak's (its remaining terms are below FP32
 // resolution of the sums).  The four exponentials are the accurate exp2f,
 // since their rounding is carried along each walk.
+// Each walk takes its rings in pairs on packed FP32 pairs (sm_100 family
+// f32x2 instructions): {w_r, w_(r+1)} steps by {q_r q_(r+1), q_(r+1) q_(r+2)},
+// which itself steps by s^4, and two partial sums per accumulator (num and
+// den are the sums of the pairs' halves) -- two multiplies and two
+// multiply-adds per pair of rings instead of eight scalar operations; a
+// pair is taken while its first (larger) weight is at least the stop value.
+template <int NR>
+__device__ __forceinline__ void ring_walk(float e0, float q0, float s, float stop, int r0, int step,
+                                          const float* v, const float* cnt, float2& num, float2& den)
+{
+    float2 E = make_float2(e0, e0 * q0);
+    const float qs = q0 * q0 * s;
+    float2 Q = make_float2(qs, qs * s * s);
+    const float s4 = (s * s) * (s * s);
+    const float2 S4 = make_float2(s4, s4);
+    int r = r0;
+    for (; r + step >= 0 && r + step < NR && E.x >= stop; r += 2 * step) {
+        num = __ffma2_rn(E, make_float2(v[r * 256], v[(r + step) * 256]), num);
+        den = __ffma2_rn(E, make_float2(cnt[r], cnt[r + step]), den);
+        E = __fmul2_rn(E, Q);
+        Q = __fmul2_rn(Q, S4);
+    }
+    if (r >= 0 && r < NR && E.x >= stop) {
+        num.x = fmaf(E.x, v[r * 256], num.x);
+        den.x = fmaf(E.x, cnt[r], den.x);
+    }
+}
+
 template <int NR>
 __device__ __forceinline__ void ring_bump(float c, float w, float b, const float* v, const float* cnt,
-                                          float& num, float& den)
+                                          float2& num, float2& den)
 {
     if (!(w > 0.f) || b == 0.f) return;
     constexpr float LOG2E = 1.4426950408889634f;
@@ -517,22 +545,10 @@ __device__ __forceinline__ void ring_bump(float c, float w, float b, const float
     const float aD = a * D;
     const float s = exp2f(2.f * aD * D);
     const float stop = e0 * 9.094947e-13f;             // 2^-40 of the peak weight
-    float e = e0, q = exp2f(aD * (D + 2.f * d));
-    for (int r = rs; r < NR && e >= stop; r++) {
-        num = fmaf(e, v[r * 256], num);
-        den = fmaf(e, cnt[r], den);
-        e *= q;
-        q *= s;
-    }
-    q = exp2f(aD * (D - 2.f * d));
-    e = e0 * q;
-    q *= s;
-    for (int r = rs - 1; r >= 0 && e >= stop; r--) {
-        num = fmaf(e, v[r * 256], num);
-        den = fmaf(e, cnt[r], den);
-        e *= q;
-        q *= s;
-    }
+    // up from the peak ring, then down from the ring below it
+    ring_walk<NR>(e0, exp2f(aD * (D + 2.f * d)), s, stop, rs, 1, v, cnt, num, den);
+    const float qd = exp2f(aD * (D - 2.f * d));
+    ring_walk<NR>(e0 * qd, qd * s, s, stop, rs - 1, -1, v, cnt, num, den);
 }
 
 constexpr int RG_TY = 8;     // rows per block of the ring epilogue (one site per thread)
@@ -656,9 +672,10 @@ __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
         // ring weights and the potential: each bump's weights over the rings,
         // walked outwards from its peak ring (recurrence below), summed
         // against the channel's ring potentials staged in shared memory
-        float num = 0.f, den = 0.f;
-        ring_bump<NR>(g[PK + 0], g[PK + 1], g[PK + 2], vst + tid, cnt_s, num, den);
-        ring_bump<NR>(g[PK + 3], g[PK + 4], g[PK + 5], vst + tid, cnt_s, num, den);
+        float2 num2 = make_float2(0.f, 0.f), den2 = make_float2(0.f, 0.f);
+        ring_bump<NR>(g[PK + 0], g[PK + 1], g[PK + 2], vst + tid, cnt_s, num2, den2);
+        ring_bump<NR>(g[PK + 3], g[PK + 4], g[PK + 5], vst + tid, cnt_s, num2, den2);
+        const float num = num2.x + num2.y, den = den2.x + den2.y;
         // the channel's last kernel: fetch the next channel's potentials now
         if (j + 1 < KT && p.kt.src[ord[j + 1]] != c) stage_v(p.kt.src[ord[j + 1]]);
         const float u = den > 0.f ? num / den : 0.f;
