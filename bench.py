@@ -153,6 +153,45 @@ def fp32_line(prof, H, W, scalar_tflops, pair_tflops):
                            "achieved_tflops": achieved, "frac": achieved / peak if peak > 0 else None}}
 
 
+def cufft_yardstick(torch, lenia, ctx, world, stream, ours_ms, reps=20):
+    """The same convolutions through torch.fft (cuFFT) as a timing yardstick
+    (not a path of the library): rfft2 of the C channel planes, the product
+    of each kernel's real spectrum with its source channel's spectrum, and
+    irfft2 of the K products -- the transforms the three FFT passes perform
+    (the products are one extra elementwise pass here)."""
+    H, W = world.height, world.width
+    dev = torch.device("cuda")
+    spec = []
+    for k, kd in enumerate(world.kernels):
+        R = kd.radius
+        w = torch.from_numpy(lenia.lenia_kernel_weights(ctx, k, R)).to(dev, torch.float32)
+        full = torch.zeros((H, W), dtype=torch.float32, device=dev)
+        idx = torch.arange(-R, R + 1, device=dev)
+        full[(idx[:, None] % H), (idx[None, :] % W)] = w          # correlation taps at (dy, dx)
+        spec.append(torch.fft.rfft2(full).conj())
+    S = torch.stack(spec)
+    src = torch.tensor([k.src for k in world.kernels], device=dev)
+    A = torch.from_numpy(world.A).to(dev)
+
+    def run():
+        F = torch.fft.rfft2(A)
+        return torch.fft.irfft2(F[src] * S, s=(H, W))
+    for _ in range(3):
+        U = run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        U = run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del U, S, A
+    return {"cufft_ms": ms, "ours_ms": ours_ms, "ours_over_cufft_time": ours_ms / ms if ms > 0 else None,
+            "note": "torch.fft (cuFFT): rfft2 of 3 planes, 15 spectral products, irfft2 of 15 planes, on "
+                    "torch's current stream; ours: the r2c, column and c2r passes of the same step"}
+
+
 def workload_config(ws, size=2048):
     """The benchmark workload, named by what it is (both arms print the same
     object; other sizes are profiling runs of the same recipe).  How an arm
@@ -721,6 +760,10 @@ def run_ours(args):
 
     ok_stats = bool(torch.isfinite(stats).all())
     path = lenia.lenia_conv_path(ctx)
+    fft_ref = None
+    if ws == 1 and not args.no_extras and path == lenia.CONV_FFT:
+        fft_ms = sum(prof[k][0] / max(1, prof[k][1]) for k in ("rows_r2c", "cols_conv", "rows_c2r") if k in prof)
+        fft_ref = cufft_yardstick(torch, lenia, ctx, world, stream, fft_ms)
     lenia.lenia_destroy(ctx)
     if rank != 0:
         if ws > 1:
@@ -763,6 +806,8 @@ def run_ours(args):
         "alpha1_sites": alpha1,
         "kernel_profile": f"per-launch CUDA events over {prof_steps} steps after the timed region",
     }
+    if fft_ref is not None:
+        line["fft_yardstick"] = fft_ref
     if not args.no_extras and ws == 1 and args.size == 2048:
         line["adjoint"] = adjoint_leg(torch, lenia, inputs, stream)
         line["batched"] = batched_leg(torch, lenia, inputs, stream)
