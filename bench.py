@@ -58,12 +58,12 @@ def fft_flops(H, W, C, K):
     return C * (rows + cols) + K * ((W // 2 + 1) * H * 2.0 + cols + rows)
 
 
-def _traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, or
-    None when the kernel's sources changed since the capture."""
+def _traffic(kernel: str, name="epilogue_traffic.json", key="dram_bytes_per_launch"):
+    """DRAM bytes (per launch of `kernel`, or per step) from a committed ncu
+    capture, or None when the sources changed since the capture."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "epilogue_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             d = json.load(f)
         if d.get("kernel") != kernel:
             return None
@@ -71,7 +71,7 @@ def _traffic(kernel: str):
         for src in d["sources"]:
             with open(os.path.join(ROOT, src), "rb") as f:
                 h.update(f.read())
-        return int(d["dram_bytes_per_launch"]) if h.hexdigest() == d["sources_sha256"] else None
+        return int(d[key]) if h.hexdigest() == d["sources_sha256"] else None
     except (OSError, KeyError, ValueError):
         return None
 
@@ -780,6 +780,8 @@ def run_ours(args):
     alg_bytes = ALG_BYTES_PER_SITE * sites if dom[0] == "epilogue" else 0
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     traffic = _traffic(dom[0]) if args.size == 2048 else None
+    step_traffic = (_traffic("step", "step_traffic.json", "dram_bytes_per_step")
+                    if args.size == 2048 and path == lenia.CONV_FFT else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -790,7 +792,10 @@ def run_ours(args):
                      "traffic": traffic,
                      "traffic_gbs": (traffic / (dom_ms / 1e3) / 1e9) if traffic else None,
                      "alg_bytes_per_site": ALG_BYTES_PER_SITE,
-                     "step_frac": (ALG_BYTES_PER_SITE * sites * args.steps / (t_max / 1e3) / 1e9) / hbm},
+                     "step_frac": (ALG_BYTES_PER_SITE * sites * args.steps / (t_max / 1e3) / 1e9) / hbm,
+                     "step_traffic": step_traffic,
+                     "step_dram_frac": (step_traffic * args.steps / (t_max / 1e3) / 1e9) / hbm
+                     if step_traffic else None},
         "fp32": fp32_line(prof, H, W, fp32_scalar, fp32_pair),
         "kernels_ms": {k: {"avg_ms": v[0] / max(1, v[1]), "launches": v[1],
                            "share": v[0] / max(1e-9, sum(x[0] for x in prof.values()))}
