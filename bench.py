@@ -309,13 +309,15 @@ def batched_leg(torch, lenia, inputs, stream, steps=200):
 def small_legs(torch, lenia, inputs, stream, fp32_peak=None):
     """The two small configurations as rollouts through lenia_rollout: the
     64^2 one-kernel world with global genes (100 steps; launch- and
-    latency-bound, reported in us per step) and the 1024^2 one-channel world
+    latency-bound, reported in us per step), on its automatic (FFT) route
+    and on the direct route (one thread-block cluster), and the 1024^2 one-channel world
     with localized mu/sigma (1000 steps; reported against the HBM and FP32
     peaks; its state, ~12 MB, stays in L2)."""
     out = {}
-    for name, w, steps in (("c1", inputs.single_kernel_global(), 100),
-                           ("c2", inputs.localized_single_channel(), 1000)):
-        cfg, ks = lenia.config_from_world(w)
+    for name, w, steps, cp in (("c1", inputs.single_kernel_global(), 100, lenia.CONV_AUTO),
+                               ("c1_direct_route", inputs.single_kernel_global(), 100, lenia.CONV_DIRECT),
+                               ("c2", inputs.localized_single_channel(), 1000, lenia.CONV_AUTO)):
+        cfg, ks = lenia.config_from_world(w, cp)
         ctx = lenia.lenia_init(cfg, ks, stream)
         try:
             a = torch.from_numpy(w.A).cuda()
@@ -331,6 +333,7 @@ def small_legs(torch, lenia, inputs, stream, fp32_peak=None):
             ms = e0.elapsed_time(e1)
             path = lenia.lenia_conv_path(ctx)
             lps = lenia.lenia_launches_per_step(ctx)
+            route = lenia.lenia_rollout_route(ctx)
         finally:
             lenia.lenia_destroy(ctx)
         v = w.sites * steps / (ms / 1e3)
@@ -338,7 +341,11 @@ def small_legs(torch, lenia, inputs, stream, fp32_peak=None):
         r = {"workload": f"{w.height}x{w.width}, {w.n_channels} channel, {w.n_kernels} kernel R={w.kernels[0].radius}, "
                          + ("localized mu/sigma, gene maintenance" if w.P is not None else "global genes"),
              "steps": steps, "us_per_step": ms * 1e3 / steps, "value": v, "unit": UNIT,
-             "conv_path": "fft" if path == lenia.CONV_FFT else "direct", "launches_per_step": lps,
+             "conv_path": "fft" if path == lenia.CONV_FFT else "direct",
+             "rollout": {lenia.ROUTE_STEPS: f"{lps} launches per step, pairs of steps replayed from a CUDA graph",
+                         lenia.ROUTE_COOPERATIVE: "one cooperative launch",
+                         lenia.ROUTE_CLUSTER: "one thread-block cluster"}.get(route, "?"),
+             "launches_per_step": lps if route == lenia.ROUTE_STEPS else 1.0 / steps,
              "alg_bytes_per_site": alg, "frac_of_hbm": v * alg / 1e9 / _peaks()[0]}
         if fp32_peak and path == lenia.CONV_FFT:
             fl = fft_flops(w.height, w.width, w.n_channels, w.n_kernels)
@@ -389,15 +396,15 @@ def evolve_leg(torch, lenia, inputs, stream, plain_ms, steps=100):
     finally:
         lenia.lenia_destroy(ctx)
     sites = H * W
-    disk_ms = sum(prof[k][0] / max(1, prof[k][1]) for k in ("oxy_disk", "pen_disk") if k in prof)
-    # each disk pass reads its input (1 or 2 bytes per site) and the second the
-    # alpha byte, and writes 2 bytes (counts) or the touched gene values
-    disk_bytes = sites * (1 + 2) + sites * (2 + 1)
+    disk_ms = prof["pen_disk"][0] / max(1, prof["pen_disk"][1]) if "pen_disk" in prof else 0.0
+    # the disk pass reads the not-Delta_sum byte and the alpha byte of every
+    # site and writes only the few gene values it changes
+    disk_bytes = sites * 2
     return {"workload": "2048x2048, 3 channels, 15 kernels R=18, walls + mutation + penalisation each step",
             "steps": steps, "ms_per_step": ms, "value": sites / (ms / 1e3), "unit": UNIT,
             "over_plain_step": ms / plain_ms if plain_ms else None,
             "kernels_ms": {k: v[0] / max(1, v[1]) for k, v in prof.items()},
-            "disk_passes_gbs": disk_bytes / (disk_ms / 1e3) / 1e9 if disk_ms > 0 else None,
+            "disk_pass_gbs": disk_bytes / (disk_ms / 1e3) / 1e9 if disk_ms > 0 else None,
             "stats_finite": bool(torch.isfinite(st).all())}
 
 

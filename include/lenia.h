@@ -326,7 +326,7 @@ LENIA_API lenia_status lenia_host_wait(lenia_ctx* ctx, void* stream);
  * lenia_profile_stop waits for those events and fills total_ms[kind] (summed
  * milliseconds) and counts[kind] for the launch kinds 0..LENIA_PROFILE_KINDS-1
  * (names from lenia_profile_kind_name), then turns recording off. */
-#define LENIA_PROFILE_KINDS 10
+#define LENIA_PROFILE_KINDS 9
 LENIA_API lenia_status lenia_profile_start(lenia_ctx* ctx, int32_t max_launches);
 LENIA_API lenia_status lenia_profile_stop(lenia_ctx* ctx, float* total_ms, int32_t* counts);
 LENIA_API const char* lenia_profile_kind_name(int32_t kind);

@@ -123,9 +123,9 @@ struct lenia_ctx {
 
 // names of the launch kinds the profiler distinguishes
 static const char* kKindNames[] = {"rows_r2c", "cols_conv", "rows_c2r", "direct_conv", "epilogue",
-                                   "stats_partials", "stats_final", "walls", "oxy_disk", "pen_disk"};
+                                   "stats_partials", "stats_final", "walls", "pen_disk"};
 enum { KIND_R2C, KIND_COLS, KIND_C2R, KIND_DIRECT, KIND_EPI, KIND_STATS_P, KIND_STATS_F, KIND_WALLS,
-       KIND_OXY, KIND_PEN, KIND_COUNT };
+       KIND_PEN, KIND_COUNT };
 static_assert(KIND_COUNT == LENIA_PROFILE_KINDS, "profile kinds and the header disagree");
 static_assert(sizeof(kKindNames) / sizeof(kKindNames[0]) == KIND_COUNT, "one name per profile kind");
 

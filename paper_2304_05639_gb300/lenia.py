@@ -31,7 +31,7 @@ EXPORTS = ("lenia_init", "lenia_step", "lenia_rollout", "lenia_backward", "lenia
            "lenia_selftest_wait_timeout", "lenia_set_walls", "lenia_step_evolve",
            "lenia_step_host_async", "lenia_host_wait", "lenia_batch_group_of", "lenia_measure_fp32_peak",
            "lenia_debug_fail_after", "lenia_batch_epilogue_shape", "lenia_batch_set_epilogue_shape")
-PROFILE_KINDS = 10
+PROFILE_KINDS = 9
 
 
 class LeniaError(RuntimeError):
