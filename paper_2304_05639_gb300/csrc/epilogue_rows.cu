@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
                     const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_h, int n_chunks, int n_bands,
                     int* status)
 {
+    pdl_enter();
     static_assert(TOPO == 0 || (KT == 15 && CT == 3), "paper topology has 15 kernels, 3 channels");
     static_assert(CT * 5 <= ER_THREADS / 32, "one warp per statistics sum");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -431,6 +432,7 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
     k_epilogue_queue(EpiParams p, const QueueWorld* __restrict__ worlds, int n_items, int n_chunks, int n_bands,
                      int* counter, int* status)
 {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
     const ErSmem<1, 1, LOC, EQ_NP, EQ_NU> sm(smem);
@@ -569,7 +571,7 @@ static cudaError_t launch_rows(const EpiParams& p, int num_sms, int* status, cud
         return cudaErrorInvalidValue;
     if (!plane_map(&tu, p.U, p.W, p.H, KT, ER_CH / 2, KT) || !plane_map(&ta, p.A, p.W, p.H, CT, ER_CH / 2, CT))
         return cudaErrorInvalidValue;
-    kern<<<n_chunks * n_bands, ER_THREADS, L::bytes, s>>>(p, tp, tu, ta, th, n_chunks, n_bands, status);
+    launch_pdl(kern, n_chunks * n_bands, ER_THREADS, L::bytes, s, p, tp, tu, ta, th, n_chunks, n_bands, status);
     return cudaGetLastError();
 }
 
@@ -639,7 +641,7 @@ static cudaError_t launch_queue(const EpiParams& p, const QueueWorld* worlds, in
     const int grid = std::min(n_items, n_sms * per_sm);
     e = cudaMemsetAsync(counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_epilogue_queue<LOC, EPS0><<<grid, ER_THREADS, L::bytes, s>>>(p, worlds, n_items, n_chunks, n_bands, counter,
+    launch_pdl(k_epilogue_queue<LOC, EPS0>, grid, ER_THREADS, L::bytes, s, p, worlds, n_items, n_chunks, n_bands, counter,
                                                                     status);
     return cudaGetLastError();
 }

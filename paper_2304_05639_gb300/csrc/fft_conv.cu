@@ -36,6 +36,7 @@ namespace lenia {
 template <int M, int T, int NB, bool BULK>
 __global__ void __launch_bounds__(T, 3) k_rows_r2c(FftParams p)
 {
+    pdl_enter();
     extern __shared__ float4 sm4[];
     float2* sm = reinterpret_cast<float2*>(sm4);
     constexpr int SZ = row_pitch(M);
@@ -160,6 +161,7 @@ template <int M, int T, int NB>
 __global__ void __launch_bounds__(T, (512 / T) < 8 ? (512 / T) : 8)
     k_rows_c2r(FftParams p, const __grid_constant__ CUtensorMap tm_uhat)
 {
+    pdl_enter();
     constexpr int R = fft_radix(M, ROW_RMAX);
     static_assert(R == 32 || R == M, "first inverse row pass is radix 32");
     constexpr int BX = M < C2R_BOX ? M : C2R_BOX;
@@ -308,6 +310,7 @@ __device__ __noinline__ void cols_conv_dc(const FftParams& p, float2* Bf, int pl
 template <int H, int T, bool PERK>
 __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(FftParams p)
 {
+    pdl_enter();
     constexpr bool TM = cols_tmem<H>();
     extern __shared__ float2 sm[];
     float2* F = sm;                                         // forward spectrum (smem variant)
@@ -427,6 +430,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
 template <int H, int T>
 __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_adj(FftParams p)
 {
+    pdl_enter();
     extern __shared__ float2 sm[];
     float2* F = sm;
     float2* Acc = sm + H;
@@ -484,11 +488,11 @@ static cudaError_t rows_launch_nb(const FftParams& p, cudaStream_t s, bool inver
         if (p.A_list ? p.list_aligned != 0 : ((uintptr_t)p.A & 15) == 0) {
             cudaError_t e = smem_limit<k_rows_r2c<M, T1, NB, true>>(smem);
             if (e != cudaSuccess) return e;
-            k_rows_r2c<M, T1, NB, true><<<dim3(p.H / NB, p.C), T1, smem, s>>>(p);
+            launch_pdl(k_rows_r2c<M, T1, NB, true>, dim3(p.H / NB, p.C), T1, smem, s, p);
         } else {
             cudaError_t e = smem_limit<k_rows_r2c<M, T1, NB, false>>(smem);
             if (e != cudaSuccess) return e;
-            k_rows_r2c<M, T1, NB, false><<<dim3(p.H / NB, p.C), T1, smem, s>>>(p);
+            launch_pdl(k_rows_r2c<M, T1, NB, false>, dim3(p.H / NB, p.C), T1, smem, s, p);
         }
     } else {
         // column-major spectrum [plane][kx][y] as (y, kx, plane) of 8-byte elements
@@ -497,7 +501,7 @@ static cudaError_t rows_launch_nb(const FftParams& p, cudaStream_t s, bool inver
         if (!spectrum_map(&tm, p.Uhat, p.H, M, p.K, NB, BX)) return cudaErrorInvalidValue;
         cudaError_t e = smem_limit<k_rows_c2r<M, TI, NB>>(smem + 128);
         if (e != cudaSuccess) return e;
-        k_rows_c2r<M, TI, NB><<<dim3(p.H / NB, p.K), TI, smem + 128, s>>>(p, tm);
+        launch_pdl(k_rows_c2r<M, TI, NB>, dim3(p.H / NB, p.K), TI, smem + 128, s, p, tm);
     }
     return cudaGetLastError();
 }
@@ -529,7 +533,7 @@ static cudaError_t cols_launch(const FftParams& p, cudaStream_t s, bool transpos
         const size_t smem = 2 * (size_t)H * 8;
         cudaError_t e = smem_limit<k_cols_adj<H, T>>(smem);
         if (e != cudaSuccess) return e;
-        k_cols_adj<H, T><<<dim3(M, p.C), T, smem, s>>>(p);
+        launch_pdl(k_cols_adj<H, T>, dim3(M, p.C), T, smem, s, p);
         return cudaGetLastError();
     }
     int kmax = 0;
@@ -538,11 +542,11 @@ static cudaError_t cols_launch(const FftParams& p, cudaStream_t s, bool transpos
     if (M * p.C < 608 && kmax > 1) {
         cudaError_t e = smem_limit<k_cols_conv<H, T, true>>(smem);
         if (e != cudaSuccess) return e;
-        k_cols_conv<H, T, true><<<dim3(M, p.C, kmax), T, smem, s>>>(p);
+        launch_pdl(k_cols_conv<H, T, true>, dim3(M, p.C, kmax), T, smem, s, p);
     } else {
         cudaError_t e = smem_limit<k_cols_conv<H, T, false>>(smem);
         if (e != cudaSuccess) return e;
-        k_cols_conv<H, T, false><<<dim3(M, p.C), T, smem, s>>>(p);
+        launch_pdl(k_cols_conv<H, T, false>, dim3(M, p.C), T, smem, s, p);
     }
     return cudaGetLastError();
 }

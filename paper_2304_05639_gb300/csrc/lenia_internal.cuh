@@ -34,6 +34,38 @@ inline cudaError_t smem_limit(size_t bytes)
     return e;
 }
 
+// Programmatic dependent launch: the kernels of the step's chain (the FFT
+// passes, the direct convolution and the epilogues) are launched with the
+// programmatic-serialization attribute, so that the launch of each one is
+// prepared while its predecessor in the stream still runs and its blocks
+// start as soon as the predecessor's last block exits.  Each of them starts
+// with pdl_enter(), which waits until the predecessor has completed and its
+// writes are visible, so no block touches global memory before the work it
+// depends on is done.  (No kernel signals its dependents early: letting them
+// be scheduled once all of a grid's blocks run made the step slower.)
+// Launched without the attribute, pdl_enter() returns at once.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Per-kernel scalars, passed by value to the kernels that need them.
 struct KernelTable {
     int K, C;

@@ -45,6 +45,7 @@ struct DcTile {
 template <int CX, int RY>
 __global__ void __launch_bounds__(256) k_direct_conv(ConvParams p, int maxR, const __grid_constant__ CUtensorMap tm_a)
 {
+    pdl_enter();
     using T = DcTile<CX, RY>;
     extern __shared__ __align__(128) unsigned char dc_raw[];
     float* tile = reinterpret_cast<float*>(dc_raw + ((128 - (smem_addr(dc_raw) & 127)) & 127));
@@ -181,7 +182,7 @@ static cudaError_t launch_dc(const ConvParams& p, int max_R, int planes, cudaStr
     // worlds too narrow or short for an interior tile use plain loads only
     q.tma = p.W >= pitch && p.H >= rows && dc_map(&tm, p.A, p.W, p.H, p.C, pitch, rows);
     dim3 grid((p.W + T::TW - 1) / T::TW, (p.H + T::TH - 1) / T::TH, planes);
-    k_direct_conv<CX, RY><<<grid, dim3(32, 8), smem, s>>>(q, max_R, tm);
+    launch_pdl(k_direct_conv<CX, RY>, grid, dim3(32, 8), smem, s, q, max_R, tm);
     return cudaGetLastError();
 }
 
@@ -255,6 +256,7 @@ __device__ __forceinline__ void block_stats(const float* st, int C, double* part
 template <int KT, int CT, int LOC, int RY = EP_RY>
 __global__ void __launch_bounds__(256, 3) k_epilogue_r1(EpiParams p)
 {
+    pdl_enter();
     constexpr int NP = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
     constexpr int PMU = (LOC & 1) ? 0 : -1;
     constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
@@ -391,6 +393,7 @@ __device__ float ring_potential(const EpiParams& p, const float* ph, int K, int 
 // live in local memory).
 __global__ void __launch_bounds__(256) k_epilogue_generic(EpiParams p)
 {
+    pdl_enter();
     const int K = p.kt.K, C = p.kt.C, n_p = p.n_p;
     const int H = p.H, W = p.W;
     const size_t N = (size_t)H * W;
@@ -559,6 +562,7 @@ constexpr int RG_TILE_W = EP_TX + 2, RG_TILE_H = RG_TY + 2;
 template <int KT, int CT, int NR, int LOC>
 __global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
 {
+    pdl_enter();
     constexpr int NG = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
     constexpr int NP = NG + 6;
     constexpr int PMU = (LOC & 1) ? 0 : -1;
@@ -739,6 +743,7 @@ int ring_epilogue_blocks(int H, int W) { return ((W + EP_TX - 1) / EP_TX) * ((H 
 template <int LOC, int BR>
 __global__ void __launch_bounds__(256) k_epilogue_batch11(EpiParams p)
 {
+    pdl_enter();
     constexpr int NP = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
     constexpr int PMU = (LOC & 1) ? 0 : -1;
     constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
@@ -833,6 +838,7 @@ __global__ void __launch_bounds__(256) k_epilogue_batch11(EpiParams p)
 template <int LOC, int BR>
 __global__ void __launch_bounds__(256) k_epilogue_batch11v(EpiParams p)
 {
+    pdl_enter();
     constexpr int NP = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
     constexpr int PMU = (LOC & 1) ? 0 : -1;
     constexpr int PSG = (LOC & 2) ? ((LOC & 1) ? 1 : 0) : -1;
@@ -953,11 +959,11 @@ cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t
     if ((br == -1 || br == -2) && K == 1 && p.W % (4 * EP_TX) == 0 && p.H % (EP_TY * -br) == 0) {
         dim3 g4(p.W / (4 * EP_TX), p.H / (EP_TY * -br), n_worlds);
         if (br == -1) {
-            if (loc == 3) k_epilogue_batch11v<3, 1><<<g4, block, 0, s>>>(p);
-            else k_epilogue_batch11v<0, 1><<<g4, block, 0, s>>>(p);
+            if (loc == 3) launch_pdl(k_epilogue_batch11v<3, 1>, g4, block, 0, s, p);
+            else launch_pdl(k_epilogue_batch11v<0, 1>, g4, block, 0, s, p);
         } else {
-            if (loc == 3) k_epilogue_batch11v<3, 2><<<g4, block, 0, s>>>(p);
-            else k_epilogue_batch11v<0, 2><<<g4, block, 0, s>>>(p);
+            if (loc == 3) launch_pdl(k_epilogue_batch11v<3, 2>, g4, block, 0, s, p);
+            else launch_pdl(k_epilogue_batch11v<0, 2>, g4, block, 0, s, p);
         }
         return cudaGetLastError();
     }
@@ -965,24 +971,24 @@ cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t
     if (K == 1 && p.W % EP_TX == 0 && p.H % (EP_TY * br) == 0) {
         dim3 g4(p.W / EP_TX, p.H / (EP_TY * br), n_worlds);
         if (br == 1) {
-            if (loc == 3) k_epilogue_batch11<3, 1><<<g4, block, 0, s>>>(p);
-            else k_epilogue_batch11<0, 1><<<g4, block, 0, s>>>(p);
+            if (loc == 3) launch_pdl(k_epilogue_batch11<3, 1>, g4, block, 0, s, p);
+            else launch_pdl(k_epilogue_batch11<0, 1>, g4, block, 0, s, p);
         } else if (br == 2) {
-            if (loc == 3) k_epilogue_batch11<3, 2><<<g4, block, 0, s>>>(p);
-            else k_epilogue_batch11<0, 2><<<g4, block, 0, s>>>(p);
+            if (loc == 3) launch_pdl(k_epilogue_batch11<3, 2>, g4, block, 0, s, p);
+            else launch_pdl(k_epilogue_batch11<0, 2>, g4, block, 0, s, p);
         } else {
-            if (loc == 3) k_epilogue_batch11<3, 4><<<g4, block, 0, s>>>(p);
-            else k_epilogue_batch11<0, 4><<<g4, block, 0, s>>>(p);
+            if (loc == 3) launch_pdl(k_epilogue_batch11<3, 4>, g4, block, 0, s, p);
+            else launch_pdl(k_epilogue_batch11<0, 4>, g4, block, 0, s, p);
         }
         return cudaGetLastError();
     }
     // one row per thread: the worlds of a group are often small, so the grid
     // needs the extra blocks (no statistics are gathered here)
     dim3 grid((p.W + EP_TX - 1) / EP_TX, (p.H + EP_TY - 1) / EP_TY, n_worlds);
-    if (K == 15 && loc == 3) k_epilogue_r1<15, 3, 3, 1><<<grid, block, 0, s>>>(p);
-    else if (K == 15) k_epilogue_r1<15, 3, 0, 1><<<grid, block, 0, s>>>(p);
-    else if (loc == 3) k_epilogue_r1<1, 1, 3, 1><<<grid, block, 0, s>>>(p);
-    else k_epilogue_r1<1, 1, 0, 1><<<grid, block, 0, s>>>(p);
+    if (K == 15 && loc == 3) launch_pdl(k_epilogue_r1<15, 3, 3, 1>, grid, block, 0, s, p);
+    else if (K == 15) launch_pdl(k_epilogue_r1<15, 3, 0, 1>, grid, block, 0, s, p);
+    else if (loc == 3) launch_pdl(k_epilogue_r1<1, 1, 3, 1>, grid, block, 0, s, p);
+    else launch_pdl(k_epilogue_r1<1, 1, 0, 1>, grid, block, 0, s, p);
     return cudaGetLastError();
 }
 
@@ -1011,22 +1017,22 @@ cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks)
         cudaError_t e = cudaSuccess;
         if (p.n_rings == 24 && K == 15) {
             e = smem_limit<k_epilogue_rings<15, 3, 24, 15>>(vb);
-            if (e == cudaSuccess) k_epilogue_rings<15, 3, 24, 15><<<rgrid, rblock, vb, s>>>(p);
+            if (e == cudaSuccess) launch_pdl(k_epilogue_rings<15, 3, 24, 15>, rgrid, rblock, vb, s, p);
         } else if (p.n_rings == 24) {
             e = smem_limit<k_epilogue_rings<1, 1, 24, 15>>(vb);
-            if (e == cudaSuccess) k_epilogue_rings<1, 1, 24, 15><<<rgrid, rblock, vb, s>>>(p);
+            if (e == cudaSuccess) launch_pdl(k_epilogue_rings<1, 1, 24, 15>, rgrid, rblock, vb, s, p);
         } else {
             e = smem_limit<k_epilogue_rings<15, 3, 12, 15>>(vb);
-            if (e == cudaSuccess) k_epilogue_rings<15, 3, 12, 15><<<rgrid, rblock, vb, s>>>(p);
+            if (e == cudaSuccess) launch_pdl(k_epilogue_rings<15, 3, 12, 15>, rgrid, rblock, vb, s, p);
         }
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
-    if (r1 && K == 15 && C == 3 && loc == 3) k_epilogue_r1<15, 3, 3><<<grid, block, 0, s>>>(p);
-    else if (r1 && K == 15 && C == 3 && loc == 0) k_epilogue_r1<15, 3, 0><<<grid, block, 0, s>>>(p);
-    else if (r1 && K == 1 && C == 1 && loc == 3) k_epilogue_r1<1, 1, 3><<<grid, block, 0, s>>>(p);
-    else if (r1 && K == 1 && C == 1 && loc == 0) k_epilogue_r1<1, 1, 0><<<grid, block, 0, s>>>(p);
-    else k_epilogue_generic<<<grid, block, 0, s>>>(p);
+    if (r1 && K == 15 && C == 3 && loc == 3) launch_pdl(k_epilogue_r1<15, 3, 3>, grid, block, 0, s, p);
+    else if (r1 && K == 15 && C == 3 && loc == 0) launch_pdl(k_epilogue_r1<15, 3, 0>, grid, block, 0, s, p);
+    else if (r1 && K == 1 && C == 1 && loc == 3) launch_pdl(k_epilogue_r1<1, 1, 3>, grid, block, 0, s, p);
+    else if (r1 && K == 1 && C == 1 && loc == 0) launch_pdl(k_epilogue_r1<1, 1, 0>, grid, block, 0, s, p);
+    else launch_pdl(k_epilogue_generic, grid, block, 0, s, p);
     return cudaGetLastError();
 }
 
