@@ -26,6 +26,7 @@ constexpr float ADJ_HALF_LOG2E = 0.721347520444481703680f;   // 0.5 log2(e)
 // the forward streaming epilogue so that clip decisions match.
 __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint_epilogue(AdjParams p)
 {
+    pdl_enter();
     const int K = p.kt.K, C = p.kt.C;
     const size_t N = (size_t)p.H * p.W;
     const size_t i = (size_t)blockIdx.x * ADJ_THREADS + threadIdx.x;
@@ -94,6 +95,7 @@ constexpr int ADJ_RED_THREADS = 256;
 __global__ void __launch_bounds__(ADJ_RED_THREADS) k_adjoint_gene_reduce(const double* partials, int nb,
                                                                       double* gene_acc)
 {
+    pdl_enter();
     __shared__ double wsum[ADJ_RED_THREADS / 32];
     const int v = blockIdx.x;
     const double* src = partials + (size_t)v * nb;
@@ -120,6 +122,7 @@ __global__ void __launch_bounds__(ADJ_RED_THREADS) k_adjoint_gene_reduce(const d
 // or gpre_c + V_c when the sum over kernels was taken in the frequency domain
 __global__ void __launch_bounds__(256) k_adjoint_gather(AdjParams p)
 {
+    pdl_enter();
     const size_t N = (size_t)p.H * p.W;
     const size_t i = (size_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= N) return;
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(256) k_adjoint_gather(AdjParams p)
 
 __global__ void k_adjoint_gene_out(const double* gene_acc, int nv, float* out)
 {
+    pdl_enter();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v < nv) out[v] = (float)gene_acc[v];
 }
@@ -146,23 +150,23 @@ int adjoint_blocks(int H, int W) { return (int)(((size_t)H * W + ADJ_THREADS - 1
 cudaError_t launch_adjoint_epilogue(const AdjParams& p, cudaStream_t s)
 {
     const int nb = adjoint_blocks(p.H, p.W);
-    k_adjoint_epilogue<<<nb, ADJ_THREADS, 0, s>>>(p);
+    launch_pdl(k_adjoint_epilogue, nb, ADJ_THREADS, 0, s, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_adjoint_gene_reduce<<<p.kt.K * 3, ADJ_RED_THREADS, 0, s>>>(p.gene_partials, nb, p.gene_acc);
+    launch_pdl(k_adjoint_gene_reduce, p.kt.K * 3, ADJ_RED_THREADS, 0, s, p.gene_partials, nb, p.gene_acc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_gather(const AdjParams& p, cudaStream_t s)
 {
     const size_t N = (size_t)p.H * p.W;
-    k_adjoint_gather<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(p);
+    launch_pdl(k_adjoint_gather, (unsigned)((N + 255) / 256), 256, 0, s, p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_gene_out(const double* gene_acc, int nv, float* out, cudaStream_t s)
 {
-    k_adjoint_gene_out<<<(nv + 63) / 64, 64, 0, s>>>(gene_acc, nv, out);
+    launch_pdl(k_adjoint_gene_out, (nv + 63) / 64, 64, 0, s, gene_acc, nv, out);
     return cudaGetLastError();
 }
 

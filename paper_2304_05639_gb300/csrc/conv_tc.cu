@@ -109,6 +109,7 @@ template <int NT, int TERMS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_conv_tc(TcConvParams p, const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo)
 {
+    pdl_enter();
     constexpr int NA = TERMS == 1 ? 1 : 2;          // input tiles (hi, lo)
     constexpr int NB = TERMS == 1 ? 1 : 2;          // Toeplitz blocks per slot (hi, lo)
     constexpr int NCOLS = 2 * TC_NG * NT;           // accumulator columns
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 __global__ void k_tc_pad(const float* A, int C, int H, int W, int R, int Hp, int Wp, __nv_bfloat16* hi,
                          __nv_bfloat16* lo)
 {
+    pdl_enter();
     const size_t n = (size_t)C * Hp * Wp;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(i % Wp);
@@ -352,7 +354,7 @@ cudaError_t launch_tc(const TcConvParams& p, cudaStream_t s)
     if (!tc_map(&th, p.Ap_hi, p.Wp, p.Hp, p.C, p.rows_pad / 2)) return cudaErrorInvalidValue;
     if (TERMS == 3 && !tc_map(&tl, p.Ap_lo, p.Wp, p.Hp, p.C, p.rows_pad / 2)) return cudaErrorInvalidValue;
     const dim3 grid(p.W / NT, p.H / TC_ROWS_OUT, p.n_groups);
-    k_conv_tc<NT, TERMS><<<grid, TC_THREADS, smem, s>>>(p, th, tl);
+    launch_pdl(k_conv_tc<NT, TERMS>, grid, TC_THREADS, smem, s, p, th, tl);
     return cudaGetLastError();
 }
 
@@ -371,7 +373,7 @@ bool tc_conv_supported(int H, int W, int max_R)
 cudaError_t launch_conv_tc(const TcConvParams& p, const float* A, cudaStream_t s)
 {
     int blocks = (int)std::min<size_t>(((size_t)p.C * p.Hp * p.Wp + 255) / 256, 4096);
-    k_tc_pad<<<blocks, 256, 0, s>>>(A, p.C, p.H, p.W, p.R, p.Hp, p.Wp, reinterpret_cast<__nv_bfloat16*>(p.Ap_hi),
+    launch_pdl(k_tc_pad, blocks, 256, 0, s, A, p.C, p.H, p.W, p.R, p.Hp, p.Wp, reinterpret_cast<__nv_bfloat16*>(p.Ap_hi),
                                     p.terms == 3 ? reinterpret_cast<__nv_bfloat16*>(p.Ap_lo) : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -74,6 +74,7 @@ __device__ __forceinline__ void row_scans(int* pre, int S, int SP)
 // (integer, exact).
 __global__ void __launch_bounds__(DK_THREADS) k_disk_fused(EvoParams p)
 {
+    pdl_enter();
     extern __shared__ int sm_i[];
     const int r = p.r_oxy;
     const int E = DK_T + 4 * r, EP = E + 1;     // empty bytes: tile + 2 r halo
@@ -171,6 +172,7 @@ __device__ __forceinline__ void row_scans_seq(int* pre, int rows, int SP)
 template <int R>
 __global__ void __launch_bounds__(DK_THREADS) k_disk_fused_t(EvoParams p)
 {
+    pdl_enter();
     constexpr int E = DK_T + 4 * R, EP = E + 1;     // empty bytes: tile + 2 R halo
     constexpr int S = DK_T + 2 * R, SP = S + 1;     // n - c: tile + R halo
     constexpr DiskRows<R> D{};
@@ -278,7 +280,7 @@ template <int R>
 static cudaError_t launch_disk_t(const EvoParams& p, cudaStream_t s)
 {
     const dim3 grid((p.W + DK_T - 1) / DK_T, (p.H + DK_T - 1) / DK_T);
-    k_disk_fused_t<R><<<grid, DK_THREADS, 0, s>>>(p);
+    launch_pdl(k_disk_fused_t<R>, grid, DK_THREADS, 0, s, p);
     return cudaGetLastError();
 }
 
@@ -305,7 +307,7 @@ cudaError_t launch_disk_fused(const EvoParams& p, cudaStream_t s)
     cudaError_t e = smem_limit<k_disk_fused>(smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((p.W + DK_T - 1) / DK_T, (p.H + DK_T - 1) / DK_T);
-    k_disk_fused<<<grid, DK_THREADS, smem, s>>>(p);
+    launch_pdl(k_disk_fused, grid, DK_THREADS, smem, s, p);
     return cudaGetLastError();
 }
 
@@ -314,6 +316,7 @@ cudaError_t launch_disk_fused(const EvoParams& p, cudaStream_t s)
 // of one plane together (the list is in increasing site order).
 __global__ void k_walls_zero(const int* idx, int n, float* A, int C, float* P, int npk, size_t N)
 {
+    pdl_enter();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * (C + npk)) return;
     const int plane = t / n, j = t - plane * n;
@@ -330,7 +333,7 @@ cudaError_t launch_walls_zero(const int* idx, int n, float* A, int C, float* P, 
     if (n <= 0) return cudaSuccess;
     const long long total = (long long)n * (C + npk);
     if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_walls_zero<<<(int)((total + 255) / 256), 256, 0, s>>>(idx, n, A, C, P, npk, N);
+    launch_pdl(k_walls_zero, (int)((total + 255) / 256), 256, 0, s, idx, n, A, C, P, npk, N);
     return cudaGetLastError();
 }
 

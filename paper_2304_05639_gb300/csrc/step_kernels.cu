@@ -1045,6 +1045,7 @@ __global__ void __launch_bounds__(256) k_stats_partials(const float* A, int C, i
                                                         const float* sin_x, const float* cos_x,
                                                         double* partials)
 {
+    pdl_enter();
     const int x = blockIdx.x * EP_TX + threadIdx.x;
     float st[kMaxChannels * 5];
     for (int v = 0; v < kMaxChannels * 5; v++) st[v] = 0.f;
@@ -1071,7 +1072,7 @@ cudaError_t launch_stats_partials(const float* A, int C, int H, int W, const flo
 {
     dim3 grid((W + EP_TX - 1) / EP_TX, (H + EP_TY * EP_RY - 1) / (EP_TY * EP_RY));
     if (n_blocks) *n_blocks = grid.x * grid.y;
-    k_stats_partials<<<grid, dim3(EP_TX, EP_TY), 0, s>>>(A, C, H, W, sin_y, cos_y, sin_x, cos_x, partials);
+    launch_pdl(k_stats_partials, grid, dim3(EP_TX, EP_TY), 0, s, A, C, H, W, sin_y, cos_y, sin_x, cos_x, partials);
     return cudaGetLastError();
 }
 
@@ -1082,6 +1083,7 @@ cudaError_t launch_stats_partials(const float* A, int C, int H, int W, const flo
 __global__ void __launch_bounds__(1024) k_stats_final(const double* partials, int n_blocks, int C,
                                                       int H, int W, float* out)
 {
+    pdl_enter();
     __shared__ double part[32];
     __shared__ double tot[kMaxChannels * 5];
     const int nv = C * 5;
@@ -1116,7 +1118,7 @@ __global__ void __launch_bounds__(1024) k_stats_final(const double* partials, in
 cudaError_t launch_stats_final(const double* partials, int n_blocks, int C, int H, int W,
                                float* out, cudaStream_t s)
 {
-    k_stats_final<<<1, 1024, 0, s>>>(partials, n_blocks, C, H, W, out);
+    launch_pdl(k_stats_final, 1, 1024, 0, s, partials, n_blocks, C, H, W, out);
     return cudaGetLastError();
 }
 
