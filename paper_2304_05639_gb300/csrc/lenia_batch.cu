@@ -16,6 +16,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <tuple>
 #include <vector>
@@ -204,24 +205,33 @@ lenia_status tune_epilogue(Group& g, cudaStream_t s)
         cudaEventDestroy(e0);
         return LENIA_ECUDA;
     }
+    // each candidate timed in three rounds of five launches (rounds interleaved
+    // over the candidates), its best round kept: single rounds of candidates
+    // within ~20% of each other ordered them differently from run to run
+    std::vector<float> t_best(cands.size(), INFINITY);
+    for (int round = 0; round < 3; round++) {
+        for (size_t ci = 0; ci < cands.size(); ci++) {
+            Group t = g;
+            t.epi = cands[ci].epi;
+            t.br = cands[ci].br;
+            t.bands = cands[ci].bands;
+            bool ok = true;
+            for (int r = 0; ok && r < 2; r++) ok = group_epilogue(t, 0, s) == cudaSuccess;     // warm-up
+            ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+            for (int r = 0; ok && r < 5; r++) ok = group_epilogue(t, 0, s) == cudaSuccess;
+            ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+            float ms = INFINITY;
+            if (ok) cudaEventElapsedTime(&ms, e0, e1);
+            else (void)cudaGetLastError();
+            t_best[ci] = std::min(t_best[ci], ms);
+        }
+    }
     float best = INFINITY;
     Cand pick = {0, 2, 1};
     for (size_t ci = 0; ci < cands.size(); ci++) {
-        Group t = g;
-        t.epi = cands[ci].epi;
-        t.br = cands[ci].br;
-        t.bands = cands[ci].bands;
-        bool ok = true;
-        for (int r = 0; ok && r < 2; r++) ok = group_epilogue(t, 0, s) == cudaSuccess;     // warm-up
-        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
-        for (int r = 0; ok && r < 5; r++) ok = group_epilogue(t, 0, s) == cudaSuccess;
-        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
-        float ms = INFINITY;
-        if (ok) cudaEventElapsedTime(&ms, e0, e1);
-        else (void)cudaGetLastError();
-        if (ci < 8) g.tune_ms[ci] = ms / 5;
-        if (ms < best) {
-            best = ms;
+        if (ci < 8) g.tune_ms[ci] = t_best[ci] / 5;
+        if (t_best[ci] < best) {
+            best = t_best[ci];
             pick = cands[ci];
         }
     }
