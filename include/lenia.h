@@ -416,7 +416,8 @@ LENIA_API lenia_status lenia_batch_rollout(lenia_batch* batch, float* const* A, 
  * planes or grid z), or -1 when it steps on its own (or w is out of range).
  * A grouped world's epilogue is the tiled kernel (FP32 division and expf),
  * which can differ in the last bits from the streaming kernel a world of
- * width 256 k would use on its own. */
+ * width 256 k uses on its own when that kernel is chosen (steps with
+ * statistics, several kernels or channels). */
 LENIA_API int32_t lenia_batch_group_of(const lenia_batch* batch, int32_t world);
 /* Epilogue shape of world w's group: 0 = the tiled kernel, *param = rows per
  * thread (1, 2 or 4); 2 = the tiled kernel with four adjacent columns per

@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(256) k_epilogue_batch11(EpiParams p)
 // scalar loads), so a thread issues 12 loads for four sites instead of 48.
 // A block of 32 x 8 threads covers 128 columns x 8 BR rows.  Needs
 // W % 128 == 0 and H % (8 BR) == 0; results are those of k_epilogue_batch11.
-template <int LOC, int BR>
+template <int LOC, int BR, bool LISTS = true>
 __global__ void __launch_bounds__(256) k_epilogue_batch11v(EpiParams p)
 {
     pdl_enter();
@@ -850,10 +850,11 @@ __global__ void __launch_bounds__(256) k_epilogue_batch11v(EpiParams p)
     const int xp = x + 4 == W ? 0 : x + 4;
     const float eps_p = p.eps_p, eps_u = p.eps_u;
     const int wz = blockIdx.z;
-    const float* pA = p.A_list[wz];
-    const float* pP = p.P_list ? p.P_list[wz] : nullptr;
-    float* pAo = p.Aout_list[wz];
-    float* pPo = p.Pout_list ? p.Pout_list[wz] : nullptr;
+    // LISTS: world blockIdx.z of a batched launch; else the single world
+    const float* pA = LISTS ? p.A_list[wz] : p.A;
+    const float* pP = LISTS ? (p.P_list ? p.P_list[wz] : nullptr) : p.P;
+    float* pAo = LISTS ? p.Aout_list[wz] : p.A_out;
+    float* pPo = LISTS ? (p.Pout_list ? p.Pout_list[wz] : nullptr) : p.P_out;
     const float* pU = p.U + (size_t)wz * p.u_stride;
 
     float4 up[BR][NP > 0 ? NP : 1], ce[BR][NP > 0 ? NP : 1], dn[BR][NP > 0 ? NP : 1];
@@ -954,11 +955,19 @@ cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t
     const int loc = (p.p_mu >= 0 ? 1 : 0) | (p.p_sigma >= 0 ? 2 : 0) | (p.p_h >= 0 ? 4 : 0);
     const int K = p.kt.K;
     if (p.partials || p.alpha_out || p.empty_out) return cudaErrorInvalidValue;
+    // the batched forms read every world's buffers through the lists; a single
+    // world (null lists) takes the four-column form or the one-row-per-thread kernel
+    const bool lists = p.A_list && p.Aout_list && (p.n_p == 0 || (p.P_list && p.Pout_list));
     dim3 block(EP_TX, EP_TY);
     // br < 0: four columns per thread, |br| rows (float4 form; widths of 128 k)
     if ((br == -1 || br == -2) && K == 1 && p.W % (4 * EP_TX) == 0 && p.H % (EP_TY * -br) == 0) {
         dim3 g4(p.W / (4 * EP_TX), p.H / (EP_TY * -br), n_worlds);
-        if (br == -1) {
+        if (br == -1 && !lists) {           // one world, its own buffers
+            if (loc == 3) launch_pdl(k_epilogue_batch11v<3, 1, false>, g4, block, 0, s, p);
+            else launch_pdl(k_epilogue_batch11v<0, 1, false>, g4, block, 0, s, p);
+        } else if (!lists) {
+            return cudaErrorInvalidValue;
+        } else if (br == -1) {
             if (loc == 3) launch_pdl(k_epilogue_batch11v<3, 1>, g4, block, 0, s, p);
             else launch_pdl(k_epilogue_batch11v<0, 1>, g4, block, 0, s, p);
         } else {
@@ -968,7 +977,7 @@ cudaError_t launch_epilogue_batch(const EpiParams& p, int n_worlds, cudaStream_t
         return cudaGetLastError();
     }
     if (br != 1 && br != 2 && br != 4) br = 2;
-    if (K == 1 && p.W % EP_TX == 0 && p.H % (EP_TY * br) == 0) {
+    if (lists && K == 1 && p.W % EP_TX == 0 && p.H % (EP_TY * br) == 0) {
         dim3 g4(p.W / EP_TX, p.H / (EP_TY * br), n_worlds);
         if (br == 1) {
             if (loc == 3) launch_pdl(k_epilogue_batch11<3, 1>, g4, block, 0, s, p);
