@@ -157,7 +157,10 @@ LENIA_API lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_de
  * localized != 0, P_in [n_p][K][H][W]; writes A_out and P_out (P_out may be
  * NULL only when localized == 0).  stats_out (nullable, device, C*3 floats)
  * receives mass, circular-mean centre y and centre x of each channel of
- * A_out.  In and out buffers must not overlap (EINVAL). */
+ * A_out.  In and out buffers must not overlap (EINVAL).  One-channel,
+ * one-kernel worlds whose width is a multiple of 128 take the tiled update
+ * kernel when stats_out is NULL and the streaming one otherwise; the two
+ * agree to FP32 rounding, not bit for bit. */
 LENIA_API lenia_status lenia_step(lenia_ctx* ctx, const float* A_in, const float* P_in,
                         float* A_out, float* P_out, float* stats_out, void* stream);
 
