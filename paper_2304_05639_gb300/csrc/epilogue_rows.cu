@@ -171,6 +171,8 @@ __device__ __forceinline__ void er_band(const EpiParams& p, const CUtensorMap* t
                 break;
             }
             const int y = r0 + i;
+            // the row's trigonometric weights, fetched before the row's arithmetic
+            const float sy = stats ? __ldg(&p.sin_y[y]) : 0.f, cy = stats ? __ldg(&p.cos_y[y]) : 0.f;
             const float* Pu = Pring + (size_t)(i % NPD) * L::p_slot;
             float* Pcw = Pring + (size_t)((i + 1) % NPD) * L::p_slot;
             const float* Pc = Pcw;
@@ -231,16 +233,15 @@ __device__ __forceinline__ void er_band(const EpiParams& p, const CUtensorMap* t
             }
             const bool alpha = !p.maintain || ((NPK == 0 || pmin > eps_p) && tmin > eps_u);
             const unsigned gi = (unsigned)y * (unsigned)W + (unsigned)x;
-            const float sy = stats ? __ldg(&p.sin_y[y]) : 0.f, cy = stats ? __ldg(&p.cos_y[y]) : 0.f;
 #pragma unroll
             for (int c = 0; c < CT; c++) {
                 const float an = __saturatef(Ar[c * ER_CH + t] + p.dt * (alpha ? acc[c] : p.acc0[c]));
                 A_out[(unsigned)c * N + gi] = an;
+                // the column's weights (sin, cos of x) are applied to the
+                // column's mass once, at the end of the band
                 st[c * 5 + 0] += an;
                 st[c * 5 + 1] += an * sy;
                 st[c * 5 + 2] += an * cy;
-                st[c * 5 + 3] += an * sx;
-                st[c * 5 + 4] += an * cx;
             }
             if (p.alpha_out) p.alpha_out[gi] = alpha ? 1 : 0;
             if (p.empty_out) p.empty_out[gi] = tsum > eps_u ? 0 : 1;
@@ -258,6 +259,12 @@ __device__ __forceinline__ void er_band(const EpiParams& p, const CUtensorMap* t
                 }
                 mbar_arrive(&empty_u[i % NUD]);
             }
+        }
+        // sum A sin(2 pi x / W), sum A cos(2 pi x / W) of this column's rows
+#pragma unroll
+        for (int c = 0; c < CT; c++) {
+            st[c * 5 + 3] = st[c * 5 + 0] * sx;
+            st[c * 5 + 4] = st[c * 5 + 0] * cx;
         }
     }
 }
@@ -371,44 +378,48 @@ __global__ void __launch_bounds__(ER_THREADS, 1)
             }
         }
         __syncthreads();
-        if (tid < CT * 5) {
-            double s = 0.0;
-            for (int w = 0; w < ER_CONSUMERS; w++) s += (double)red[w][tid];
-            p.partials[(size_t)blockIdx.x * CT * 5 + tid] = s;
+        // The producer warp writes the block's record: it has no global
+        // stores of its own in flight, so its fence waits only for the record
+        // (the consumers' streaming stores drain meanwhile, unfenced).
+        const bool writer = warp == ER_CONSUMERS && lane < CT * 5;
+        if (writer) {
+            float2 s = make_float2(0.f, 0.f);
+            for (int w = 0; w < ER_CONSUMERS; w++) s = ff_add(s, make_float2(red[w][lane], 0.f));
+            p.partials[(size_t)blockIdx.x * CT * 5 + lane] = s;
         }
         if (p.stats_out) {
             // The last block to finish reduces every block's record in block
             // order (deterministic) and re-arms the ticket for the next launch.
+            // Each record writer fences, the block meets, then one writer
+            // takes the ticket.
             __shared__ unsigned int ticket;
-            __threadfence();
+            if (writer) __threadfence();
             __syncthreads();
-            if (tid == 0) ticket = atomicAdd(p.ticket, 1u);
+            if (warp == ER_CONSUMERS && lane == 0) ticket = atomicAdd(p.ticket, 1u);
             __syncthreads();
             if (ticket == gridDim.x - 1) {
                 __threadfence();
-                __shared__ double tot[CT * 5];
+                __shared__ float2 tot[CT * 5];
                 // one warp per sum: lanes stride over the block records, then a
-                // fixed shuffle tree (deterministic)
+                // fixed shuffle tree (deterministic; compensated FP32 pairs)
                 if (warp < CT * 5) {
-                    double s = 0.0;
-                    for (unsigned b = lane; b < gridDim.x; b += 32)
-                        s += __ldcg(&p.partials[(size_t)b * CT * 5 + warp]);
+                    float2 s = make_float2(0.f, 0.f);
+                    for (unsigned b = lane; b < gridDim.x; b += 32 * 4) {
+                        // four records in flight per lane, added in block order
+                        float2 r[4];
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+                        for (int u = 0; u < 4; u++)
+                            r[u] = b + 32 * u < gridDim.x ? __ldcg(&p.partials[(size_t)(b + 32 * u) * CT * 5 + warp])
+                                                          : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < 4; u++) s = ff_add(s, r[u]);
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) s = ff_add(s, ff_shfl_down(s, off));
                     if (lane == 0) tot[warp] = s;
                 }
                 __syncthreads();
-                if (tid < CT) {
-                    const int c = tid;
-                    const double two_pi = 6.283185307179586476925286766559;
-                    double ty = atan2(tot[c * 5 + 1], tot[c * 5 + 2]) * H / two_pi;
-                    double tx = atan2(tot[c * 5 + 3], tot[c * 5 + 4]) * p.W / two_pi;
-                    if (ty < 0.0) ty += H;
-                    if (tx < 0.0) tx += p.W;
-                    p.stats_out[c * 3 + 0] = (float)tot[c * 5 + 0];
-                    p.stats_out[c * 3 + 1] = (float)ty;
-                    p.stats_out[c * 3 + 2] = (float)tx;
-                }
+                if (tid < 2 * CT) stats_centre(tot, tid >> 1, tid & 1, H, p.W, p.stats_out);
                 if (tid == 0) *p.ticket = 0u;
             }
         }

@@ -59,7 +59,7 @@ struct lenia_ctx {
     float2* d_Ahat = nullptr;
     float2* d_Uhat = nullptr;
     float* d_U = nullptr;
-    double* d_partials = nullptr;
+    float2* d_partials = nullptr;
     float* d_trig = nullptr;               // sin_y, cos_y, sin_x, cos_x
     float* d_A2 = nullptr;
     float* d_P2 = nullptr;

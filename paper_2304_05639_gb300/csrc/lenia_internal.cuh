@@ -66,6 +66,45 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Compensated FP32 sums for the statistics' block records and their final
+// reduction.  A value is the unevaluated pair hi + lo; each addition keeps
+// its rounding error with Knuth's two-sum (exact in round-to-nearest) and
+// renormalises, so a fixed-order sum of pairs is deterministic and accurate
+// to about 2^-44 of the summed magnitudes, on the FP32 pipe (FP64
+// arithmetic runs at a small fraction of the FP32 rate on sm_103).
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float bv = s - a.x;
+    const float e = (a.x - (s - bv)) + (b.x - bv);
+    const float t = e + (a.y + b.y);
+    const float hi = s + t;
+    return make_float2(hi, t - (hi - s));
+}
+
+__device__ __forceinline__ float2 ff_shfl_down(float2 v, int off)
+{
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, off), __shfl_down_sync(0xffffffffu, v.y, off));
+}
+
+// One channel's outputs from its five reduced sums tot[c * 5 + (M, S_y,
+// C_y, S_x, C_x)]: axis 0 (y) also writes the mass; each axis writes the
+// circular-mean centre atan2(S, C) n / (2 pi) wrapped to [0, n), in FP64 on
+// the pairs' values.  One thread per (channel, axis), so that the two
+// arctangents of a channel run side by side.
+__device__ __forceinline__ void stats_centre(const float2* tot, int c, int axis, int H, int W, float* out)
+{
+    constexpr double kInv2Pi = 0.15915494309189533576888376337251;
+    const float2* t = tot + c * 5;
+    const int n = axis ? W : H;
+    const double s = (double)t[1 + 2 * axis].x + (double)t[1 + 2 * axis].y;
+    const double co = (double)t[2 + 2 * axis].x + (double)t[2 + 2 * axis].y;
+    double centre = atan2(s, co) * ((double)n * kInv2Pi);
+    if (centre < 0.0) centre += n;
+    out[c * 3 + 1 + axis] = (float)centre;
+    if (axis == 0) out[c * 3] = t[0].x + t[0].y;
+}
+
 // Per-kernel scalars, passed by value to the kernels that need them.
 struct KernelTable {
     int K, C;
@@ -82,7 +121,7 @@ struct EpiParams {
     float* P_out;
     uint8_t* alpha_out;
     uint8_t* empty_out;        // 1 where sum_k t_k <= eps_u (not Delta_sum(U)), or null
-    double* partials;          // [n_blocks][C][5] or null
+    float2* partials;          // [n_blocks][C][5] compensated (hi, lo) sums, or null
     float* stats_out;          // [C][3]; when set, the last block reduces the partials (streaming kernel)
     unsigned int* ticket;      // completion counter for that reduction (0 between launches)
     const float* sin_y;
@@ -250,8 +289,8 @@ cudaError_t launch_fft_rows_c2r(const FftParams& p, cudaStream_t s);
 cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks);
 cudaError_t launch_stats_partials(const float* A, int C, int H, int W, const float* sin_y,
                                   const float* cos_y, const float* sin_x, const float* cos_x,
-                                  double* partials, cudaStream_t s, int* n_blocks);
-cudaError_t launch_stats_final(const double* partials, int n_blocks, int C, int H, int W,
+                                  float2* partials, cudaStream_t s, int* n_blocks);
+cudaError_t launch_stats_final(const float2* partials, int n_blocks, int C, int H, int W,
                                float* out, cudaStream_t s);
 cudaError_t launch_spectra(const double* Kd, int R, int H, int W, const double* cos_H,
                            const double* cos_W, double* T_scratch, float* S_out, cudaStream_t s);

@@ -15,12 +15,13 @@ using namespace lenia;
 namespace {
 
 // Limits of the static scratch: (stats blocks x channels) partial records of
-// five doubles, and sine/cosine tables for H, W <= 8192.
+// five compensated (hi, lo) FP32 pairs, 8 bytes each, and sine/cosine tables
+// for H, W <= 8192; the array is declared in 8-byte slots.
 constexpr int kNoAllocMaxRecords = 65536;
 constexpr int kNoAllocMaxSide = 8192;
-constexpr size_t kPartialDoubles = (size_t)kNoAllocMaxRecords * 5;
+constexpr size_t kPartialSlots = (size_t)kNoAllocMaxRecords * 5;
 constexpr size_t kTrigFloats = 4 * (size_t)kNoAllocMaxSide;
-constexpr size_t kScratchDoubles = kPartialDoubles + kTrigFloats / 2;   // 2.75 MB
+constexpr size_t kScratchDoubles = kPartialSlots + kTrigFloats / 2;   // 2.75 MB
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
@@ -106,8 +107,8 @@ extern "C" lenia_status lenia_stats_noalloc(const float* A, int32_t n_channels, 
         fprintf(stderr, "lenia_stats_noalloc: scratch address lookup: %s\n", cudaGetErrorString(e));
         return LENIA_ECUDA;
     }
-    double* partials = (double*)base;
-    float* trig = (float*)(partials + kPartialDoubles);
+    float2* partials = (float2*)base;
+    float* trig = (float*)(partials + kPartialSlots);
     const int H = height, W = width, C = n_channels;
     k_noalloc_trig<<<(H + W + 255) / 256, 256, 0, s>>>(trig, H, W);
     e = cudaGetLastError();

@@ -226,9 +226,10 @@ constexpr int EP_TX = 32, EP_TY = 8, EP_RY = 4;    // block: 32 x 8 threads, 4 r
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // Block reduction of per-thread stats (CA channels x 5 sums) into one record
-// per block; every thread of the block must call it.
+// per block (compensated pairs, warp order); every thread of the block must
+// call it.
 template <int CA>
-__device__ __forceinline__ void block_stats(const float* st, int C, double* partials)
+__device__ __forceinline__ void block_stats(const float* st, int C, float2* partials)
 {
     __shared__ float red[EP_TY][kMaxChannels * 5];
     const int lane = threadIdx.x;
@@ -243,8 +244,8 @@ __device__ __forceinline__ void block_stats(const float* st, int C, double* part
     __syncthreads();
     const int tid = threadIdx.y * EP_TX + threadIdx.x;
     if (tid < C * 5) {
-        double s = 0.0;
-        for (int w = 0; w < EP_TY; w++) s += (double)red[w][tid];
+        float2 s = make_float2(0.f, 0.f);
+        for (int w = 0; w < EP_TY; w++) s = ff_add(s, make_float2(red[w][tid], 0.f));
         const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
         partials[blk * C * 5 + tid] = s;
     }
@@ -1052,7 +1053,7 @@ cudaError_t launch_epilogue(const EpiParams& p, cudaStream_t s, int* n_blocks)
 __global__ void __launch_bounds__(256) k_stats_partials(const float* A, int C, int H, int W,
                                                         const float* sin_y, const float* cos_y,
                                                         const float* sin_x, const float* cos_x,
-                                                        double* partials)
+                                                        float2* partials)
 {
     pdl_enter();
     const int x = blockIdx.x * EP_TX + threadIdx.x;
@@ -1077,7 +1078,7 @@ __global__ void __launch_bounds__(256) k_stats_partials(const float* A, int C, i
 
 cudaError_t launch_stats_partials(const float* A, int C, int H, int W, const float* sin_y,
                                   const float* cos_y, const float* sin_x, const float* cos_x,
-                                  double* partials, cudaStream_t s, int* n_blocks)
+                                  float2* partials, cudaStream_t s, int* n_blocks)
 {
     dim3 grid((W + EP_TX - 1) / EP_TX, (H + EP_TY * EP_RY - 1) / (EP_TY * EP_RY));
     if (n_blocks) *n_blocks = grid.x * grid.y;
@@ -1086,45 +1087,43 @@ cudaError_t launch_stats_partials(const float* A, int C, int H, int W, const flo
 }
 
 // Final reduction, one block of 1024 threads: for each of the C*5 sums,
-// 64 threads stride over the block records in FP64 (fixed order), then two
-// fixed shuffle trees and one add.  out[c] = (mass, centre y, centre x),
-// centres from the circular mean atan2(sum A sin, sum A cos) scaled to [0, n).
-__global__ void __launch_bounds__(1024) k_stats_final(const double* partials, int n_blocks, int C,
+// 64 threads stride over the block records (fixed order), then two fixed
+// shuffle trees and one add, all in compensated FP32 pairs.  out[c] = (mass,
+// centre y, centre x), centres from the circular mean atan2(sum A sin, sum A
+// cos) scaled to [0, n) (FP64, on the pairs' values).
+__global__ void __launch_bounds__(1024) k_stats_final(const float2* partials, int n_blocks, int C,
                                                       int H, int W, float* out)
 {
     pdl_enter();
-    __shared__ double part[32];
-    __shared__ double tot[kMaxChannels * 5];
+    __shared__ float2 part[32];
+    __shared__ float2 tot[kMaxChannels * 5];
     const int nv = C * 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int v0 = 0; v0 < nv; v0 += 16) {
         const int v = v0 + (threadIdx.x >> 6);     // 16 values per pass, 64 threads each
         const int stripe = threadIdx.x & 63;
-        double s = 0.0;
+        float2 s = make_float2(0.f, 0.f);
         if (v < nv)
-            for (int b = stripe; b < n_blocks; b += 64) s += partials[(size_t)b * nv + v];
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+            for (int b = stripe; b < n_blocks; b += 64 * 8) {
+                // eight records in flight per thread, added in block order
+                float2 x[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+                    x[u] = b + 64 * u < n_blocks ? partials[(size_t)(b + 64 * u) * nv + v] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 8; u++) s = ff_add(s, x[u]);
+            }
+        for (int off = 16; off > 0; off >>= 1) s = ff_add(s, ff_shfl_down(s, off));
         if (lane == 0) part[warp] = s;
         __syncthreads();
         if (threadIdx.x < 16 && v0 + threadIdx.x < nv)
-            tot[v0 + threadIdx.x] = part[2 * threadIdx.x] + part[2 * threadIdx.x + 1];
+            tot[v0 + threadIdx.x] = ff_add(part[2 * threadIdx.x], part[2 * threadIdx.x + 1]);
         __syncthreads();
     }
-    if (threadIdx.x < C) {
-        const int c = threadIdx.x;
-        const double two_pi = 6.283185307179586476925286766559;
-        const double m = tot[c * 5 + 0];
-        double ty = atan2(tot[c * 5 + 1], tot[c * 5 + 2]) * H / two_pi;
-        double tx = atan2(tot[c * 5 + 3], tot[c * 5 + 4]) * W / two_pi;
-        if (ty < 0.0) ty += H;
-        if (tx < 0.0) tx += W;
-        out[c * 3 + 0] = (float)m;
-        out[c * 3 + 1] = (float)ty;
-        out[c * 3 + 2] = (float)tx;
-    }
+    if (threadIdx.x < 2 * C) stats_centre(tot, threadIdx.x >> 1, threadIdx.x & 1, H, W, out);
 }
 
-cudaError_t launch_stats_final(const double* partials, int n_blocks, int C, int H, int W,
+cudaError_t launch_stats_final(const float2* partials, int n_blocks, int C, int H, int W,
                                float* out, cudaStream_t s)
 {
     launch_pdl(k_stats_final, 1, 1024, 0, s, partials, n_blocks, C, H, W, out);
