@@ -9,8 +9,8 @@
 //   dL/dmu_k    = sum gpre dt h_k F' g (U - mu) / sigma^2
 //   dL/dsigma_k = sum gpre dt h_k F' g (U - mu)^2 / sigma^3
 //   dL/dh_k     = sum gpre dt F(g)
-// as FP64 block partials, reduced in a fixed order by a second small kernel
-// (one block per value).  The transposed convolution (gA_src += K~_k (x) gU_k; K~ is
+// as block partials in compensated FP32 pairs (hi + lo), reduced in a fixed
+// order by a second small kernel (one block per value).  The transposed convolution (gA_src += K~_k (x) gU_k; K~ is
 // point symmetric, so it is the same convolution) runs on the forward
 // machinery; its inverse row pass adds gpre (FFT path) or k_adjoint_gather
 // adds it (direct path).
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint_epilogue(AdjParams p)
     __syncthreads();
     // value-major partials [K * 3][blocks]: the reduction kernel reads them coalesced
     for (int v = threadIdx.x; v < K * 3; v += ADJ_THREADS) {
-        double s = 0.0;
-        for (int w = 0; w < ADJ_THREADS / 32; w++) s += (double)red[w][v];
+        float2 s = make_float2(0.f, 0.f);
+        for (int w = 0; w < ADJ_THREADS / 32; w++) s = ff_add(s, make_float2(red[w][v], 0.f));
         p.gene_partials[(size_t)v * gridDim.x + blockIdx.x] = s;
     }
 }
@@ -92,29 +92,29 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint_epilogue(AdjParams p)
 // sums blocks t, t + 256, ... in order, then a fixed shuffle / shared tree,
 // so every launch adds in the same order.
 constexpr int ADJ_RED_THREADS = 256;
-__global__ void __launch_bounds__(ADJ_RED_THREADS) k_adjoint_gene_reduce(const double* partials, int nb,
-                                                                      double* gene_acc)
+__global__ void __launch_bounds__(ADJ_RED_THREADS) k_adjoint_gene_reduce(const float2* partials, int nb,
+                                                                      float2* gene_acc)
 {
     pdl_enter();
-    __shared__ double wsum[ADJ_RED_THREADS / 32];
+    __shared__ float2 wsum[ADJ_RED_THREADS / 32];
     const int v = blockIdx.x;
-    const double* src = partials + (size_t)v * nb;
-    double s0 = 0.0, s1 = 0.0;
+    const float2* src = partials + (size_t)v * nb;
+    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
     int b = threadIdx.x;
     for (; b + ADJ_RED_THREADS < nb; b += 2 * ADJ_RED_THREADS) {
-        s0 += src[b];
-        s1 += src[b + ADJ_RED_THREADS];
+        s0 = ff_add(s0, src[b]);
+        s1 = ff_add(s1, src[b + ADJ_RED_THREADS]);
     }
-    if (b < nb) s0 += src[b];
-    double s = s0 + s1;
+    if (b < nb) s0 = ff_add(s0, src[b]);
+    float2 s = ff_add(s0, s1);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    for (int off = 16; off > 0; off >>= 1) s = ff_add(s, ff_shfl_down(s, off));
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < ADJ_RED_THREADS / 32; w++) t += wsum[w];
-        gene_acc[v] += t;
+        float2 t = make_float2(0.f, 0.f);
+        for (int w = 0; w < ADJ_RED_THREADS / 32; w++) t = ff_add(t, wsum[w]);
+        gene_acc[v] = ff_add(gene_acc[v], t);
     }
 }
 
@@ -138,11 +138,11 @@ __global__ void __launch_bounds__(256) k_adjoint_gather(AdjParams p)
     }
 }
 
-__global__ void k_adjoint_gene_out(const double* gene_acc, int nv, float* out)
+__global__ void k_adjoint_gene_out(const float2* gene_acc, int nv, float* out)
 {
     pdl_enter();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < nv) out[v] = (float)gene_acc[v];
+    if (v < nv) out[v] = gene_acc[v].x + gene_acc[v].y;
 }
 
 int adjoint_blocks(int H, int W) { return (int)(((size_t)H * W + ADJ_THREADS - 1) / ADJ_THREADS); }
@@ -164,7 +164,7 @@ cudaError_t launch_adjoint_gather(const AdjParams& p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_gene_out(const double* gene_acc, int nv, float* out, cudaStream_t s)
+cudaError_t launch_adjoint_gene_out(const float2* gene_acc, int nv, float* out, cudaStream_t s)
 {
     launch_pdl(k_adjoint_gene_out, (nv + 63) / 64, 64, 0, s, gene_acc, nv, out);
     return cudaGetLastError();

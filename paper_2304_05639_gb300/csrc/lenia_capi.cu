@@ -84,8 +84,8 @@ struct lenia_ctx {
     float* d_gpre = nullptr;
     float* d_gU = nullptr;
     float* d_V = nullptr;
-    double* d_gene_part = nullptr;
-    double* d_gene_acc = nullptr;
+    float2* d_gene_part = nullptr;    // compensated FP32 (hi, lo) pairs
+    float2* d_gene_acc = nullptr;
     float2* d_Ahat_t = nullptr;            // spectra of the K gradient planes (transposed conv)
     float2* d_Uhat_t = nullptr;
     // evolutionary operators (lenia_set_walls, lenia_step_evolve)
@@ -1156,7 +1156,8 @@ lenia_status lenia_rollout(lenia_ctx* c, float* A, float* P, int32_t n_steps, fl
 // copies for given arguments: no host decision depends on device data).
 // Reads A_0 from the first checkpoint slot and dL/dA_T from d_gA[0]; leaves
 // dL/dA_0 in d_gA[n_steps % 2] (one buffer swap per reversed step) and the
-// FP64 gene gradients in d_gene_acc, so that it touches library buffers only.
+// gene gradients in d_gene_acc (compensated FP32 pairs), so that it touches
+// library buffers only.
 static lenia_status backward_body(lenia_ctx* c, int32_t n_steps, cudaStream_t s)
 {
     const int C = c->cfg.n_channels, K = c->cfg.n_kernels, L = c->ckpt;
@@ -1175,7 +1176,7 @@ static lenia_status backward_body(lenia_ctx* c, int32_t n_steps, cudaStream_t s)
                 st = step_impl(c, ckpt(t), nullptr, ckpt(t + 1), nullptr, nullptr, nullptr, uall(t), s);
             if (st != LENIA_OK) return st;
         }
-        CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_gene_acc, 0, (size_t)K * 3 * sizeof(double), s));
+        CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_gene_acc, 0, (size_t)K * 3 * sizeof(float2), s));
         int cur = 0;
         for (int t = n_steps - 1; t >= 0; t--) {
             AdjParams ap;
@@ -1212,7 +1213,7 @@ static lenia_status backward_body(lenia_ctx* c, int32_t n_steps, cudaStream_t s)
     // backward, segment by segment from the last: recompute the segment's
     // states and their potentials from its checkpoint, then apply the step
     // adjoint in reverse
-    CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_gene_acc, 0, (size_t)K * 3 * sizeof(double), s));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->d_gene_acc, 0, (size_t)K * 3 * sizeof(float2), s));
     auto useg = [&](int j) { return c->d_Useg + (size_t)j * K * c->N; };
     int cur = 0;
     const int n_seg = (n_steps + L - 1) / L;

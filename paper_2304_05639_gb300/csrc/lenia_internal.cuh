@@ -272,8 +272,8 @@ struct AdjParams {
     const float* V;            // K~_k (x) gU_k [K][H][W], or summed per source channel [C][H][W]
     int v_per_channel;         // 1: V holds sum_{src(k) = c} K~_k (x) gU_k per channel c
     float* gA_out;             // dL/dA_t [C][H][W]
-    double* gene_partials;     // [K][3][blocks]
-    double* gene_acc;          // [K][3]: d/dmu, d/dsigma, d/dh
+    float2* gene_partials;     // [K][3][blocks], compensated (hi, lo) sums
+    float2* gene_acc;          // [K][3]: d/dmu, d/dsigma, d/dh, compensated (hi, lo) sums
     int H, W, growth_form;
     float dt;
     KernelTable kt;
@@ -299,7 +299,7 @@ int adjoint_blocks(int H, int W);
 cudaError_t launch_adjoint_epilogue(const AdjParams& p, cudaStream_t s);
 cudaError_t measure_fp32_peak(cudaStream_t s, double* scalar_tflops, double* pair_tflops);
 cudaError_t launch_adjoint_gather(const AdjParams& p, cudaStream_t s);
-cudaError_t launch_adjoint_gene_out(const double* gene_acc, int nv, float* out, cudaStream_t s);
+cudaError_t launch_adjoint_gene_out(const float2* gene_acc, int nv, float* out, cudaStream_t s);
 bool epilogue_rows_supported(const EpiParams& p);
 // The streaming epilogue over the worlds of a batched group (one persistent
 // launch; work items taken from a device queue): one world's tensor maps and

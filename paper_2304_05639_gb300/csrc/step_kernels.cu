@@ -558,10 +558,11 @@ __device__ __forceinline__ void ring_bump(float c, float w, float b, const float
 constexpr int RG_TY = 8;     // rows per block of the ring epilogue (one site per thread)
 constexpr int RG_TILE_W = EP_TX + 2, RG_TILE_H = RG_TY + 2;
 
-// Four blocks per SM (64 registers): at five the kernel spills (0.43 ms on the
-// paper's configuration against 0.36), at three it loses latency hiding (0.375).
+// Three blocks per SM (72 registers): 0.2585 ms on the paper's configuration
+// against 0.2613 at four blocks (64 registers) and 0.2592 at two (80); gene
+// tiles three buffers deep (two kernels ahead) measured 0.2608.
 template <int KT, int CT, int NR, int LOC>
-__global__ void __launch_bounds__(256, 4) k_epilogue_rings(EpiParams p)
+__global__ void __launch_bounds__(256, 3) k_epilogue_rings(EpiParams p)
 {
     pdl_enter();
     constexpr int NG = ((LOC & 1) != 0) + ((LOC & 2) != 0) + ((LOC & 4) != 0);
