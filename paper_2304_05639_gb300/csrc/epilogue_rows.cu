@@ -198,38 +198,91 @@ __device__ __forceinline__ void er_band(const EpiParams& p, const CUtensorMap* t
             for (int c = 0; c < CT; c++) acc[c] = 0.f;
 #pragma unroll
             for (int k = 0; k < KT; k++) {
-#pragma unroll
-                for (int pp = 0; pp < NP; pp++) {
-                    const int o = (pp * KT + k) * ER_PW + t + 4;
-                    float v;
+                if constexpr (NP == 2) {
+                    // the kernel's two gene planes side by side on packed FP32
+                    // pairs: the same additions and products, lane by lane
+                    const int o0 = k * ER_PW + t + 4, o1 = (KT + k) * ER_PW + t + 4;
+                    float2 v;
                     if (p.maintain) {
                         // disk |d| <= 1 in the order (-1,0), (0,-1), (0,0), (0,1), (1,0)
-                        const float v0 = Pu[o], v1 = Pc[o - 1], v2 = Pc[o], v3 = Pc[o + 1], v4 = Pd[o];
-                        const float s = (((v0 + v1) + v2) + v3) + v4;
-                        const float n = (float)(v0 > eps_p) + (float)(v1 > eps_p) + (float)(v2 > eps_p) +
-                                        (float)(v3 > eps_p) + (float)(v4 > eps_p);
-                        v = __saturatef(s * rcp_approx(n));
-                        if (!EPS0) v = n > 0.f ? v : 0.f;
-                        pmin = fminf(pmin, v);
+                        const float2 v0 = make_float2(Pu[o0], Pu[o1]), v1 = make_float2(Pc[o0 - 1], Pc[o1 - 1]),
+                                     v2 = make_float2(Pc[o0], Pc[o1]), v3 = make_float2(Pc[o0 + 1], Pc[o1 + 1]),
+                                     v4 = make_float2(Pd[o0], Pd[o1]);
+                        const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(v0, v1), v2), v3), v4);
+                        auto ind = [&](float2 a) { return make_float2((float)(a.x > eps_p), (float)(a.y > eps_p)); };
+                        const float2 n = __fadd2_rn(
+                            __fadd2_rn(__fadd2_rn(__fadd2_rn(ind(v0), ind(v1)), ind(v2)), ind(v3)), ind(v4));
+                        const float2 q = __fmul2_rn(s, make_float2(rcp_approx(n.x), rcp_approx(n.y)));
+                        v = make_float2(__saturatef(q.x), __saturatef(q.y));
+                        if (!EPS0) v = make_float2(n.x > 0.f ? v.x : 0.f, n.y > 0.f ? v.y : 0.f);
+                        pmin = fminf(pmin, fminf(v.x, v.y));
                     } else {
-                        v = Pc[o];
+                        v = make_float2(Pc[o0], Pc[o1]);
                     }
-                    ph[pp * KT + k] = v;
+                    ph[k] = v.x;
+                    ph[KT + k] = v.y;
+                } else {
+#pragma unroll
+                    for (int pp = 0; pp < NP; pp++) {
+                        const int o = (pp * KT + k) * ER_PW + t + 4;
+                        float v;
+                        if (p.maintain) {
+                            // disk |d| <= 1 in the order (-1,0), (0,-1), (0,0), (0,1), (1,0)
+                            const float v0 = Pu[o], v1 = Pc[o - 1], v2 = Pc[o], v3 = Pc[o + 1], v4 = Pd[o];
+                            const float s = (((v0 + v1) + v2) + v3) + v4;
+                            const float n = (float)(v0 > eps_p) + (float)(v1 > eps_p) + (float)(v2 > eps_p) +
+                                            (float)(v3 > eps_p) + (float)(v4 > eps_p);
+                            v = __saturatef(s * rcp_approx(n));
+                            if (!EPS0) v = n > 0.f ? v : 0.f;
+                            pmin = fminf(pmin, v);
+                        } else {
+                            v = Pc[o];
+                        }
+                        ph[pp * KT + k] = v;
+                    }
                 }
-                const float u = Ur[k * ER_CH + t];
-                const float m = PMU >= 0 ? ph[(PMU >= 0 ? PMU : 0) * KT + k] : p.kt.mu[k];
-                const float sg = PSG >= 0 ? ph[(PSG >= 0 ? PSG : 0) * KT + k] : p.kt.sigma[k];
-                const float hh = PH >= 0 ? ph[(PH >= 0 ? PH : 0) * KT + k] : p.kt.h[k];
-                const float z = (u - m) * rcp_approx(sg);
-                const float gk = sg > 0.f ? ex2_approx(-C_HALF_LOG2E * (z * z)) : 0.f;
-                const float tk = p.alpha_on ? u : hh * gk;
-                tmin = fminf(tmin, tk);
-                tsum += tk;
-                const float G = p.growth_form == 0 ? fmaf(2.f * gk, hh, -hh) : hh * gk;
+            }
+            // growth, two kernels at a time on packed FP32 pairs (the same
+            // operations, lane by lane; sums and minima in kernel order)
+            auto gene = [&](int pl, int k, const float* bank) {
+                return pl >= 0 ? ph[(pl >= 0 ? pl : 0) * KT + k] : bank[k];
+            };
+            auto add_growth = [&](int k, float G) {
                 const int d = TOPO ? paper_dst(k) : p.kt.dst[k];
 #pragma unroll
                 for (int c = 0; c < CT; c++)
                     if (c == d) acc[c] += G;
+            };
+#pragma unroll
+            for (int k = 0; k < KT; k += 2) {
+                if (k + 1 < KT) {
+                    const float2 u = make_float2(Ur[k * ER_CH + t], Ur[(k + 1) * ER_CH + t]);
+                    const float2 m = make_float2(gene(PMU, k, p.kt.mu), gene(PMU, k + 1, p.kt.mu));
+                    const float2 sg = make_float2(gene(PSG, k, p.kt.sigma), gene(PSG, k + 1, p.kt.sigma));
+                    const float2 hh = make_float2(gene(PH, k, p.kt.h), gene(PH, k + 1, p.kt.h));
+                    const float2 z = __fmul2_rn(__fadd2_rn(u, make_float2(-m.x, -m.y)),
+                                                make_float2(rcp_approx(sg.x), rcp_approx(sg.y)));
+                    const float2 e = __fmul2_rn(make_float2(-C_HALF_LOG2E, -C_HALF_LOG2E), __fmul2_rn(z, z));
+                    const float2 gk = make_float2(sg.x > 0.f ? ex2_approx(e.x) : 0.f, sg.y > 0.f ? ex2_approx(e.y) : 0.f);
+                    const float2 tk = p.alpha_on ? u : __fmul2_rn(hh, gk);
+                    tmin = fminf(fminf(tmin, tk.x), tk.y);
+                    tsum += tk.x;
+                    tsum += tk.y;
+                    const float2 G = p.growth_form == 0
+                                         ? __ffma2_rn(__fmul2_rn(make_float2(2.f, 2.f), gk), hh, make_float2(-hh.x, -hh.y))
+                                         : __fmul2_rn(hh, gk);
+                    add_growth(k, G.x);
+                    add_growth(k + 1, G.y);
+                } else {
+                    const float u = Ur[k * ER_CH + t];
+                    const float m = gene(PMU, k, p.kt.mu), sg = gene(PSG, k, p.kt.sigma), hh = gene(PH, k, p.kt.h);
+                    const float z = (u - m) * rcp_approx(sg);
+                    const float gk = sg > 0.f ? ex2_approx(-C_HALF_LOG2E * (z * z)) : 0.f;
+                    const float tk = p.alpha_on ? u : hh * gk;
+                    tmin = fminf(tmin, tk);
+                    tsum += tk;
+                    add_growth(k, p.growth_form == 0 ? fmaf(2.f * gk, hh, -hh) : hh * gk);
+                }
             }
             const bool alpha = !p.maintain || ((NPK == 0 || pmin > eps_p) && tmin > eps_u);
             const unsigned gi = (unsigned)y * (unsigned)W + (unsigned)x;
