@@ -299,9 +299,15 @@ __device__ __forceinline__ void er_band(const EpiParams& p, const CUtensorMap* t
             if (p.alpha_out) p.alpha_out[gi] = alpha ? 1 : 0;
             if (p.empty_out) p.empty_out[gi] = tsum > eps_u ? 0 : 1;
             if (P_out) {
-                const bool keep = !p.maintain || alpha;
+                // kept genes, or zeros (one branch per site instead of a select per plane)
+                float* Po = P_out + gi;
+                if (!p.maintain || alpha) {
 #pragma unroll
-                for (int pk = 0; pk < NPK; pk++) P_out[(unsigned)pk * N + gi] = keep ? ph[pk] : 0.f;
+                    for (int pk = 0; pk < NPK; pk++) Po[(unsigned)pk * N] = ph[pk];
+                } else {
+#pragma unroll
+                    for (int pk = 0; pk < NPK; pk++) Po[(unsigned)pk * N] = 0.f;
+                }
             }
             // this warp is done with gene rows l = i, i + 1 and U/A row i
             __syncwarp();
