@@ -753,15 +753,20 @@ def run_ours(args):
     hst = outs[0][2]
     e2e_steps = max(4, min(args.steps, 20))
     e2e_s = float("nan")
+    e2e_rounds = []
     if not args.no_e2e:
         lenia.lenia_step_host(ctx, hA, hP, outs[0][0], outs[0][1], outs[0][2], stream)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(e2e_steps):
-            oA, oP, ost = outs[i % 2]
-            lenia.lenia_step_host_async(ctx, hA, hP, oA, oP, ost, stream)
-        lenia.lenia_host_wait(ctx, stream)
-        e2e_s = time.perf_counter() - t0
+        # three rounds of e2e_steps steps; the median round is reported (the
+        # host link is shared, and one slow round should not set the number)
+        for _ in range(3):
+            t0 = time.perf_counter()
+            for i in range(e2e_steps):
+                oA, oP, ost = outs[i % 2]
+                lenia.lenia_step_host_async(ctx, hA, hP, oA, oP, ost, stream)
+            lenia.lenia_host_wait(ctx, stream)
+            e2e_rounds.append(time.perf_counter() - t0)
+        e2e_s = sorted(e2e_rounds)[1]
 
     t_max, e2e_max = max_over_ranks([ms, e2e_s if e2e_s == e2e_s else 0.0], torch, dev)
     if e2e_s != e2e_s:
@@ -813,7 +818,9 @@ def run_ours(args):
                 "unit": UNIT,
                 "h2d_bytes_per_step": int(world.A.nbytes + world.P.nbytes),
                 "d2h_bytes_per_step": int(world.A.nbytes + world.P.nbytes + hst.numel() * 4),
-                "mode": "independent host worlds, lenia_step_host_async + lenia_host_wait, pinned buffers"},
+                "mode": "independent host worlds, lenia_step_host_async + lenia_host_wait, pinned buffers",
+                "rounds_ms_per_step": [r * 1e3 / e2e_steps for r in e2e_rounds],
+                "reported": "median of the rounds"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "stats_finite": ok_stats,
