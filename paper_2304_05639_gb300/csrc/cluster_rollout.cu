@@ -17,13 +17,17 @@
 // step is done: the state is read from A before the first step and written
 // back after the last.
 //
-// The convolution is a dense sum over the (2R + 1)^2 square of each kernel
-// (zero weights included, R at compile time): a thread takes a strip of 8
-// sites of one row and every eighth kernel row dy (row group g: dy + R = g,
-// g + 8, ...), keeps the strip's input window for that row (2R + 8 values) in
-// registers and adds 8 products per weight; the 8 row groups of a strip sit
-// in neighbouring lanes and meet in a reduce-scatter of shuffles, after which
-// lane g holds the potential of the strip's site g.  A warp takes four
+// The convolution sums each kernel over the disk |d| < R of its support (R
+// at compile time): a thread takes a strip of 8 sites of one row and every
+// eighth kernel row dy (row group g: dy + R = g, g + 8, ...), keeps the
+// strip's input window for that row in registers and adds 8 products per
+// weight; the 8 row groups of a strip sit in neighbouring lanes and meet in
+// a reduce-scatter of shuffles, after which lane g holds the potential of
+// the strip's site g.  The lanes of a warp take kernel rows 8j .. 8j + 7
+// together, so each pass j spans only the columns where one of those rows
+// has support (a compile-time range); the weights outside it are zero (the
+// host checks this before it picks the route), and the sums are the dense
+// sums without their zero terms.  A warp takes four
 // strips 8 columns apart and the tile's row pitch is 1 modulo 32, so its 32
 // lanes (8 consecutive rows, four strips) read 32 different banks.  (Sixteen
 // warps with 16 row groups measured the same.)
@@ -42,6 +46,57 @@ constexpr int CR_XS = 8;          // sites per strip
 constexpr int CR_G = 8;           // kernel-row groups per strip (lane bits 0..2)
 constexpr int CR_THREADS = 256;
 constexpr int CR_MIN_R = 1, CR_MAX_R = 16;
+
+// Half-width of the support of kernel row dy (|d| < R): the largest h with
+// h^2 + dy^2 < R^2, or -1 for an empty row.
+__host__ __device__ constexpr int cr_row_hw(int R, int dy)
+{
+    int h = -1;
+    while ((h + 1) * (h + 1) + dy * dy < R * R) h++;
+    return h;
+}
+
+// The widest half-width among kernel rows CR_G J .. CR_G J + CR_G - 1 (row
+// index dy + R), or -1 when none of them has support.
+__host__ __device__ constexpr int cr_group_hw(int R, int J)
+{
+    int m = -1;
+    for (int r = CR_G * J; r < CR_G * J + CR_G && r <= 2 * R; r++) {
+        const int h = cr_row_hw(R, r - R);
+        m = h > m ? h : m;
+    }
+    return m;
+}
+
+// Pass J of a lane's kernel rows: row CR_G J + g over the group's column
+// range, then the next pass.
+template <int R, int J>
+__device__ __forceinline__ void cr_row_passes(int g, const float* tk, const float* wk, int yl, int TW,
+                                              float (&acc)[CR_XS])
+{
+    constexpr int KW = 2 * R + 1;
+    if constexpr (CR_G * J < KW) {
+        constexpr int HW = cr_group_hw(R, J);
+        if constexpr (HW >= 0) {
+            constexpr int LO = R - HW, NDX = 2 * HW + 1;
+            const int dyi = CR_G * J + g;
+            if (dyi < KW) {
+                const float* trow = tk + (size_t)(yl + dyi) * TW + LO;
+                const float* wrow = wk + dyi * KW + LO;
+                float v[NDX + CR_XS - 1];
+#pragma unroll
+                for (int j = 0; j < NDX + CR_XS - 1; j++) v[j] = trow[j];
+#pragma unroll
+                for (int dx = 0; dx < NDX; dx++) {
+                    const float wv = wrow[dx];
+#pragma unroll
+                    for (int s = 0; s < CR_XS; s++) acc[s] = fmaf(wv, v[dx + s], acc[s]);
+                }
+            }
+        }
+        cr_row_passes<R, J + 1>(g, tk, wk, yl, TW, acc);
+    }
+}
 
 // Shared-memory layout (floats): own[2][C][HS][W], tile[C][TH][TW],
 // weights[K][KW][KW].  Tile column R + x holds column x of the world
@@ -134,20 +189,7 @@ __global__ void __launch_bounds__(CR_THREADS, 1) k_cluster_rollout(ClusterRollou
                 float acc[CR_XS];
 #pragma unroll
                 for (int s = 0; s < CR_XS; s++) acc[s] = 0.f;
-#pragma unroll 1
-                for (int dyi = g; dyi < KW; dyi += CR_G) {       // kernel row dyi (dy = dyi - R)
-                    const float* trow = tk + (size_t)(yl + dyi) * TW;
-                    const float* wrow = wk + dyi * KW;
-                    float v[KW + CR_XS - 1];
-#pragma unroll
-                    for (int j = 0; j < KW + CR_XS - 1; j++) v[j] = trow[j];
-#pragma unroll
-                    for (int dx = 0; dx < KW; dx++) {
-                        const float wv = wrow[dx];
-#pragma unroll
-                        for (int s = 0; s < CR_XS; s++) acc[s] = fmaf(wv, v[dx + s], acc[s]);
-                    }
-                }
+                cr_row_passes<R, 0>(g, tk, wk, yl, TW, acc);     // kernel rows g, g + 8, ... (dy = row - R)
                 // reduce-scatter over the 8 row groups: lane g ends with site x0 + g
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
@@ -232,6 +274,20 @@ cudaError_t cr_prepare(CrKernel fn, size_t smem)
 }
 
 }  // namespace
+
+bool cluster_rollout_weights_fit(const float* w, int K, int maxR)
+{
+    const int KW = 2 * maxR + 1;
+    for (int k = 0; k < K; k++)
+        for (int r = 0; r < KW; r++) {
+            const int hw = cr_group_hw(maxR, r / CR_G);
+            for (int dx = 0; dx < KW; dx++) {
+                const int off = dx - maxR < 0 ? maxR - dx : dx - maxR;
+                if (off > hw && w[((size_t)k * KW + r) * KW + dx] != 0.f) return false;
+            }
+        }
+    return true;
+}
 
 size_t cluster_rollout_smem(int H, int W, int C, int K, int maxR, int Q)
 {

@@ -810,8 +810,12 @@ lenia_status lenia_init(const lenia_config* cfg, const lenia_kernel_desc* kernel
                     for (int dx = 0; dx < n; dx++)
                         dense[((size_t)k * KW + dy + o) * KW + dx + o] = (float)c->conv_w[k][(size_t)dy * n + dx];
             }
-            ALLOC(c->d_cr_w, dense.size());
-            CK_INIT(cudaMemcpy(c->d_cr_w, dense.data(), dense.size() * sizeof(float), cudaMemcpyHostToDevice));
+            if (cluster_rollout_weights_fit(dense.data(), NC, c->max_R)) {
+                ALLOC(c->d_cr_w, dense.size());
+                CK_INIT(cudaMemcpy(c->d_cr_w, dense.data(), dense.size() * sizeof(float), cudaMemcpyHostToDevice));
+            } else {
+                c->cr_Q = 0;
+            }
         }
     }
     if (path == LENIA_CONV_DIRECT) {

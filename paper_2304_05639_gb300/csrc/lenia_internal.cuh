@@ -229,6 +229,9 @@ struct ClusterRolloutParams {
 };
 // Blocks of the cluster the world can run on (16 or 8), or 0 if it cannot.
 int cluster_rollout_blocks(int H, int W, int C, int K, int maxR);
+// true when the dense [K][2 maxR + 1]^2 weights are zero wherever the
+// cluster rollout skips them (outside the disk |d| < maxR, row group by row group)
+bool cluster_rollout_weights_fit(const float* w, int K, int maxR);
 size_t cluster_rollout_smem(int H, int W, int C, int K, int maxR, int Q);
 cudaError_t launch_cluster_rollout(const ClusterRolloutParams& p, cudaStream_t s);
 
