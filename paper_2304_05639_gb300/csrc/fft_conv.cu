@@ -33,6 +33,11 @@ namespace lenia {
 // unswizzled, at the start of the work buffer, and the first pass reads them
 // from there (its stores follow the pass's barrier, so the two layouts may
 // share the buffer).  Otherwise the first pass reads A directly.
+// Where every pass has 32 butterflies per row (M = 1024: two radix-32
+// passes) and a block has one warp per row, each row instead gets its own
+// bulk copy and mbarrier and lands at its work pitch, and its warp
+// transforms it in place as soon as it arrives, synchronising only itself;
+// the block meets once, before the even/odd split that mixes rows.
 template <int M, int T, int NB, bool BULK>
 __global__ void __launch_bounds__(T, 3) k_rows_r2c(FftParams p)
 {
@@ -47,7 +52,32 @@ __global__ void __launch_bounds__(T, 3) k_rows_r2c(FftParams p)
     const float2* src = reinterpret_cast<const float2*>(plane + (size_t)y0 * W);
     auto sld = [&](int b, int i) { return sm[b * SZ + swz32(i)]; };
     auto sst = [&](int b, int i, float2 v) { sm[b * SZ + swz32(i)] = v; };
-    if constexpr (BULK) {
+    // two radix-32 passes of 32 butterflies per row, one warp per row
+    constexpr bool ROWPIPE = BULK && ROW_RMAX == 32 && M == 32 * 32 && T == 32 * NB;
+    if constexpr (ROWPIPE) {
+        __shared__ uint64_t bars[NB];
+        if (threadIdx.x == 0) {
+            for (int b = 0; b < NB; b++) mbar_init(&bars[b], 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int b = 0; b < NB; b++) {
+                mbar_arrive_expect_tx(&bars[b], (uint32_t)M * sizeof(float2));
+                bulk_g2s(sm + (size_t)b * SZ, src + (size_t)b * M, (uint32_t)M * sizeof(float2), &bars[b]);
+            }
+        }
+        const bool landed = mbar_wait_bounded(&bars[threadIdx.x >> 5], 0);    // this warp's row
+        auto ld_s = [&](int b, int i) { return sm[b * SZ + i]; };
+        fft_run<M, NB, T, false, false, ROW_RMAX, 1, false, true>(p.tw_M, ld_s, sld, sst, sst);
+        if (!__syncthreads_and(landed)) {
+            if (threadIdx.x == 0) {
+                if (p.status) atomicExch(p.status, kStatusWaitTimeout);
+                for (int b = 0; b < NB; b++) mbar_wait_bounded(&bars[b], 0);
+            }
+            return;
+        }
+    } else if constexpr (BULK) {
         __shared__ uint64_t bar;
         constexpr uint32_t bytes = (uint32_t)NB * M * sizeof(float2);
         if (threadIdx.x == 0) {

@@ -162,8 +162,10 @@ __host__ __device__ constexpr int fft_tw_offset(int N, int NS, int rmax = 16)
 // One Stockham pass over NB independent length-N transforms held by a block of
 // T threads.  Element i of transform b is read with ld(b, i) and written with
 // st(b, i, v).  BFAST: consecutive threads take consecutive transforms b
-// (interleaved layouts), else consecutive butterflies j.
-template <int N, int R, int NB, int T, bool INV, bool BFAST, bool PK = false, class LD, class ST>
+// (interleaved layouts), else consecutive butterflies j.  SW: each warp's
+// butterflies and shared-memory elements belong to the warp alone (one
+// transform per warp), so the pass synchronises the warp, not the block.
+template <int N, int R, int NB, int T, bool INV, bool BFAST, bool PK = false, bool SW = false, class LD, class ST>
 __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp, LD ld, ST st)
 {
     constexpr int NBF = NB * (N / R);
@@ -197,7 +199,8 @@ __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp,
             DFT<R, INV, PK>::run(v[p]);
         }
     }
-    __syncthreads();
+    if constexpr (SW) __syncwarp();
+    else __syncthreads();
 #pragma unroll
     for (int p = 0; p < PER; p++) {
         const int u = threadIdx.x + p * T;
@@ -210,14 +213,15 @@ __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp,
             for (int q = 0; q < R; q++) st(b, base + q * Ns, v[p][q]);
         }
     }
-    __syncthreads();
+    if constexpr (SW) __syncwarp();
+    else __syncthreads();
 }
 
 // Full transform: pass 1 reads with ld_first, middle passes use the shared
 // accessors sld/sst, the last pass writes with st_last.  With a single pass
 // the first reader and the last writer are used together.
-template <int N, int NB, int T, bool INV, bool BFAST, int RMAX = 16, int NS = 1, bool PK = false, class LF,
-          class SL, class SS, class STL>
+template <int N, int NB, int T, bool INV, bool BFAST, int RMAX = 16, int NS = 1, bool PK = false, bool SW = false,
+          class LF, class SL, class SS, class STL>
 __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_first, SL sld, SS sst, STL st_last)
 {
     constexpr int R = fft_radix(N / NS, RMAX);
@@ -225,15 +229,15 @@ __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_fir
     constexpr bool last = (NS * R == N);
     const float2* twp = tw + fft_tw_offset(N, NS, RMAX);
     if constexpr (first && last) {
-        fft_pass<N, R, NB, T, INV, BFAST, PK>(NS, twp, ld_first, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK, SW>(NS, twp, ld_first, st_last);
     } else if constexpr (first) {
-        fft_pass<N, R, NB, T, INV, BFAST, PK>(NS, twp, ld_first, sst);
-        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK>(tw, ld_first, sld, sst, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK, SW>(NS, twp, ld_first, sst);
+        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK, SW>(tw, ld_first, sld, sst, st_last);
     } else if constexpr (last) {
-        fft_pass<N, R, NB, T, INV, BFAST, PK>(NS, twp, sld, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK, SW>(NS, twp, sld, st_last);
     } else {
-        fft_pass<N, R, NB, T, INV, BFAST, PK>(NS, twp, sld, sst);
-        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK>(tw, ld_first, sld, sst, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK, SW>(NS, twp, sld, sst);
+        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK, SW>(tw, ld_first, sld, sst, st_last);
     }
 }
 
