@@ -208,7 +208,9 @@ LENIA_API lenia_status lenia_backward(lenia_ctx* ctx, const float* A0, const flo
 LENIA_API lenia_status lenia_set_genes(lenia_ctx* ctx, const float* genes);
 
 /* Mass, circular-mean centre y, centre x of each channel of A: out is a
- * device array of C*3 floats.  Sums run in a fixed order (deterministic). */
+ * device array of C*3 floats.  Sums run in a fixed order (deterministic),
+ * block records and their reduction in compensated FP32 pairs (hi + lo),
+ * the arctangents in FP64. */
 LENIA_API lenia_status lenia_stats(lenia_ctx* ctx, const float* A, float* out, void* stream);
 
 /* Potentials U_k = K~_k * A_src(k) for every kernel (Algorithm 2, convolve
