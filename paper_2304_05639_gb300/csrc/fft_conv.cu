@@ -317,7 +317,7 @@ __device__ __noinline__ void cols_conv_dc(const FftParams& p, float2* Bf, int pl
     auto sld = [&](int, int i) { return Bf[swx(i)]; };
     auto sst = [&](int, int i, float2 v) { Bf[swx(i)] = v; };
     for (int t = t0; t < nk; t++) {
-        fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sld, sst, sst);
+        fft_run<H, 1, T, false, false, 16, 1, true, false, true>(p.tw_H, ld_g, sld, sst, sst);
         const int k = p.klist[c][t];
         const float* Sk = Sw + (size_t)k * (M + 1) * HS;
         // the first inverse pass reads every input before its barrier, so it
@@ -333,7 +333,7 @@ __device__ __noinline__ void cols_conv_dc(const FftParams& p, float2* Bf, int pl
         };
         float2* dst = p.Uhat + ((size_t)(w * p.kpw + k - p.k_base) * M) * H;
         auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
-        fft_run<H, 1, T, true, false, 16, 1, true>(p.tw_H, ld_mul, sld, sst, st_g);
+        fft_run<H, 1, T, true, false, 16, 1, true, false, true>(p.tw_H, ld_mul, sld, sst, st_g);
     }
 }
 
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
     constexpr int R1 = fft_radix(H, 16);
     if constexpr (!TM) {
         if (t0 < nk) fetch_s(t0);
-        fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
+        fft_run<H, 1, T, false, false, 16, 1, true, false, true>(p.tw_H, ld_g, sldF, sstF, sstF);
         auto ld_mul = [&](int, int i) { return cscale(F[swx(i)], Sb[i <= H / 2 ? i : H - i]); };
         for (int t = t0; t < nk; t++) {
             const int k = p.klist[c][t];
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
             // first pass (reads Sb, then a barrier), then the next column's copy
             fft_pass<H, R1, 1, T, true, false, true>(1, p.tw_H, ld_mul, sstW);
             if (t + 1 < nk) fetch_s(t + 1);
-            fft_run<H, 1, T, true, false, 16, R1, true>(p.tw_H, sldW, sldW, sstW, st_g);
+            fft_run<H, 1, T, true, false, 16, R1, true, false, true>(p.tw_H, sldW, sldW, sstW, st_g);
         }
     } else {
         // The first inverse pass (radix 16, one butterfly per thread) takes
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
             tmem_fence_before_sync();
         }
         if (t0 < nk) fetch_s(t0);
-        fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);   // ends with a barrier
+        fft_run<H, 1, T, false, false, 16, 1, true, false, true>(p.tw_H, ld_g, sldF, sstF, sstF);   // ends with a barrier
         tmem_fence_after_sync();
         const uint32_t taddr = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
         {
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
             if (t + 1 < nk) fetch_s(t + 1);
             float2* dst = p.Uhat + ((size_t)(w * p.kpw + k - p.k_base) * M + kx) * H;
             auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
-            fft_run<H, 1, T, true, false, 16, R1, true>(p.tw_H, sldW, sldW, sstW, st_g);
+            fft_run<H, 1, T, true, false, 16, R1, true, false, true>(p.tw_H, sldW, sldW, sstW, st_g);
         }
         tmem_fence_before_sync();
         __syncthreads();
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_adj(Fft
         const int k = p.klist[c][t];
         const float2* src = p.Ahat + ((size_t)k * M + kx) * H;
         auto ld_g = [&](int, int i) { return __ldg(&src[i]); };
-        fft_run<H, 1, T, false, false, 16, 1, true>(p.tw_H, ld_g, sldF, sstF, sstF);
+        fft_run<H, 1, T, false, false, 16, 1, true, false, true>(p.tw_H, ld_g, sldF, sstF, sstF);
         const float* Sk = p.S + (size_t)k * (M + 1) * HS;
         // each thread updates its own entries of Acc (no barrier needed between
         // the zeroing and the updates); F is complete after fft_run's barrier
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_adj(Fft
     float2* dst = p.Uhat + ((size_t)c * M + kx) * H;
     auto ld_acc = [&](int, int i) { return Acc[swx(i)]; };
     auto st_g = [&](int, int i, float2 v) { dst[i] = v; };
-    fft_run<H, 1, T, true, false, 16, 1, true>(p.tw_H, ld_acc, sldF, sstF, st_g);
+    fft_run<H, 1, T, true, false, 16, 1, true, false, true>(p.tw_H, ld_acc, sldF, sstF, st_g);
 }
 
 // ------------------------------------------------------------ dispatch

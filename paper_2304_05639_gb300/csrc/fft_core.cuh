@@ -165,7 +165,11 @@ __host__ __device__ constexpr int fft_tw_offset(int N, int NS, int rmax = 16)
 // (interleaved layouts), else consecutive butterflies j.  SW: each warp's
 // butterflies and shared-memory elements belong to the warp alone (one
 // transform per warp), so the pass synchronises the warp, not the block.
-template <int N, int R, int NB, int T, bool INV, bool BFAST, bool PK = false, bool SW = false, class LD, class ST>
+// TWC: only w and w^4 come from the table; w^2, w^3 and w^(4a) for a > 1 are
+// products of them (squarings first, at most three roundings deep), which
+// trades table loads through L1 for multiplies.
+template <int N, int R, int NB, int T, bool INV, bool BFAST, bool PK = false, bool SW = false, bool TWC = false,
+          class LD, class ST>
 __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp, LD ld, ST st)
 {
     constexpr int NBF = NB * (N / R);
@@ -185,10 +189,27 @@ __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp,
                 // w^r for r = 4a + b: w^b (b < 4) and w^(4a) from the table,
                 // their product for the others (one rounding more)
                 float2 wb[4], wa[R / 4 > 0 ? R / 4 : 1];
+                if constexpr (TWC && R >= 8) {
+                    wb[1] = __ldg(&twp[k]);
+                    wa[1] = __ldg(&twp[3 * Ns + k]);
+                    wb[2] = cmul(wb[1], wb[1]);
+                    wb[3] = cmul(wb[2], wb[1]);
+                    if constexpr (R >= 16) {
+                        wa[2] = cmul(wa[1], wa[1]);
+                        wa[3] = cmul(wa[2], wa[1]);
+                    }
+                    if constexpr (R >= 32) {
+                        wa[4] = cmul(wa[2], wa[2]);
+                        wa[5] = cmul(wa[4], wa[1]);
+                        wa[6] = cmul(wa[4], wa[2]);
+                        wa[7] = cmul(wa[6], wa[1]);
+                    }
+                } else {
 #pragma unroll
-                for (int b2 = 1; b2 < 4 && b2 < R; b2++) wb[b2] = __ldg(&twp[(b2 - 1) * Ns + k]);
+                    for (int b2 = 1; b2 < 4 && b2 < R; b2++) wb[b2] = __ldg(&twp[(b2 - 1) * Ns + k]);
 #pragma unroll
-                for (int a = 1; a < R / 4; a++) wa[a] = __ldg(&twp[(4 * a - 1) * Ns + k]);
+                    for (int a = 1; a < R / 4; a++) wa[a] = __ldg(&twp[(4 * a - 1) * Ns + k]);
+                }
 #pragma unroll
                 for (int r = 1; r < R; r++) {
                     const int a = r / 4, b2 = r % 4;
@@ -221,7 +242,7 @@ __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp,
 // accessors sld/sst, the last pass writes with st_last.  With a single pass
 // the first reader and the last writer are used together.
 template <int N, int NB, int T, bool INV, bool BFAST, int RMAX = 16, int NS = 1, bool PK = false, bool SW = false,
-          class LF, class SL, class SS, class STL>
+          bool TWC = false, class LF, class SL, class SS, class STL>
 __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_first, SL sld, SS sst, STL st_last)
 {
     constexpr int R = fft_radix(N / NS, RMAX);
@@ -229,15 +250,15 @@ __device__ __forceinline__ void fft_run(const float2* __restrict__ tw, LF ld_fir
     constexpr bool last = (NS * R == N);
     const float2* twp = tw + fft_tw_offset(N, NS, RMAX);
     if constexpr (first && last) {
-        fft_pass<N, R, NB, T, INV, BFAST, PK, SW>(NS, twp, ld_first, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK, SW, TWC>(NS, twp, ld_first, st_last);
     } else if constexpr (first) {
-        fft_pass<N, R, NB, T, INV, BFAST, PK, SW>(NS, twp, ld_first, sst);
-        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK, SW>(tw, ld_first, sld, sst, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK, SW, TWC>(NS, twp, ld_first, sst);
+        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK, SW, TWC>(tw, ld_first, sld, sst, st_last);
     } else if constexpr (last) {
-        fft_pass<N, R, NB, T, INV, BFAST, PK, SW>(NS, twp, sld, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK, SW, TWC>(NS, twp, sld, st_last);
     } else {
-        fft_pass<N, R, NB, T, INV, BFAST, PK, SW>(NS, twp, sld, sst);
-        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK, SW>(tw, ld_first, sld, sst, st_last);
+        fft_pass<N, R, NB, T, INV, BFAST, PK, SW, TWC>(NS, twp, sld, sst);
+        fft_run<N, NB, T, INV, BFAST, RMAX, NS * R, PK, SW, TWC>(tw, ld_first, sld, sst, st_last);
     }
 }
 
