@@ -405,21 +405,24 @@ __global__ void __launch_bounds__(T, 1024 / T < 8 ? 1024 / T : 8) k_cols_conv(Ff
             tmem_fence_before_sync();
         }
         if (t0 < nk) fetch_s(t0);
-        fft_run<H, 1, T, false, false, 16, 1, true, false, true>(p.tw_H, ld_g, sldF, sstF, sstF);   // ends with a barrier
+        // The forward transform's last pass (sub-transforms of 256, radix
+        // H / 256) leaves butterfly p of thread j with outputs j + p T + q 256
+        // (q < H / 256), which are exactly this thread's elements j + r TS,
+        // r = p + q (256 / T): they go from registers to TMEM, not through
+        // shared memory.
+        static_assert(H / 256 <= 16 && (H / 256) * (256 / T) * T == H && 256 % T == 0, "last forward pass layout");
+        constexpr int PL = 256 / T;                           // butterflies per thread in the last pass
+        float fv[32];
+        auto st_reg = [&](int, int, float2 v, int pp, int q) {
+            fv[2 * (pp + q * PL)] = v.x;
+            fv[2 * (pp + q * PL) + 1] = v.y;
+        };
+        fft_run<H, 1, T, false, false, 16, 1, true, false, true>(p.tw_H, ld_g, sldF, sstF, st_reg);   // ends with a barrier
         tmem_fence_after_sync();
         const uint32_t taddr = tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
-        {
-            float fv[32];
-#pragma unroll
-            for (int r = 0; r < 16; r++) {
-                const float2 f = F[swx(j + r * TS)];
-                fv[2 * r] = f.x;
-                fv[2 * r + 1] = f.y;
-            }
-            tmem_st16(taddr, fv);
-            tmem_st16(taddr + 16, fv + 16);
-            tmem_wait_st();
-        }
+        tmem_st16(taddr, fv);
+        tmem_st16(taddr + 16, fv + 16);
+        tmem_wait_st();
         for (int t = t0; t < nk; t++) {
             const int k = p.klist[c][t];
             cp_async_wait_all();

@@ -26,6 +26,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace lenia {
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -231,7 +233,11 @@ __device__ __forceinline__ void fft_pass(int Ns, const float2* __restrict__ twp,
             const int k = j & (Ns - 1);
             const int base = (j - k) * R + k;
 #pragma unroll
-            for (int q = 0; q < R; q++) st(b, base + q * Ns, v[p][q]);
+            for (int q = 0; q < R; q++) {
+                // a writer that also takes (p, q) can place the output in registers
+                if constexpr (std::is_invocable_v<ST, int, int, float2, int, int>) st(b, base + q * Ns, v[p][q], p, q);
+                else st(b, base + q * Ns, v[p][q]);
+            }
         }
     }
     if constexpr (SW) __syncwarp();
