@@ -72,6 +72,21 @@ def test_kernel_bump_form(oracle):
     assert K[c, c + 10] == 0.0                 # rho = 1 is outside
 
 
+@pytest.mark.parametrize("R,form,beta,bump", [(13, 0, (1.0,), None), (18, 0, (0.3, 0.9, 0.5), None),
+                                              (16, 0, (1.0, 0.5), None),
+                                              (12, 1, (1.0,), (0.3, 0.15, 1.0, 0.8, 0.1, 0.5))])
+def test_kernel_support_is_open_disk(oracle, R, form, beta, bump):
+    """Algorithm 1: the kernel is defined for d / R < 1 only, so every tap with
+    dx^2 + dy^2 >= R^2 is zero (the corners of the (2R+1)^2 square and the
+    axis taps at distance R), while taps well inside the disk are not."""
+    K = oracle.kernel(R, form, beta) if bump is None else oracle.kernel(R, form, bump=bump)
+    dy, dx = np.mgrid[-R:R + 1, -R:R + 1]
+    outside = dx * dx + dy * dy >= R * R
+    assert (K[outside] == 0.0).all()
+    assert K[R, 0] == 0.0 and K[0, R] == 0.0          # |d| = R exactly
+    assert (K[~outside] > 0).sum() > 0.5 * (~outside).sum()
+
+
 # ------------------------------------------------------------ convolution
 
 def _embed(K, H, W):
