@@ -684,15 +684,15 @@ __global__ void __launch_bounds__(256, 3) k_epilogue_rings(EpiParams p)
         const float num = num2.x + num2.y, den = den2.x + den2.y;
         // the channel's last kernel: fetch the next channel's potentials now
         if (j + 1 < KT && p.kt.src[ord[j + 1]] != c) stage_v(p.kt.src[ord[j + 1]]);
-        const float u = den > 0.f ? num / den : 0.f;
-        // growth (as in the other epilogues)
+        const float u = den > 0.f ? num * rcp_approx(den) : 0.f;
+        // growth (the streaming epilogue's arithmetic: hardware reciprocal and exponential)
         const float m = PMU >= 0 ? g[PMU >= 0 ? PMU : 0] : p.kt.mu[k];
         const float sg = PSG >= 0 ? g[PSG >= 0 ? PSG : 0] : p.kt.sigma[k];
         const float hh = PH >= 0 ? g[PH >= 0 ? PH : 0] : p.kt.h[k];
         float gk = 0.f;
         if (sg > 0.f) {
-            const float z = (u - m) / sg;
-            gk = expf(-0.5f * z * z);
+            const float z = (u - m) * rcp_approx(sg);
+            gk = ex2_approx(-0.721347520444481703680f * (z * z));
         }
         const float t = p.alpha_on ? u : hh * gk;
         tsum += t;
